@@ -1,0 +1,222 @@
+/*
+ * voxsim.h -- C ABI of the GB300 (sm_103a) voxel soft-robot co-design library.
+ *
+ * The library runs, on one GPU, the data-parallel hot path of "CUDA-Accelerated Soft Robot
+ * Neural Evolution with Large Language Model Supervision" (L. Zhang, arXiv 2405.00698):
+ *   decode (Gaussian positional encoding, Eq. (1), and the MLP spatial query, Section II-C)
+ *   -> largest connected component -> masses / springs (Section II-A, Table II)
+ *   -> batched time stepping (spring and mass updates, Section II-C)
+ *   -> centroid fitness -> elite selection, crossover, mutation (Section II-C, Table I)
+ *   and the reverse-mode adjoint of the time stepping.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  A `mem` argument says where a caller buffer lives:
+ *     SIM_MEM_HOST (ordinary or pinned host memory) or SIM_MEM_DEVICE (device memory of the
+ *     context's GPU, e.g. a torch tensor's data_ptr()).
+ *   - The caller owns every buffer it passes.  The library copies what it needs before the call
+ *     returns and keeps no caller pointer afterwards.
+ *   - Work is enqueued on the context's stream.  Calls that write host memory synchronise that
+ *     stream before returning; device-to-device calls are asynchronous.
+ *   - Nothing aborts or exits.  Every call returns a sim_status; sim_last_error() gives the
+ *     message of the most recent failure on the calling thread.
+ *   - One context per thread at a time; a context is not safe for concurrent calls.
+ *
+ * Material ids (Section II-A): 0 empty, 1 expanding muscle, 2 contracting muscle,
+ * 3 soft tissue, 4 bone.
+ */
+#ifndef VOXSIM_H
+#define VOXSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = 1,    /* bad argument (size, pointer, mode, out-of-range value) */
+    SIM_ENOMEM = 2,    /* device or host allocation failed */
+    SIM_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    SIM_ESTATE = 4,    /* call out of order (e.g. stepping before a population is set) */
+    SIM_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    SIM_ENUMERIC = 6   /* non-finite values where finite ones are required */
+} sim_status;
+
+enum { SIM_MEM_HOST = 0, SIM_MEM_DEVICE = 1 };
+
+/* How sim_set_population reads `genomes`. */
+enum {
+    SIM_MODE_MATERIALS = 0, /* uint8 material id per voxel, all robots' grids concatenated */
+    SIM_MODE_LOGITS = 1,    /* float32 [voxels][5] material scores; material = argmax (lowest id
+                               on ties), material weight 1 */
+    SIM_MODE_MLP = 2,       /* float32 [P][20998] MLP genomes, queried at every voxel centre */
+    SIM_MODE_PARAMS = 3     /* const sim_voxel_params*: materials plus per-voxel weight,
+                               stiffness and phase (the differentiable parametrisation) */
+};
+
+/* Force accumulation of the time stepping kernels. */
+enum {
+    SIM_ACC_AUTO = 0,   /* library choice (measured default) */
+    SIM_ACC_ATOMIC = 1, /* per-spring threads add into per-mass accumulators atomically */
+    SIM_ACC_GATHER = 2  /* per-mass threads gather their springs' forces in a fixed order:
+                           bit-reproducible */
+};
+
+/* Execution path of the time stepping. */
+enum {
+    SIM_PATH_AUTO = 0,      /* resident for robots whose masses fit on chip, streamed otherwise */
+    SIM_PATH_RESIDENT = 1,  /* one thread-block group per robot, state in shared memory for all
+                               steps of a call */
+    SIM_PATH_STREAMED = 2   /* structure-of-arrays state in device memory, one pass per step */
+};
+
+/* Physics constants (Table II; the workload configurations override some of them) and
+ * execution choices. */
+typedef struct {
+    double dt;          /* time step [s] */
+    double gravity;     /* [m/s^2] */
+    double mass;        /* point mass per voxel corner [kg] */
+    double edge;        /* voxel edge = original rest length [m] */
+    double damping;     /* velocity multiplier applied every step (1 = none) */
+    double k_ground;    /* ground penalty stiffness [N/m] */
+    double mu_s;        /* static friction coefficient */
+    double mu_k;        /* kinetic friction coefficient */
+    double freq;        /* muscle actuation frequency [Hz] */
+    double dead_bound;  /* |coordinate| beyond this marks a robot dead [m] */
+    double k_mat[5];    /* stiffness per material [N/m] */
+    double amp_mat[5];  /* actuation amplitude per material, fraction of the rest length */
+    double phase_mat[5];/* actuation phase per material [rad] */
+    int32_t ground_on;  /* 0 removes the ground plane */
+    int32_t accumulate; /* SIM_ACC_* */
+    int32_t path;       /* SIM_PATH_* */
+    int32_t threads;    /* threads per robot on the resident path; 0 = autotuned */
+} sim_params;
+
+/* Per-voxel parametrisation for SIM_MODE_PARAMS (all arrays cover every voxel of every grid):
+ * stiffness k_v = w_v * kappa_v, actuation amplitude a_v = w_v * amp_mat[material], phase phi_v. */
+typedef struct {
+    const uint8_t* mat;
+    const float* w;
+    const float* kappa;
+    const float* phi;
+} sim_voxel_params;
+
+/* Evolution rates (Table I; configuration values: elites 25 %, sigma 0.05, rate 0.1). */
+typedef struct {
+    int32_t elites;         /* E >= 1: genomes kept unchanged */
+    uint32_t mut_threshold; /* a gene mutates when its 32-bit draw is below this
+                               (floor(rate * 2^32)) */
+    float sigma;            /* standard deviation of the Gaussian mutation */
+    int32_t pad_;
+    uint64_t seed;          /* seed of the counter-based generator */
+} evo_params;
+
+typedef struct voxsim_ctx voxsim_ctx;
+
+/* Create a context on CUDA device `device`, enqueueing all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  `p` is copied.  Errors: SIM_EINVAL for a
+ * NULL out pointer or non-positive dt / mass / edge, SIM_ECUDA if the device cannot be used. */
+sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, voxsim_ctx** out);
+
+/* Release every device buffer of the context (synchronises its stream first).  NULL is a no-op. */
+sim_status sim_destroy(voxsim_ctx* ctx);
+
+/* Message of the most recent failed call on this thread ("" if none).  Valid until the next
+ * call on this thread. */
+const char* sim_last_error(const voxsim_ctx* ctx);
+
+/* Replace the population: P robots, robot r on a dims[3r] x dims[3r+1] x dims[3r+2] voxel grid
+ * (each 1..64; host array).  Voxel (i, j, k) of robot r is entry i + nx*(j + ny*k) of its grid,
+ * grids concatenated in robot order.  Decoding by `mode` (see SIM_MODE_*); for SIM_MODE_MLP
+ * `B` is the float32 [128][3] Gaussian encoding matrix of Eq. (1) in the same memory as
+ * `genomes` and all robots must share one grid shape.  Then, per robot: only the largest
+ * face-connected component of occupied voxels is kept (size ties keep the component holding
+ * the smallest voxel index); masses sit at the corners of kept voxels (ascending corner id
+ * ci + (nx+1)*(cj + (ny+1)*ck)); springs join the 28 corner pairs of every kept voxel, one
+ * spring per distinct pair, with stiffness and actuation terms averaged over the kept voxels
+ * that share it; the initial pose is the lattice at rest with its lowest mass at z = 0, and the
+ * step counter restarts at 0.  Errors: SIM_EINVAL (sizes, mode, pointers), SIM_ENOMEM. */
+sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, int32_t mode,
+                              const void* genomes, const float* B, int32_t mem);
+
+/* Advance every robot by n_steps time steps (Section II-C: each spring's force with its
+ * sinusoidal rest-length actuation, accumulation onto masses, gravity, ground contact with
+ * static / kinetic friction, semi-implicit Euler with velocity damping; Table II).  Time of
+ * step n is n * dt from the last sim_set_population.  When checkpointing is on
+ * (sim_set_checkpointing), the call records the states the adjoint needs.
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL for n_steps < 0. */
+sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
+
+/* Fitness of every robot: centroid displacement along +x since the initial pose (the paper
+ * names "fitness", Section III; the displacement is the workloads' definition), reduced in
+ * FP64.  Empty robots score 0; a robot with a non-finite coordinate, or one beyond dead_bound,
+ * scores -infinity.  out: double [P] in `mem`. */
+sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
+
+/* One generation of the evolutionary step, fully on the GPU (Section II-C; Table I):
+ * rank by fitness (descending, ties by ascending index, NaN as -infinity); copy the E best
+ * genomes unchanged into rows 0..E-1 in rank order; every row c >= E is a uniform crossover of
+ * two elites (parent ranks floor(u E / 2^32) from the draws (c, parent A / B); gene j from
+ * parent A when the top bit of draw (c, j, mask) is set) followed by Gaussian mutation
+ * (when draw (c, j, mutate) < mut_threshold add sigma * sqrt(-2 ln u1) cos(2 pi u2),
+ * u1 = (draw(c, j, u1) + 1) / 2^32, u2 = draw(c, j, u2) / 2^32).  A draw is the high 32 bits of
+ * SplitMix64 output number ((((generation << 16 | c) << 26 | j) << 3) | purpose) of the stream
+ * seeded with e->seed; purposes: parent A 0, parent B 1, mask 2, mutate 3, u1 4, u2 5.
+ * fitness: double [P]; genomes_in / genomes_out: float [P][G] (may alias: the input is copied
+ * first); parents_out: int32 [P][2] or NULL (elites name themselves twice); mask_out: uint8
+ * [P][G] or NULL (1 = gene from parent A, 0 for elites).  All device memory of the context's
+ * GPU.  Limits: 1 <= E <= P <= 65536, G <= 2^26, generation < 2^19.
+ * Errors: SIM_EINVAL, SIM_ENOMEM (library scratch). */
+sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* genomes_in,
+                          float* genomes_out, int32_t P, int32_t G, const evo_params* e,
+                          uint64_t generation, int32_t* parents_out, uint8_t* mask_out);
+
+/* Turn state checkpointing on (every k_steps steps, k_steps >= 1) or off (0).  While on, each
+ * sim_step_n call records the state at its start and every k_steps steps after, which
+ * sim_backward replays.  Errors: SIM_EINVAL, SIM_ENOMEM. */
+sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
+
+/* Reverse-mode gradient of L = sum_r dL_df[r] * fitness_r over the most recent recorded
+ * sim_step_n call, with respect to the per-voxel material weight w, stiffness kappa and
+ * actuation phase phi (k_v = w_v kappa_v, a_v = w_v amp_mat[material], phase phi_v).  The
+ * forward steps are recomputed from the checkpoints segment by segment, bit-identically, and
+ * each segment is swept backwards; contact modes of the forward run are held fixed.  Empty
+ * voxels get 0.  dL_df: double [P]; g_w, g_kappa, g_phi: float, one entry per voxel of every
+ * grid (concatenated as in sim_set_population); all device memory.
+ * Errors: SIM_ESTATE without a recorded run, SIM_EINVAL, SIM_ENOMEM. */
+sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
+                        float* g_phi);
+
+/* Mass and spring count of every robot (host arrays of P int32; either may be NULL).
+ * Synchronises the stream.  Errors: SIM_ESTATE without a population. */
+sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs);
+
+/* Current state: positions and velocities (float32 [total masses][3], robots in order, masses
+ * in ascending corner order); mass_offsets: int32 [P+1] prefix offsets (host) or NULL.  Any
+ * output may be NULL.  mem applies to x_out and v_out. */
+sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* mass_offsets,
+                         int32_t mem);
+
+/* Decoded voxels before / after the largest-component filter and the per-voxel parameters
+ * actually simulated (host arrays over all voxels; any may be NULL). */
+sim_status sim_get_voxels(voxsim_ctx* ctx, uint8_t* mat_decoded, uint8_t* mat_kept, float* w,
+                          float* kappa, float* phi);
+
+/* Topology (host arrays, robots concatenated, sized by sim_get_counts): mass_corner int32 per
+ * mass; spring_ab int32 [springs][2] (mass indices within the robot, a < b, sorted by (a, b));
+ * spring_params float [springs][4] = rest length, stiffness, alpha, beta with the actuated rest
+ * length L0 (1 + alpha sin(w t) + beta cos(w t)).  Any may be NULL. */
+sim_status sim_get_topology(voxsim_ctx* ctx, int32_t* mass_corner, int32_t* spring_ab,
+                            float* spring_params);
+
+/* Since the last call: cumulative device time of the time-stepping kernels (milliseconds,
+ * CUDA events on the context's stream) and the number of kernels the library launched (all
+ * entry points).  Synchronises the stream and resets both. */
+sim_status sim_get_timing(voxsim_ctx* ctx, double* step_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOXSIM_H */

@@ -1,0 +1,644 @@
+// Host side of the C ABI declared in include/voxsim.h: context, device buffers, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace vx;
+
+namespace {
+
+thread_local std::string g_err;
+
+sim_status fail(sim_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+sim_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define VX_CK(call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
+    } while (0)
+
+// A kernel launch through one of the launch_* helpers, counted for sim_get_timing.
+#define VX_LAUNCH(ctx, call)                                          \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
+        (ctx)->launches += 1;                                         \
+    } while (0)
+
+// Device buffer that only grows.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= n && p) return cudaSuccess;
+        release();
+        if (want == 0) want = 1;
+        cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
+        if (e != cudaSuccess) { p = nullptr; n = 0; return e; }
+        n = want;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int64_t full_springs(int nx, int ny, int nz)
+{
+    const int64_t X = nx, Y = ny, Z = nz;
+    const int64_t edges = X * (Y + 1) * (Z + 1) + Y * (X + 1) * (Z + 1) + Z * (X + 1) * (Y + 1);
+    const int64_t faces = 2 * (X * Y * (Z + 1) + X * Z * (Y + 1) + Y * Z * (X + 1));
+    return edges + faces + 4 * X * Y * Z;
+}
+
+}  // namespace
+
+struct voxsim_ctx {
+    sim_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    // population layout (host copies)
+    int P = 0;
+    bool have_pop = false;
+    std::vector<int> dims;
+    std::vector<int64_t> voff, moff, soff;
+    int64_t V_tot = 0, M_cap = 0, S_cap = 0;
+    int max_corner = 0;
+    int64_t max_spring_cap = 0;
+    int64_t step = 0;
+    // device buffers
+    DevBuf<int> d_dims;
+    DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
+    DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status;
+    DevBuf<uint8_t> d_in_u8, d_mat_raw, d_mat;
+    DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
+    DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
+    DevBuf<int2> d_sab;
+    DevBuf<float4> d_sp, d_spack, d_x, d_v;
+    DevBuf<double> d_x0c, d_keys, d_fit;
+    DevBuf<float2> d_sc;
+    DevBuf<unsigned char> d_pe;
+    DevBuf<float> d_compact;
+    // evolution scratch
+    DevBuf<int> d_order;
+    DevBuf<float> d_gcopy;
+    // timing: one event pair per stepping call since the last sim_get_timing
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double step_ms = 0.0;
+    int64_t launches = 0;
+
+    PopView view()
+    {
+        PopView v;
+        v.P = P;
+        v.dims = d_dims.p;
+        v.voff = d_voff.p;
+        v.moff = d_moff.p;
+        v.soff = d_soff.p;
+        v.n_mass = d_nm.p;
+        v.n_spring = d_ns.p;
+        return v;
+    }
+    MatConst matconst() const
+    {
+        MatConst m;
+        for (int i = 0; i < kNumMat; ++i) {
+            m.k[i] = (float)p.k_mat[i];
+            m.amp[i] = (float)p.amp_mat[i];
+            m.phase[i] = (float)p.phase_mat[i];
+        }
+        return m;
+    }
+    StepConst stepconst() const
+    {
+        StepConst c;
+        c.dt = (float)p.dt;
+        c.dt_over_m = (float)(p.dt / p.mass);
+        c.weight = (float)(p.mass * p.gravity);
+        c.damping = (float)p.damping;
+        c.k_ground = (float)p.k_ground;
+        c.mu_s = (float)p.mu_s;
+        c.mu_k = (float)p.mu_k;
+        c.edge = (float)p.edge;
+        c.edge_sqrt2 = (float)(p.edge * 1.4142135623730951);
+        c.edge_sqrt3 = (float)(p.edge * 1.7320508075688772);
+        c.ground_on = p.ground_on ? 1 : 0;
+        return c;
+    }
+};
+
+namespace {
+
+sim_status check_ctx(voxsim_ctx* ctx)
+{
+    if (!ctx) return fail(SIM_EINVAL, "null context");
+    return SIM_OK;
+}
+
+sim_status copy_in(const void* src, size_t bytes, int mem, void* dst, cudaStream_t s)
+{
+    if (bytes == 0) return SIM_OK;
+    if (!src) return fail(SIM_EINVAL, "null input pointer");
+    VX_CK(cudaMemcpyAsync(dst, src, bytes,
+                          mem == SIM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    return SIM_OK;
+}
+
+sim_status copy_out(void* dst, const void* src, size_t bytes, int mem, cudaStream_t s)
+{
+    if (bytes == 0) return SIM_OK;
+    VX_CK(cudaMemcpyAsync(dst, src, bytes,
+                          mem == SIM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (mem == SIM_MEM_HOST) VX_CK(cudaStreamSynchronize(s));
+    return SIM_OK;
+}
+
+__global__ void k_spring_keys(const int* ns, int P, double* keys)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) keys[i] = (double)ns[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_last_error(const voxsim_ctx*) { return g_err.c_str(); }
+
+sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, voxsim_ctx** out)
+{
+    if (!p || !out) return fail(SIM_EINVAL, "null argument");
+    *out = nullptr;
+    if (!(p->dt > 0) || !(p->mass > 0) || !(p->edge > 0))
+        return fail(SIM_EINVAL, "dt, mass and edge must be positive");
+    int ndev = 0;
+    VX_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SIM_EINVAL, "device %d out of range", device);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SIM_ECUDA, "cannot select device %d", device);
+    voxsim_ctx* c = new (std::nothrow) voxsim_ctx();
+    if (!c) return fail(SIM_ENOMEM, "host allocation");
+    c->p = *p;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = c;
+    return SIM_OK;
+}
+
+sim_status sim_destroy(voxsim_ctx* ctx)
+{
+    if (!ctx) return SIM_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;   // device buffers are released by their destructors
+    return SIM_OK;
+}
+
+sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, int32_t mode,
+                              const void* genomes, const float* B, int32_t mem)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (P < 0) return fail(SIM_EINVAL, "P must be >= 0");
+    if (P > 0 && !dims) return fail(SIM_EINVAL, "null dims");
+    if (mem != SIM_MEM_HOST && mem != SIM_MEM_DEVICE) return fail(SIM_EINVAL, "bad mem %d", mem);
+    if (mode < SIM_MODE_MATERIALS || mode > SIM_MODE_PARAMS) return fail(SIM_EINVAL, "bad mode %d", mode);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    // layout
+    std::vector<int> d(3 * (size_t)P);
+    std::vector<int64_t> voff(P + 1, 0), moff(P + 1, 0), soff(P + 1, 0);
+    int max_corner = 0;
+    int64_t max_sc = 0;
+    for (int r = 0; r < P; ++r) {
+        for (int a = 0; a < 3; ++a) {
+            int v = dims[3 * r + a];
+            if (v < 1 || v > kMaxAxis) return fail(SIM_EINVAL, "robot %d: dims must be in 1..%d", r, kMaxAxis);
+            d[3 * r + a] = v;
+        }
+        const int nx = d[3 * r], ny = d[3 * r + 1], nz = d[3 * r + 2];
+        const int corners = (nx + 1) * (ny + 1) * (nz + 1);
+        const int64_t sc = full_springs(nx, ny, nz);
+        voff[r + 1] = voff[r] + (int64_t)nx * ny * nz;
+        moff[r + 1] = moff[r] + corners;
+        soff[r + 1] = soff[r] + sc;
+        max_corner = std::max(max_corner, corners);
+        max_sc = std::max(max_sc, sc);
+    }
+    if (mode == SIM_MODE_MLP && P > 0) {
+        for (int r = 1; r < P; ++r)
+            if (d[3 * r] != d[0] || d[3 * r + 1] != d[1] || d[3 * r + 2] != d[2])
+                return fail(SIM_EINVAL, "MLP mode needs one grid shape for all robots");
+        if (!B) return fail(SIM_EINVAL, "MLP mode needs the encoding matrix B");
+    }
+    if (P > 0 && !genomes) return fail(SIM_EINVAL, "null genomes");
+    const int64_t V = voff[P], Mc = moff[P], Sc = soff[P];
+    const bool packed = max_corner <= kResidentMaxMass;
+    if (!packed && ctx->p.path == SIM_PATH_RESIDENT)
+        return fail(SIM_EINVAL, "robots with more than %d corners need the streamed path", kResidentMaxMass);
+    // host-side validation of host materials
+    if (mem == SIM_MEM_HOST && (mode == SIM_MODE_MATERIALS || mode == SIM_MODE_PARAMS)) {
+        const uint8_t* m = mode == SIM_MODE_MATERIALS ? (const uint8_t*)genomes
+                                                      : ((const sim_voxel_params*)genomes)->mat;
+        if (V > 0 && !m) return fail(SIM_EINVAL, "null materials");
+        for (int64_t i = 0; i < V; ++i)
+            if (m[i] >= kNumMat) return fail(SIM_EINVAL, "material id %d at voxel %lld", (int)m[i], (long long)i);
+    }
+    if (mode == SIM_MODE_PARAMS) {
+        const sim_voxel_params* vp = (const sim_voxel_params*)genomes;
+        if (V > 0 && (!vp->mat || !vp->w || !vp->kappa || !vp->phi))
+            return fail(SIM_EINVAL, "null per-voxel parameter array");
+    }
+    // buffers
+    VX_CK(ctx->d_dims.ensure(3 * (size_t)P));
+    VX_CK(ctx->d_voff.ensure(P + 1)); VX_CK(ctx->d_moff.ensure(P + 1)); VX_CK(ctx->d_soff.ensure(P + 1));
+    VX_CK(ctx->d_tmp_off.ensure(P + 1));
+    VX_CK(ctx->d_nm.ensure(P)); VX_CK(ctx->d_ns.ensure(P)); VX_CK(ctx->d_lpt.ensure(P));
+    VX_CK(ctx->d_queue.ensure(1)); VX_CK(ctx->d_status.ensure(4));
+    VX_CK(ctx->d_mat_raw.ensure(V)); VX_CK(ctx->d_mat.ensure(V));
+    VX_CK(ctx->d_w.ensure(V)); VX_CK(ctx->d_kappa.ensure(V)); VX_CK(ctx->d_phi.ensure(V));
+    VX_CK(ctx->d_label.ensure(V)); VX_CK(ctx->d_count.ensure(V));
+    VX_CK(ctx->d_corner_mass.ensure(Mc)); VX_CK(ctx->d_mass_corner.ensure(Mc));
+    VX_CK(ctx->d_sab.ensure(Sc)); VX_CK(ctx->d_sp.ensure(Sc));
+    if (packed) VX_CK(ctx->d_spack.ensure(Sc));
+    VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
+    VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
+    ctx->dims = d; ctx->voff = voff; ctx->moff = moff; ctx->soff = soff;
+    ctx->P = P; ctx->V_tot = V; ctx->M_cap = Mc; ctx->S_cap = Sc;
+    ctx->max_corner = max_corner; ctx->max_spring_cap = max_sc;
+    ctx->have_pop = false;
+    if (P > 0) {
+        VX_CK(cudaMemcpyAsync(ctx->d_dims.p, d.data(), sizeof(int) * 3 * P, cudaMemcpyHostToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_voff.p, voff.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_moff.p, moff.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_soff.p, soff.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
+    }
+    VX_CK(cudaMemsetAsync(ctx->d_status.p, 0, 4 * sizeof(int), s));
+    const MatConst mc = ctx->matconst();
+    // decode
+    if (P > 0) {
+        if (mode == SIM_MODE_MATERIALS) {
+            const uint8_t* src = (const uint8_t*)genomes;
+            if (mem == SIM_MEM_HOST) {
+                VX_CK(ctx->d_in_u8.ensure(V));
+                if (sim_status st = copy_in(genomes, V, mem, ctx->d_in_u8.p, s)) return st;
+                src = ctx->d_in_u8.p;
+            }
+            VX_LAUNCH(ctx, launch_decode_materials(src, V, mc, ctx->d_mat_raw.p, ctx->d_w.p, ctx->d_kappa.p,
+                                          ctx->d_phi.p, ctx->d_status.p, s));
+        } else if (mode == SIM_MODE_LOGITS) {
+            const float* src = (const float*)genomes;
+            if (mem == SIM_MEM_HOST) {
+                VX_CK(ctx->d_in_f32.ensure(5 * (size_t)V));
+                if (sim_status st = copy_in(genomes, sizeof(float) * 5 * V, mem, ctx->d_in_f32.p, s)) return st;
+                src = ctx->d_in_f32.p;
+            }
+            VX_LAUNCH(ctx, launch_decode_logits(src, V, mc, ctx->d_mat_raw.p, ctx->d_w.p, ctx->d_kappa.p,
+                                       ctx->d_phi.p, s));
+        } else if (mode == SIM_MODE_PARAMS) {
+            const sim_voxel_params* vp = (const sim_voxel_params*)genomes;
+            const uint8_t* m = vp->mat;
+            const float *w = vp->w, *k = vp->kappa, *ph = vp->phi;
+            if (mem == SIM_MEM_HOST) {
+                VX_CK(ctx->d_in_u8.ensure(V));
+                VX_CK(ctx->d_in_f32.ensure(V)); VX_CK(ctx->d_in_f32b.ensure(V)); VX_CK(ctx->d_in_f32c.ensure(V));
+                if (sim_status st = copy_in(m, V, mem, ctx->d_in_u8.p, s)) return st;
+                if (sim_status st = copy_in(w, 4 * V, mem, ctx->d_in_f32.p, s)) return st;
+                if (sim_status st = copy_in(k, 4 * V, mem, ctx->d_in_f32b.p, s)) return st;
+                if (sim_status st = copy_in(ph, 4 * V, mem, ctx->d_in_f32c.p, s)) return st;
+                m = ctx->d_in_u8.p; w = ctx->d_in_f32.p; k = ctx->d_in_f32b.p; ph = ctx->d_in_f32c.p;
+            }
+            VX_LAUNCH(ctx, launch_decode_params(m, w, k, ph, V, ctx->d_mat_raw.p, ctx->d_w.p, ctx->d_kappa.p,
+                                       ctx->d_phi.p, ctx->d_status.p, s));
+        } else {
+            const int Q = d[0] * d[1] * d[2];
+            const float* gsrc = (const float*)genomes;
+            const float* bsrc = B;
+            if (mem == SIM_MEM_HOST) {
+                VX_CK(ctx->d_in_f32.ensure((size_t)P * kGenome));
+                VX_CK(ctx->d_in_f32b.ensure(kPeRows * 3));
+                if (sim_status st = copy_in(genomes, sizeof(float) * (size_t)P * kGenome, mem, ctx->d_in_f32.p, s)) return st;
+                if (sim_status st = copy_in(B, sizeof(float) * kPeRows * 3, mem, ctx->d_in_f32b.p, s)) return st;
+                gsrc = ctx->d_in_f32.p;
+                bsrc = ctx->d_in_f32b.p;
+            }
+            VX_CK(ctx->d_pe.ensure((size_t)Q * kPeDim * 2));
+            VX_LAUNCH(ctx, launch_pe_table(d[0], d[1], d[2], bsrc, ctx->d_pe.p, s));
+            VX_LAUNCH(ctx, launch_mlp_query_simt(P, Q, ctx->d_pe.p, gsrc, mc, ctx->d_mat_raw.p, ctx->d_w.p,
+                                        ctx->d_kappa.p, ctx->d_phi.p, s));
+        }
+        // topology
+        VX_LAUNCH(ctx, launch_topology(ctx->view(), ctx->d_mat_raw.p, ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p,
+                              ctx->d_phi.p, mc, ctx->p.edge, ctx->d_label.p, ctx->d_count.p,
+                              ctx->d_corner_mass.p, ctx->d_mass_corner.p, ctx->d_sab.p, ctx->d_sp.p,
+                              packed ? ctx->d_spack.p : nullptr, ctx->d_x.p, ctx->d_v.p,
+                              ctx->d_x0c.p, ctx->d_status.p, 0, s));
+        // longest-first processing order (by spring count, ties by index)
+        k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
+        VX_LAUNCH(ctx, cudaGetLastError());
+        VX_LAUNCH(ctx, launch_evo_rank(ctx->d_keys.p, P, ctx->d_lpt.p, s));
+    }
+    ctx->step = 0;
+    ctx->have_pop = true;
+    return SIM_OK;
+}
+
+// Next free event pair of the timing pool (grown on demand).
+static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
+{
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t e;
+        VX_CK(cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    ev[0] = ctx->ev_pool[ctx->ev_used];
+    ev[1] = ctx->ev_pool[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+    return SIM_OK;
+}
+
+static sim_status step_resident(voxsim_ctx* ctx, int n)
+{
+    cudaStream_t s = ctx->stream;
+    ResidentArgs a{};
+    a.pv = ctx->view();
+    a.spr_pack = ctx->d_spack.p;
+    a.x = ctx->d_x.p;
+    a.v = ctx->d_v.p;
+    a.sc = ctx->d_sc.p;
+    a.nsteps = n;
+    a.c = ctx->stepconst();
+    a.order = ctx->d_lpt.p;
+    a.queue = ctx->d_queue.p;
+    a.accumulate = SIM_ACC_ATOMIC;
+    // launch shape: threads per robot and blocks per SM from the largest robot's capacity
+    int threads = ctx->p.threads;
+    const int64_t sc = ctx->max_spring_cap;
+    if (threads <= 0) threads = sc <= 1536 ? 256 : (sc <= 6144 ? 512 : 1024);
+    threads = std::max(32, std::min(1024, (threads + 31) / 32 * 32));
+    const size_t mass_bytes = resident_smem_bytes(ctx->max_corner, 0, a.accumulate);
+    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    if (mass_bytes > budget) return fail(SIM_EINVAL, "robot too large for the resident path");
+    int64_t spr_fit = (int64_t)((budget - mass_bytes) / sizeof(float4));
+    // several blocks per SM when everything of the largest robot fits in a fraction of it
+    int per_sm = 1;
+    const size_t need = mass_bytes + sizeof(float4) * (size_t)sc;
+    while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin &&
+           threads * (per_sm + 1) <= 2048)
+        ++per_sm;
+    if (per_sm > 1) spr_fit = sc;
+    a.max_mass = ctx->max_corner;
+    a.max_spring_smem = (int)std::min<int64_t>(sc, spr_fit);
+    const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
+    int grid = std::min<int64_t>(ctx->P, (int64_t)ctx->num_sms * per_sm);
+    if (grid < 1) grid = 1;
+    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+    VX_LAUNCH(ctx, launch_step_resident(a, grid, threads, smem, s));
+    return SIM_OK;
+}
+
+sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    if (n_steps < 0) return fail(SIM_EINVAL, "n_steps must be >= 0");
+    if (n_steps == 0 || ctx->P == 0) return SIM_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_sc.ensure(n_steps));
+    VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->step, n_steps,
+                              ctx->d_sc.p, s));
+    if (ctx->max_corner > kResidentMaxMass || ctx->p.path == SIM_PATH_STREAMED)
+        return fail(SIM_EINVAL, "streamed path not available for this population");
+    cudaEvent_t ev[2];
+    if (sim_status st = timing_pair(ctx, ev)) return st;
+    VX_CK(cudaEventRecord(ev[0], s));
+    if (sim_status st = step_resident(ctx, n_steps)) return st;
+    VX_CK(cudaEventRecord(ev[1], s));
+    ctx->step += n_steps;
+    return SIM_OK;
+}
+
+sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    if (ctx->P > 0 && !out) return fail(SIM_EINVAL, "null output");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    double* dst = mem == SIM_MEM_DEVICE ? out : ctx->d_fit.p;
+    VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_x.p, ctx->d_x0c.p, (float)ctx->p.dead_bound, dst, s));
+    if (mem == SIM_MEM_HOST) return copy_out(out, ctx->d_fit.p, sizeof(double) * ctx->P, mem, s);
+    return SIM_OK;
+}
+
+sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* genomes_in,
+                          float* genomes_out, int32_t P, int32_t G, const evo_params* e,
+                          uint64_t generation, int32_t* parents_out, uint8_t* mask_out)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!e || !fitness || !genomes_in || !genomes_out) return fail(SIM_EINVAL, "null argument");
+    if (P < 1 || P > 65535) return fail(SIM_EINVAL, "P must be in 1..65535");
+    if (G < 1 || G > (1 << 26)) return fail(SIM_EINVAL, "G must be in 1..2^26");
+    if (e->elites < 1 || e->elites > P) return fail(SIM_EINVAL, "elites must be in 1..P");
+    if (generation >= (1ull << 19)) return fail(SIM_EINVAL, "generation must be < 2^19");
+    if (!(e->sigma >= 0.f)) return fail(SIM_EINVAL, "sigma must be >= 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_order.ensure(P));
+    const float* src = genomes_in;
+    const size_t n = (size_t)P * G;
+    const float* lo_in = genomes_in; const float* hi_in = genomes_in + n;
+    const float* lo_out = genomes_out; const float* hi_out = genomes_out + n;
+    if (lo_in < hi_out && lo_out < hi_in) {   // overlapping: read from a copy
+        VX_CK(ctx->d_gcopy.ensure(n));
+        VX_CK(cudaMemcpyAsync(ctx->d_gcopy.p, genomes_in, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        src = ctx->d_gcopy.p;
+    }
+    VX_LAUNCH(ctx, launch_evo_rank(fitness, P, ctx->d_order.p, s));
+    VX_LAUNCH(ctx, launch_evo_children(src, genomes_out, ctx->d_order.p, P, G, e->elites, e->seed, generation,
+                              e->mut_threshold, e->sigma, parents_out, mask_out, s));
+    return SIM_OK;
+}
+
+sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (k_steps < 0) return fail(SIM_EINVAL, "k_steps must be >= 0");
+    return fail(SIM_ESTATE, "checkpointing is not available in this build");
+}
+
+sim_status sim_backward(voxsim_ctx* ctx, const double*, float*, float*, float*)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    return fail(SIM_ESTATE, "no recorded forward run");
+}
+
+sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    if (n_masses && ctx->P) VX_CK(cudaMemcpyAsync(n_masses, ctx->d_nm.p, 4 * ctx->P, cudaMemcpyDeviceToHost, s));
+    if (n_springs && ctx->P) VX_CK(cudaMemcpyAsync(n_springs, ctx->d_ns.p, 4 * ctx->P, cudaMemcpyDeviceToHost, s));
+    VX_CK(cudaStreamSynchronize(s));
+    return SIM_OK;
+}
+
+sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* mass_offsets, int32_t mem)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int P = ctx->P;
+    std::vector<int32_t> nm(P);
+    if (sim_status st = sim_get_counts(ctx, nm.data(), nullptr)) return st;
+    std::vector<int64_t> off(P + 1, 0);
+    for (int r = 0; r < P; ++r) off[r + 1] = off[r] + nm[r];
+    if (mass_offsets)
+        for (int r = 0; r <= P; ++r) mass_offsets[r] = (int32_t)off[r];
+    const int64_t Mt = off[P];
+    if (P == 0 || Mt == 0) return SIM_OK;
+    VX_CK(cudaMemcpyAsync(ctx->d_tmp_off.p, off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
+    VX_CK(ctx->d_compact.ensure(3 * (size_t)Mt));
+    float* outs[2] = {x_out, v_out};
+    const float4* srcs[2] = {ctx->d_x.p, ctx->d_v.p};
+    for (int i = 0; i < 2; ++i) {
+        if (!outs[i]) continue;
+        float* dst = mem == SIM_MEM_DEVICE ? outs[i] : ctx->d_compact.p;
+        VX_LAUNCH(ctx, launch_compact_state(ctx->view(), srcs[i], dst, ctx->d_tmp_off.p, s));
+        if (mem == SIM_MEM_HOST)
+            if (sim_status st = copy_out(outs[i], ctx->d_compact.p, sizeof(float) * 3 * Mt, mem, s)) return st;
+    }
+    VX_CK(cudaStreamSynchronize(s));
+    return SIM_OK;
+}
+
+sim_status sim_get_voxels(voxsim_ctx* ctx, uint8_t* mat_decoded, uint8_t* mat_kept, float* w,
+                          float* kappa, float* phi)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const size_t V = ctx->V_tot;
+    if (mat_decoded) if (sim_status st = copy_out(mat_decoded, ctx->d_mat_raw.p, V, SIM_MEM_HOST, s)) return st;
+    if (mat_kept) if (sim_status st = copy_out(mat_kept, ctx->d_mat.p, V, SIM_MEM_HOST, s)) return st;
+    if (w) if (sim_status st = copy_out(w, ctx->d_w.p, 4 * V, SIM_MEM_HOST, s)) return st;
+    if (kappa) if (sim_status st = copy_out(kappa, ctx->d_kappa.p, 4 * V, SIM_MEM_HOST, s)) return st;
+    if (phi) if (sim_status st = copy_out(phi, ctx->d_phi.p, 4 * V, SIM_MEM_HOST, s)) return st;
+    return SIM_OK;
+}
+
+sim_status sim_get_topology(voxsim_ctx* ctx, int32_t* mass_corner, int32_t* spring_ab, float* spring_params)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int P = ctx->P;
+    std::vector<int32_t> nm(P), ns(P);
+    if (sim_status st = sim_get_counts(ctx, nm.data(), ns.data())) return st;
+    if (mass_corner) {
+        std::vector<int32_t> all(ctx->M_cap);
+        if (sim_status st = copy_out(all.data(), ctx->d_mass_corner.p, 4 * ctx->M_cap, SIM_MEM_HOST, s)) return st;
+        int64_t o = 0;
+        for (int r = 0; r < P; ++r) {
+            std::memcpy(mass_corner + o, all.data() + ctx->moff[r], 4 * (size_t)nm[r]);
+            o += nm[r];
+        }
+    }
+    if (spring_ab || spring_params) {
+        std::vector<int2> ab(ctx->S_cap);
+        std::vector<float4> sp(ctx->S_cap);
+        if (sim_status st = copy_out(ab.data(), ctx->d_sab.p, sizeof(int2) * ctx->S_cap, SIM_MEM_HOST, s)) return st;
+        if (sim_status st = copy_out(sp.data(), ctx->d_sp.p, sizeof(float4) * ctx->S_cap, SIM_MEM_HOST, s)) return st;
+        int64_t o = 0;
+        for (int r = 0; r < P; ++r) {
+            for (int i = 0; i < ns[r]; ++i) {
+                const int2 q = ab[ctx->soff[r] + i];
+                const float4 t = sp[ctx->soff[r] + i];
+                if (spring_ab) { spring_ab[2 * (o + i)] = q.x; spring_ab[2 * (o + i) + 1] = q.y; }
+                if (spring_params) {
+                    float* dst = spring_params + 4 * (o + i);
+                    dst[0] = t.x; dst[1] = t.y; dst[2] = t.z; dst[3] = t.w;
+                }
+            }
+            o += ns[r];
+        }
+    }
+    return SIM_OK;
+}
+
+sim_status sim_get_timing(voxsim_ctx* ctx, double* step_ms, int64_t* launches)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    DeviceGuard g(ctx->device);
+    VX_CK(cudaStreamSynchronize(ctx->stream));
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float ms = 0.f;
+        VX_CK(cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+        total += ms;
+    }
+    if (step_ms) *step_ms = total;
+    if (launches) *launches = ctx->launches;
+    ctx->ev_used = 0;
+    ctx->launches = 0;
+    return SIM_OK;
+}
+
+}  // extern "C"

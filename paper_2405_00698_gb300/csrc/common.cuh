@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of the voxsim library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/voxsim.h"
+
+namespace vx {
+
+// ----------------------------------------------------------------------------------------------
+// Constants
+// ----------------------------------------------------------------------------------------------
+constexpr int kNumMat = 5;
+constexpr int kGenome = 20998;       // MLP 3 -> gamma(256) -> 64 -> 64 -> 6
+constexpr int kPeRows = 128;         // m of Eq. (1)
+constexpr int kPeDim = 256;          // 2m
+constexpr int kHidden = 64;
+constexpr int kOut = 6;
+constexpr int kOffW1 = 0, kOffB1 = 16384, kOffW2 = 16448, kOffB2 = 20544, kOffW3 = 20608,
+              kOffB3 = 20992;
+constexpr int kMaxAxis = 64;          // largest grid extent per axis
+constexpr int kResidentMaxMass = 32767;  // packed 15-bit mass indices on the resident path
+
+// Per-material constants in float, passed by value to kernels.
+struct MatConst {
+    float k[kNumMat];
+    float amp[kNumMat];
+    float phase[kNumMat];
+};
+
+// Physics constants in float for the step kernels.
+struct StepConst {
+    float dt;
+    float dt_over_m;    // dt / mass
+    float weight;       // mass * gravity
+    float damping;
+    float k_ground;
+    float mu_s;
+    float mu_k;
+    float edge;
+    float edge_sqrt2;
+    float edge_sqrt3;
+    int ground_on;
+};
+
+// Device view of a population's layout.
+struct PopView {
+    int P;
+    const int* dims;         // [3P]
+    const int64_t* voff;     // [P+1] voxel offsets
+    const int64_t* moff;     // [P+1] mass (= corner) capacity offsets
+    const int64_t* soff;     // [P+1] spring capacity offsets
+    int* n_mass;             // [P]
+    int* n_spring;           // [P]
+};
+
+// ----------------------------------------------------------------------------------------------
+// Kernel launchers (each returns the launch error, if any)
+// ----------------------------------------------------------------------------------------------
+cudaError_t launch_decode_materials(const uint8_t* mats, int64_t n, MatConst mc, uint8_t* mat,
+                                    float* w, float* kappa, float* phi, int* bad, cudaStream_t s);
+cudaError_t launch_decode_logits(const float* logits, int64_t n, MatConst mc, uint8_t* mat,
+                                 float* w, float* kappa, float* phi, cudaStream_t s);
+cudaError_t launch_decode_params(const uint8_t* mats, const float* w_in, const float* k_in,
+                                 const float* p_in, int64_t n, uint8_t* mat, float* w,
+                                 float* kappa, float* phi, int* bad, cudaStream_t s);
+cudaError_t launch_pe_table(int nx, int ny, int nz, const float* B, void* pe_bf16,
+                            cudaStream_t s);
+cudaError_t launch_mlp_query(int P, int Q, const void* pe_bf16, const float* genomes, MatConst mc,
+                             uint8_t* mat, float* w, float* kappa, float* phi, cudaStream_t s);
+cudaError_t launch_mlp_query_simt(int P, int Q, const void* pe_bf16, const float* genomes,
+                                  MatConst mc, uint8_t* mat, float* w, float* kappa, float* phi,
+                                  cudaStream_t s);
+
+cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, const float* w,
+                            const float* kappa, const float* phi, MatConst mc, double edge,
+                            int* label, int* count, int* corner_mass, int* mass_corner,
+                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x, float4* v,
+                            double* x0c, int* status, int max_threads, cudaStream_t s);
+
+cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, float2* out,
+                                cudaStream_t s);
+
+struct ResidentArgs {
+    PopView pv;
+    const float4* spr_pack;  // packed springs (k, alpha*L0, beta*L0, a | b<<15 | cls<<30)
+    float4* x;
+    float4* v;
+    const float2* sc;        // sin / cos of w t per step of this call
+    int nsteps;
+    StepConst c;
+    const int* order;        // robot processing order (longest first) or NULL
+    int* queue;              // work counter (zeroed by the launcher) or NULL for static split
+    int max_mass;            // smem layout: masses per robot slot
+    int max_spring_smem;     // springs cached in shared memory per robot
+    int accumulate;          // SIM_ACC_ATOMIC or SIM_ACC_GATHER
+    // gather path
+    const int* inc_off;      // [moff-based] per-mass incidence start (length M+1 per robot)
+    const int* inc_list;     // [soff*2-based] spring index * 2 + side
+};
+cudaError_t launch_step_resident(const ResidentArgs& a, int grid, int threads, size_t smem,
+                                 cudaStream_t s);
+size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);
+
+cudaError_t launch_fitness(PopView pv, const float4* x, const double* x0c, float dead_bound,
+                           double* out, cudaStream_t s);
+
+cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s);
+cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
+                                int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
+                                int* parents, uint8_t* mask, cudaStream_t s);
+
+cudaError_t launch_compact_state(PopView pv, const float4* src, float* dst,
+                                 const int64_t* dst_off, cudaStream_t s);
+
+}  // namespace vx

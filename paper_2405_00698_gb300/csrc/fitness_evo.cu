@@ -1,0 +1,218 @@
+// Fitness reduction and the evolutionary step, fully on the GPU (Section II-C: "crossover,
+// mutation and elite selection ... fully parallel"; Table I).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace vx {
+namespace {
+
+// ----------------------------------------------------------------------------------------------
+// Fitness: centroid x displacement, FP64 warp-shuffle block reduction, one block per robot.
+// ----------------------------------------------------------------------------------------------
+constexpr int kFitThreads = 256;
+
+__global__ void __launch_bounds__(kFitThreads)
+k_fitness(PopView pv, const float4* __restrict__ x, const double* __restrict__ x0c,
+          float dead_bound, double* __restrict__ out)
+{
+    __shared__ double sh_sum[kFitThreads / 32];
+    __shared__ int sh_dead;
+    const int r = blockIdx.x;
+    const int M = pv.n_mass[r];
+    const int64_t mo = pv.moff[r];
+    if (threadIdx.x == 0) sh_dead = 0;
+    __syncthreads();
+    double s = 0.0;
+    int dead = 0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 p = x[mo + m];
+        if (!(fabsf(p.x) <= dead_bound) || !(fabsf(p.y) <= dead_bound) || !(fabsf(p.z) <= dead_bound))
+            dead = 1;   // catches NaN too
+        s += (double)p.x;
+    }
+    if (dead) sh_dead = 1;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh_sum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kFitThreads / 32; ++i) t += sh_sum[i];
+        double f;
+        if (M == 0) f = 0.0;
+        else if (sh_dead) f = -INFINITY;
+        else f = t / M - x0c[r];
+        out[r] = f;
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Counter-based random numbers: SplitMix64 (Steele, Lea and Flood, OOPSLA 2014).  Output
+// number `ctr` of the stream seeded with `seed` is the SplitMix64 finaliser applied to
+// seed + (ctr + 1) * golden-gamma.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr)
+{
+    uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+enum { kParentA = 0, kParentB = 1, kMask = 2, kMutate = 3, kU1 = 4, kU2 = 5 };
+
+// High 32 bits of the draw for (generation, child, gene, purpose), fields packed as
+// generation | child (16 bits) | gene (26 bits) | purpose (3 bits).
+__device__ __forceinline__ uint32_t draw32(uint64_t seed, uint64_t gen, uint32_t child,
+                                           uint32_t gene, uint32_t purpose)
+{
+    const uint64_t ctr = ((((gen << 16) | child) << 26 | gene) << 3) | purpose;
+    return (uint32_t)(splitmix64_at(seed, ctr) >> 32);
+}
+
+// Rank by counting: the rank of robot i is the number of robots ordered before it
+// (larger fitness, or equal fitness and smaller index; NaN counts as -infinity).
+__global__ void k_rank(const double* __restrict__ f, int P, int* __restrict__ order)
+{
+    extern __shared__ double tile[];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double fi = -INFINITY;
+    if (i < P) { fi = f[i]; if (isnan(fi)) fi = -INFINITY; }
+    int rank = 0;
+    for (int base = 0; base < P; base += blockDim.x) {
+        __syncthreads();
+        const int j = base + threadIdx.x;
+        double fj = -INFINITY;
+        if (j < P) { fj = f[j]; if (isnan(fj)) fj = -INFINITY; }
+        tile[threadIdx.x] = fj;
+        __syncthreads();
+        const int n = min((int)blockDim.x, P - base);
+        if (i < P)
+            for (int t = 0; t < n; ++t) {
+                const double g = tile[t];
+                const int jj = base + t;
+                rank += (g > fi) || (g == fi && jj < i);
+            }
+    }
+    if (i < P) order[rank] = i;
+}
+
+// One thread per (child row, gene).  Elite rows copy their genome; child rows pick parents,
+// crossover mask and mutation from the counter-based generator.
+__global__ void k_children(const float* __restrict__ gin, float* __restrict__ gout,
+                           const int* __restrict__ order, int P, int G, int E, uint64_t seed,
+                           uint64_t gen, uint32_t thresh, float sigma, int* __restrict__ parents,
+                           uint8_t* __restrict__ mask)
+{
+    const int c = blockIdx.y;
+    const size_t row = (size_t)c * G;
+    if (c < E) {
+        const float* src = gin + (size_t)order[c] * G;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G; j += gridDim.x * blockDim.x) {
+            gout[row + j] = src[j];
+            if (mask) mask[row + j] = 0;
+        }
+        if (parents && blockIdx.x == 0 && threadIdx.x == 0) {
+            parents[2 * c] = order[c];
+            parents[2 * c + 1] = order[c];
+        }
+        return;
+    }
+    const uint32_t ua = draw32(seed, gen, c, 0, kParentA);
+    const uint32_t ub = draw32(seed, gen, c, 0, kParentB);
+    const int pa = order[(int)(((uint64_t)ua * (uint64_t)E) >> 32)];
+    const int pb = order[(int)(((uint64_t)ub * (uint64_t)E) >> 32)];
+    if (parents && blockIdx.x == 0 && threadIdx.x == 0) {
+        parents[2 * c] = pa;
+        parents[2 * c + 1] = pb;
+    }
+    const float* A = gin + (size_t)pa * G;
+    const float* Bp = gin + (size_t)pb * G;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G; j += gridDim.x * blockDim.x) {
+        const uint32_t m = draw32(seed, gen, c, j, kMask) >> 31;
+        float g = m ? A[j] : Bp[j];
+        if (draw32(seed, gen, c, j, kMutate) < thresh) {
+            const float u1 = ((float)draw32(seed, gen, c, j, kU1) + 1.0f) * 2.3283064365386963e-10f;
+            const float u2 = (float)draw32(seed, gen, c, j, kU2) * 2.3283064365386963e-10f;
+            const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            g = g + sigma * z;
+        }
+        gout[row + j] = g;
+        if (mask) mask[row + j] = (uint8_t)m;
+    }
+}
+
+// sin and cos of w t for the steps of one call, FP64 then rounded to float:
+// phase = (2 pi freq) (step dt), evaluated in that order.
+__global__ void k_sincos(double omega, double dt, int64_t step0, int n, float2* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double t = __dmul_rn((double)(step0 + i), dt);
+    const double ph = __dmul_rn(omega, t);
+    double s, c;
+    sincos(ph, &s, &c);
+    out[i] = make_float2((float)s, (float)c);
+}
+
+__global__ void k_compact(PopView pv, const float4* __restrict__ src, float* __restrict__ dst,
+                          const int64_t* __restrict__ dst_off)
+{
+    const int r = blockIdx.x;
+    const int M = pv.n_mass[r];
+    const int64_t mo = pv.moff[r], d = dst_off[r];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 p = src[mo + m];
+        dst[3 * (d + m) + 0] = p.x;
+        dst[3 * (d + m) + 1] = p.y;
+        dst[3 * (d + m) + 2] = p.z;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fitness(PopView pv, const float4* x, const double* x0c, float dead_bound,
+                           double* out, cudaStream_t s)
+{
+    if (pv.P == 0) return cudaSuccess;
+    k_fitness<<<pv.P, kFitThreads, 0, s>>>(pv, x, x0c, dead_bound, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s)
+{
+    const int T = 256;
+    k_rank<<<(P + T - 1) / T, T, T * sizeof(double), s>>>(fitness, P, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
+                                int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
+                                int* parents, uint8_t* mask, cudaStream_t s)
+{
+    const int T = 256;
+    int bx = (G + T - 1) / T;
+    if (bx > 64) bx = 64;
+    dim3 grid(bx, P);
+    k_children<<<grid, T, 0, s>>>(gin, gout, order, P, G, E, seed, gen, thresh, sigma, parents,
+                                  mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, float2* out,
+                                cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_sincos<<<(n + 255) / 256, 256, 0, s>>>(omega, dt, step0, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_state(PopView pv, const float4* src, float* dst, const int64_t* dst_off,
+                                 cudaStream_t s)
+{
+    if (pv.P == 0) return cudaSuccess;
+    k_compact<<<pv.P, 256, 0, s>>>(pv, src, dst, dst_off);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

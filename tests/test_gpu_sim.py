@@ -1,0 +1,220 @@
+"""GPU vs oracle parity of decode, largest component, topology, time stepping and fitness.
+
+Tolerances: integer work (materials, kept voxels, mass corners, spring endpoints, counts) is
+bit-exact; positions after the run within 1e-4 of the robot size s * max(n) (max-norm), fitness
+within 1e-3 relative with a floor of 1e-3 * s; spring parameters within float32 rounding."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2405_00698_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PHYS = W.CONFIG
+POS_TOL = 1e-4
+FIT_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def vs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00698_gb300 import build
+    build.build()
+    from paper_2405_00698_gb300 import voxsim
+    return voxsim
+
+
+def rel_pos_err(pop, x_gpu, off, x_ref, edge):
+    worst = 0.0
+    for r in range(pop.P):
+        xg = x_gpu[off[r]:off[r + 1]].astype(np.float64)
+        xr = x_ref[r]
+        if xr.size == 0:
+            continue
+        scale = edge * float(pop.dims[r].max())
+        worst = max(worst, float(np.abs(xg - xr).max()) / scale)
+    return worst
+
+
+def rel_fit_err(f, fr, edge):
+    f, fr = np.asarray(f), np.asarray(fr)
+    same_inf = np.isinf(f) & np.isinf(fr) & (np.sign(f) == np.sign(fr))
+    err = np.abs(f - fr) / np.maximum(np.abs(fr), 1e-3 * edge)
+    err[same_inf] = 0.0
+    return float(err.max()) if err.size else 0.0
+
+
+def run_both(vs, orc, pop, phys, nsteps, **kw):
+    sim = vs.Simulator(phys, **kw)
+    sim.set_population_from(pop)
+    sim.step(nsteps)
+    f = sim.fitness()
+    x, v, off = sim.state()
+    M, S = sim.counts()
+    ref = orc.run_population(pop, phys, nsteps, want_x=True)
+    sim.close()
+    return dict(f=f, x=x, off=off, M=M, S=S), ref
+
+
+def test_small_workload_1000_steps(vs, orc):
+    """16 robots, 4x4x4, materials uniform over the five ids, 1000 steps."""
+    pop = W.workload_small(seed=0)
+    g, ref = run_both(vs, orc, pop, PHYS, 1000)
+    assert np.array_equal(g["M"], ref["M"]) and np.array_equal(g["S"], ref["S"])
+    assert rel_pos_err(pop, g["x"], g["off"], ref["x"], PHYS.edge) < POS_TOL
+    assert rel_fit_err(g["f"], ref["fitness"], PHYS.edge) < FIT_TOL
+
+
+def test_topology_bit_exact(vs, orc):
+    pop = W.population_uneven(24, seed=21, sizes=(1, 2, 3, 5, 7, 9))
+    sim = vs.Simulator(PHYS)
+    sim.set_population_from(pop)
+    vox = sim.voxels()
+    topo = sim.topology()
+    mo = so = 0
+    for r in range(pop.P):
+        R = orc.Robot(pop.grid(r), pop.dims[r], PHYS)
+        t = R.topology()
+        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+        assert np.array_equal(vox["kept"][a:b], t["kept"]), r
+        assert topo["M"][r] == R.M and topo["S"][r] == R.S, r
+        assert np.array_equal(topo["mass_corner"][mo:mo + R.M], t["mass_corner"]), r
+        ab = topo["ab"][so:so + R.S]
+        assert np.array_equal(ab[:, 0], t["a"]) and np.array_equal(ab[:, 1], t["b"]), r
+        sp = topo["params"][so:so + R.S].astype(np.float64)
+        assert np.allclose(sp[:, 0], t["L0"], rtol=1e-6)
+        assert np.allclose(sp[:, 1], t["k"], rtol=1e-6)
+        assert np.allclose(sp[:, 2], t["alpha"], atol=1e-6)
+        assert np.allclose(sp[:, 3], t["beta"], atol=1e-6)
+        mo += R.M
+        so += R.S
+    sim.close()
+
+
+def test_uneven_population_ragged_sizes(vs, orc):
+    """Grids from 1 to 12 voxels per axis, several tiles and ragged tails of threads."""
+    pop = W.population_uneven(40, seed=22, sizes=(1, 3, 4, 6, 8, 12))
+    g, ref = run_both(vs, orc, pop, PHYS, 400)
+    assert np.array_equal(g["S"], ref["S"])
+    assert rel_pos_err(pop, g["x"], g["off"], ref["x"], PHYS.edge) < POS_TOL
+    assert rel_fit_err(g["f"], ref["fitness"], PHYS.edge) < FIT_TOL
+
+
+@pytest.mark.parametrize("threads", [32, 96, 256, 1024])
+def test_thread_counts_agree(vs, orc, threads):
+    pop = W.population_uneven(8, seed=23, sizes=(4, 8, 12))
+    g, ref = run_both(vs, orc, pop, PHYS, 300, threads=threads)
+    assert rel_pos_err(pop, g["x"], g["off"], ref["x"], PHYS.edge) < POS_TOL
+
+
+def test_empty_and_degenerate_robots(vs, orc):
+    grids = [np.zeros((2, 2, 2), np.uint8),              # empty: no masses, fitness 0
+             np.full((1, 1, 1), 4, np.uint8),            # one voxel
+             np.array([[[1, 0, 2]]], np.uint8),          # two components of equal size
+             np.full((1, 1, 12), 3, np.uint8)]           # a rod
+    pop = W.make_population([g.shape[::-1] for g in grids], grids)
+    g, ref = run_both(vs, orc, pop, PHYS, 500)
+    assert list(g["M"]) == list(ref["M"]) and g["M"][0] == 0
+    assert g["f"][0] == 0.0
+    assert rel_pos_err(pop, g["x"], g["off"], ref["x"], PHYS.edge) < POS_TOL
+    assert rel_fit_err(g["f"], ref["fitness"], PHYS.edge) < FIT_TOL
+
+
+def test_split_calls_continue_time(vs, orc):
+    """step(300) + step(700) equals step(1000): the actuation clock runs across calls."""
+    pop = W.workload_small(seed=3).subset(range(6))
+    sim = vs.Simulator(PHYS)
+    sim.set_population_from(pop)
+    sim.step(300)
+    sim.step(700)
+    x, _, off = sim.state()
+    ref = orc.run_population(pop, PHYS, 1000, want_x=True)
+    assert rel_pos_err(pop, x, off, ref["x"], PHYS.edge) < POS_TOL
+    sim.close()
+
+
+def test_no_ground_conserves_centroid(vs):
+    phys = dataclasses.replace(PHYS, gravity=0.0, ground_on=False, damping=1.0)
+    pop = W.workload_small(seed=4)
+    sim = vs.Simulator(phys)
+    sim.set_population_from(pop)
+    sim.step(1000)
+    assert np.abs(sim.fitness()).max() < 1e-5
+    sim.close()
+
+
+def test_dead_robot_scores_minus_infinity(vs, orc):
+    phys = dataclasses.replace(PHYS, dt=2e-2)      # far beyond the stability limit
+    pop = W.workload_small(seed=5).subset(range(3))
+    sim = vs.Simulator(phys)
+    sim.set_population_from(pop)
+    sim.step(200)
+    f = sim.fitness()
+    ref = orc.run_population(pop, phys, 200)
+    assert np.all(np.isneginf(f)) and np.all(np.isneginf(ref["fitness"]))
+    sim.close()
+
+
+def test_logits_mode(vs, orc):
+    rng = np.random.default_rng(31)
+    pop = W.population_uniform(6, (5, 4, 3), seed=31)
+    logits = rng.standard_normal((pop.mats.size, 5)).astype(np.float32)
+    logits[::7, 2] = logits[::7, 1]                  # exact ties go to the lower id
+    sim = vs.Simulator(PHYS)
+    sim.set_population(pop.dims, logits, vs.MODE_LOGITS)
+    vox = sim.voxels()
+    assert np.array_equal(vox["decoded"], np.argmax(logits, axis=1).astype(np.uint8))
+    sim.step(300)
+    f = sim.fitness()
+    ref_pop = W.make_population(pop.dims, [vox["decoded"][pop.voxel_off[r]:pop.voxel_off[r + 1]]
+                                           for r in range(pop.P)])
+    ref = orc.run_population(ref_pop, PHYS, 300)
+    assert rel_fit_err(f, ref["fitness"], PHYS.edge) < FIT_TOL
+    sim.close()
+
+
+def test_params_mode(vs, orc):
+    rng = np.random.default_rng(32)
+    pop = W.population_uniform(5, (4, 4, 4), seed=32)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    sim = vs.Simulator(PHYS)
+    sim.set_population(pop.dims, (pop.mats, w, kappa, phi), vs.MODE_PARAMS)
+    sim.step(800)
+    f = sim.fitness()
+    x, _, off = sim.state()
+    ref = orc.run_population(pop, PHYS, 800, w=w, kappa=kappa, phi=phi, want_x=True)
+    assert rel_pos_err(pop, x, off, ref["x"], PHYS.edge) < POS_TOL
+    assert rel_fit_err(f, ref["fitness"], PHYS.edge) < FIT_TOL
+    sim.close()
+
+
+def test_device_inputs(vs, orc):
+    import torch
+    pop = W.workload_small(seed=6).subset(range(5))
+    sim = vs.Simulator(PHYS)
+    sim.set_population(pop.dims, torch.from_numpy(pop.mats).cuda(), vs.MODE_MATERIALS)
+    sim.step(200)
+    out = torch.empty(pop.P, dtype=torch.float64, device="cuda")
+    sim.fitness(out)
+    torch.cuda.synchronize()
+    ref = orc.run_population(pop, PHYS, 200)
+    assert rel_fit_err(out.cpu().numpy(), ref["fitness"], PHYS.edge) < FIT_TOL
+    sim.close()
+
+
+def test_invalid_inputs_rejected(vs):
+    sim = vs.Simulator(PHYS)
+    with pytest.raises(vs.VoxsimError):
+        sim.step(10)                                   # no population yet
+    bad = np.full(8, 9, np.uint8)
+    with pytest.raises(vs.VoxsimError):
+        sim.set_population([[2, 2, 2]], bad)
+    with pytest.raises(vs.VoxsimError):
+        sim.set_population([[0, 2, 2]], np.zeros(0, np.uint8))
+    with pytest.raises(vs.VoxsimError):
+        sim.set_population([[65, 1, 1]], np.zeros(65, np.uint8))
+    sim.close()
