@@ -119,7 +119,7 @@ struct voxsim_ctx {
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
     DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
     DevBuf<int2> d_sab;
-    DevBuf<float4> d_sp, d_spack, d_x, d_v;
+    DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v;
     DevBuf<double> d_x0c, d_keys, d_fit;
     DevBuf<float2> d_sc;
     DevBuf<unsigned char> d_pe;
@@ -312,7 +312,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     VX_CK(ctx->d_corner_mass.ensure(Mc)); VX_CK(ctx->d_mass_corner.ensure(Mc));
     VX_CK(ctx->d_sab.ensure(Sc)); VX_CK(ctx->d_sp.ensure(Sc));
     if (packed) VX_CK(ctx->d_spack.ensure(Sc));
-    VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
+    VX_CK(ctx->d_x0.ensure(Mc)); VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
     VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
     ctx->dims = d; ctx->voff = voff; ctx->moff = moff; ctx->soff = soff;
     ctx->P = P; ctx->V_tot = V; ctx->M_cap = Mc; ctx->S_cap = Sc;
@@ -382,7 +382,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         VX_LAUNCH(ctx, launch_topology(ctx->view(), ctx->d_mat_raw.p, ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p,
                               ctx->d_phi.p, mc, ctx->p.edge, ctx->d_label.p, ctx->d_count.p,
                               ctx->d_corner_mass.p, ctx->d_mass_corner.p, ctx->d_sab.p, ctx->d_sp.p,
-                              packed ? ctx->d_spack.p : nullptr, ctx->d_x.p, ctx->d_v.p,
+                              packed ? ctx->d_spack.p : nullptr, ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
                               ctx->d_x0c.p, ctx->d_status.p, 0, s));
         // longest-first processing order (by spring count, ties by index)
         k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
@@ -478,7 +478,7 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem)
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     double* dst = mem == SIM_MEM_DEVICE ? out : ctx->d_fit.p;
-    VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_x.p, ctx->d_x0c.p, (float)ctx->p.dead_bound, dst, s));
+    VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_x.p, ctx->d_x0.p, (float)ctx->p.dead_bound, dst, s));
     if (mem == SIM_MEM_HOST) return copy_out(out, ctx->d_fit.p, sizeof(double) * ctx->P, mem, s);
     return SIM_OK;
 }
@@ -556,10 +556,11 @@ sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* m
     VX_CK(ctx->d_compact.ensure(3 * (size_t)Mt));
     float* outs[2] = {x_out, v_out};
     const float4* srcs[2] = {ctx->d_x.p, ctx->d_v.p};
+    const float4* adds[2] = {ctx->d_x0.p, nullptr};   // position = rest lattice + displacement
     for (int i = 0; i < 2; ++i) {
         if (!outs[i]) continue;
         float* dst = mem == SIM_MEM_DEVICE ? outs[i] : ctx->d_compact.p;
-        VX_LAUNCH(ctx, launch_compact_state(ctx->view(), srcs[i], dst, ctx->d_tmp_off.p, s));
+        VX_LAUNCH(ctx, launch_compact_state(ctx->view(), srcs[i], adds[i], dst, ctx->d_tmp_off.p, s));
         if (mem == SIM_MEM_HOST)
             if (sim_status st = copy_out(outs[i], ctx->d_compact.p, sizeof(float) * 3 * Mt, mem, s)) return st;
     }

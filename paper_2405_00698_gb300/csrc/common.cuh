@@ -24,7 +24,16 @@ constexpr int kOut = 6;
 constexpr int kOffW1 = 0, kOffB1 = 16384, kOffW2 = 16448, kOffB2 = 20544, kOffW3 = 20608,
               kOffB3 = 20992;
 constexpr int kMaxAxis = 64;          // largest grid extent per axis
-constexpr int kResidentMaxMass = 32767;  // packed 15-bit mass indices on the resident path
+constexpr int kResidentMaxMass = 16383;  // packed 14-bit mass indices on the resident path
+
+// The 13 lattice directions (dx, dy, dz) of springs from a corner to a larger corner id, in
+// increasing (dz, dy, dx) order: (1,0,0) (-1,1,0) (0,1,0) (1,1,0) (-1,-1,1) (0,-1,1) (1,-1,1)
+// (-1,0,1) (0,0,1) (1,0,1) (-1,1,1) (0,1,1) (1,1,1).  Component `axis` of direction d, stored
+// as 2-bit fields (value + 1); a packed resident spring stores its direction index.
+__host__ __device__ constexpr int lattice_dir(int d, int axis)
+{
+    return (int)((axis == 0 ? 0x2492492u : (axis == 1 ? 0x2a540a9u : 0x2aaaa55u)) >> (2 * d) & 3u) - 1;
+}
 
 // Per-material constants in float, passed by value to kernels.
 struct MatConst {
@@ -80,16 +89,16 @@ cudaError_t launch_mlp_query_simt(int P, int Q, const void* pe_bf16, const float
 cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, const float* w,
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
-                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x, float4* v,
-                            double* x0c, int* status, int max_threads, cudaStream_t s);
+                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x0, float4* x,
+                            float4* v, double* x0c, int* status, int max_threads, cudaStream_t s);
 
 cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, float2* out,
                                 cudaStream_t s);
 
 struct ResidentArgs {
     PopView pv;
-    const float4* spr_pack;  // packed springs (k, alpha*L0, beta*L0, a | b<<15 | cls<<30)
-    float4* x;
+    const float4* spr_pack;  // packed springs (k, alpha L0, beta L0, a | b << 14 | dir << 28)
+    float4* x;               // displacement from the rest lattice, rest height in .w
     float4* v;
     const float2* sc;        // sin / cos of w t per step of this call
     int nsteps;
@@ -107,7 +116,7 @@ cudaError_t launch_step_resident(const ResidentArgs& a, int grid, int threads, s
                                  cudaStream_t s);
 size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);
 
-cudaError_t launch_fitness(PopView pv, const float4* x, const double* x0c, float dead_bound,
+cudaError_t launch_fitness(PopView pv, const float4* u, const float4* x0, float dead_bound,
                            double* out, cudaStream_t s);
 
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s);
@@ -115,7 +124,7 @@ cudaError_t launch_evo_children(const float* gin, float* gout, const int* order,
                                 int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
                                 int* parents, uint8_t* mask, cudaStream_t s);
 
-cudaError_t launch_compact_state(PopView pv, const float4* src, float* dst,
+cudaError_t launch_compact_state(PopView pv, const float4* src, const float4* add, float* dst,
                                  const int64_t* dst_off, cudaStream_t s);
 
 }  // namespace vx

@@ -9,11 +9,13 @@ namespace {
 
 // ----------------------------------------------------------------------------------------------
 // Fitness: centroid x displacement, FP64 warp-shuffle block reduction, one block per robot.
+// The state is the displacement u from the rest pose, so the centroid displacement is the mean
+// of u_x (u = 0 at the start).
 // ----------------------------------------------------------------------------------------------
 constexpr int kFitThreads = 256;
 
 __global__ void __launch_bounds__(kFitThreads)
-k_fitness(PopView pv, const float4* __restrict__ x, const double* __restrict__ x0c,
+k_fitness(PopView pv, const float4* __restrict__ u, const float4* __restrict__ x0,
           float dead_bound, double* __restrict__ out)
 {
     __shared__ double sh_sum[kFitThreads / 32];
@@ -26,10 +28,11 @@ k_fitness(PopView pv, const float4* __restrict__ x, const double* __restrict__ x
     double s = 0.0;
     int dead = 0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 p = x[mo + m];
-        if (!(fabsf(p.x) <= dead_bound) || !(fabsf(p.y) <= dead_bound) || !(fabsf(p.z) <= dead_bound))
+        const float4 d = u[mo + m], r0 = x0[mo + m];
+        const float px = r0.x + d.x, py = r0.y + d.y, pz = r0.z + d.z;
+        if (!(fabsf(px) <= dead_bound) || !(fabsf(py) <= dead_bound) || !(fabsf(pz) <= dead_bound))
             dead = 1;   // catches NaN too
-        s += (double)p.x;
+        s += (double)d.x;
     }
     if (dead) sh_dead = 1;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -41,7 +44,7 @@ k_fitness(PopView pv, const float4* __restrict__ x, const double* __restrict__ x
         double f;
         if (M == 0) f = 0.0;
         else if (sh_dead) f = -INFINITY;
-        else f = t / M - x0c[r];
+        else f = t / M;
         out[r] = f;
     }
 }
@@ -155,14 +158,20 @@ __global__ void k_sincos(double omega, double dt, int64_t step0, int n, float2* 
     out[i] = make_float2((float)s, (float)c);
 }
 
-__global__ void k_compact(PopView pv, const float4* __restrict__ src, float* __restrict__ dst,
-                          const int64_t* __restrict__ dst_off)
+// Gather a per-mass float4 state into packed float[3] rows; `add` (optional) is added first
+// (rest lattice + displacement = position).
+__global__ void k_compact(PopView pv, const float4* __restrict__ src, const float4* __restrict__ add,
+                          float* __restrict__ dst, const int64_t* __restrict__ dst_off)
 {
     const int r = blockIdx.x;
     const int M = pv.n_mass[r];
     const int64_t mo = pv.moff[r], d = dst_off[r];
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 p = src[mo + m];
+        float4 p = src[mo + m];
+        if (add) {
+            const float4 q = add[mo + m];
+            p.x += q.x; p.y += q.y; p.z += q.z;
+        }
         dst[3 * (d + m) + 0] = p.x;
         dst[3 * (d + m) + 1] = p.y;
         dst[3 * (d + m) + 2] = p.z;
@@ -171,11 +180,11 @@ __global__ void k_compact(PopView pv, const float4* __restrict__ src, float* __r
 
 }  // namespace
 
-cudaError_t launch_fitness(PopView pv, const float4* x, const double* x0c, float dead_bound,
+cudaError_t launch_fitness(PopView pv, const float4* u, const float4* x0, float dead_bound,
                            double* out, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
-    k_fitness<<<pv.P, kFitThreads, 0, s>>>(pv, x, x0c, dead_bound, out);
+    k_fitness<<<pv.P, kFitThreads, 0, s>>>(pv, u, x0, dead_bound, out);
     return cudaGetLastError();
 }
 
@@ -207,11 +216,11 @@ cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, f
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_state(PopView pv, const float4* src, float* dst, const int64_t* dst_off,
-                                 cudaStream_t s)
+cudaError_t launch_compact_state(PopView pv, const float4* src, const float4* add, float* dst,
+                                 const int64_t* dst_off, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
-    k_compact<<<pv.P, 256, 0, s>>>(pv, src, dst, dst_off);
+    k_compact<<<pv.P, 256, 0, s>>>(pv, src, add, dst, dst_off);
     return cudaGetLastError();
 }
 

@@ -1,12 +1,15 @@
 // Resident time stepping (Section II-C: one thread per spring for the force update, one thread
 // per mass for the integration; Table II constants).  One thread block owns one robot at a
 // time and keeps its whole state in shared memory for every step of the call:
-//   positions  float4[M]   (read by the spring phase, written by the mass phase)
-//   velocities float4[M]
-//   forces     float[3][M] (accumulated by the spring phase, consumed and cleared by the
-//                           mass phase)
-//   springs    float4[S]   when they fit (k, alpha L0, beta L0, a | b << 15 | class << 30),
-//                          otherwise streamed from device memory (L2-resident) every step.
+//   u       float4[M]   displacement from the rest lattice (ux, uy, uz) and rest height z0
+//   v       float4[M]   velocity
+//   F       float[3][M] accumulated by the spring phase, consumed and cleared by the mass phase
+//   springs float4[S]   when they fit, otherwise streamed from device memory (L2) every step:
+//                       (k, alpha L0, beta L0, a | b << 14 | direction << 28), ordered by
+//                       direction then a, so a warp's atomic updates hit distinct masses.
+// Keeping the displacement instead of the position keeps float32 precise: a spring vector is
+// d = d0 + (u_b - u_a) with d0 the exact lattice offset, and the extension is formed without
+// cancellation as l - L0 = (2 d0.du + du.du) / (l + L0).
 // Blocks are persistent: each pops the next robot from a work counter over a longest-first
 // order, so an uneven population runs in one launch.
 #include "common.cuh"
@@ -15,19 +18,19 @@ namespace vx {
 namespace {
 
 struct SmemLayout {
-    float4* pos;
+    float4* u;
     float4* vel;
+    float4* spr;
     float* fx;
     float* fy;
     float* fz;
-    float4* spr;
 };
 
 __device__ __forceinline__ SmemLayout carve(void* base, int max_mass, int max_spring_smem)
 {
     SmemLayout L;
     char* p = (char*)base;
-    L.pos = (float4*)p; p += sizeof(float4) * max_mass;
+    L.u = (float4*)p; p += sizeof(float4) * max_mass;
     L.vel = (float4*)p; p += sizeof(float4) * max_mass;
     L.spr = (float4*)p; p += sizeof(float4) * max_spring_smem;
     L.fx = (float*)p; p += sizeof(float) * max_mass;
@@ -36,26 +39,20 @@ __device__ __forceinline__ SmemLayout carve(void* base, int max_mass, int max_sp
     return L;
 }
 
-// Spring force on mass a (the negative acts on b): f = k (l - L) d / l with d = x_b - x_a and
-// L = L0 + alpha L0 sin(w t) + beta L0 cos(w t).  Returns false for a zero-length spring.
-__device__ __forceinline__ float spring_scale(float4 q, float l2, float sn, float cs,
-                                              const StepConst& c)
-{
-    const unsigned bits = __float_as_uint(q.w);
-    const unsigned cls = bits >> 30;
-    const float L0 = cls == 1u ? c.edge : (cls == 2u ? c.edge_sqrt2 : c.edge_sqrt3);
-    const float L = L0 + q.y * sn + q.z * cs;
-    const float inv = rsqrtf(l2);
-    return l2 > 1e-30f ? q.x * (1.0f - L * inv) : 0.0f;
-}
-
 __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sh_robot;
+    __shared__ float4 sh_d0[13];   // lattice offset of each direction, rest length in .w
     const SmemLayout L = carve(smem_raw, a.max_mass, a.max_spring_smem);
     const int tid = threadIdx.x, T = blockDim.x;
     const StepConst c = a.c;
+    if (tid < 13) {
+        const int ix = lattice_dir(tid, 0), iy = lattice_dir(tid, 1), iz = lattice_dir(tid, 2);
+        const float dx = c.edge * ix, dy = c.edge * iy, dz = c.edge * iz;
+        const int cls = (ix != 0) + (iy != 0) + (iz != 0);
+        sh_d0[tid] = make_float4(dx, dy, dz, cls == 1 ? c.edge : (cls == 2 ? c.edge_sqrt2 : c.edge_sqrt3));
+    }
     int iter = 0;
     for (;;) {
         if (tid == 0) {
@@ -69,7 +66,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
         const int M = a.pv.n_mass[r], S = a.pv.n_spring[r];
         const int64_t mo = a.pv.moff[r], so = a.pv.soff[r];
         for (int m = tid; m < M; m += T) {
-            L.pos[m] = a.x[mo + m];
+            L.u[m] = a.x[mo + m];
             L.vel[m] = a.v[mo + m];
             L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
         }
@@ -83,11 +80,17 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             for (int s = tid; s < S; s += T) {
                 const float4 q = spr[s];
                 const unsigned bits = __float_as_uint(q.w);
-                const int ia = bits & 0x7fffu, ib = (bits >> 15) & 0x7fffu;
-                const float4 pa = L.pos[ia], pb = L.pos[ib];
-                const float dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
+                const int ia = bits & 0x3fffu, ib = (bits >> 14) & 0x3fffu, dir = bits >> 28;
+                const float4 ua = L.u[ia], ub = L.u[ib], d0 = sh_d0[dir];
+                const float dux = ub.x - ua.x, duy = ub.y - ua.y, duz = ub.z - ua.z;
+                const float dx = d0.x + dux, dy = d0.y + duy, dz = d0.z + duz;
                 const float l2 = dx * dx + dy * dy + dz * dz;
-                const float f = spring_scale(q, l2, sc.x, sc.y, c);
+                const float inv = rsqrtf(l2);
+                const float l = l2 * inv;
+                const float num = 2.0f * (d0.x * dux + d0.y * duy + d0.z * duz) +
+                                  (dux * dux + duy * duy + duz * duz);
+                const float ext = __fdividef(num, l + d0.w) - (q.y * sc.x + q.z * sc.y);
+                const float f = l2 > 1e-30f ? q.x * ext * inv : 0.0f;
                 const float gx = f * dx, gy = f * dy, gz = f * dz;
                 atomicAdd(&L.fx[ia], gx); atomicAdd(&L.fy[ia], gy); atomicAdd(&L.fz[ia], gz);
                 atomicAdd(&L.fx[ib], -gx); atomicAdd(&L.fy[ib], -gy); atomicAdd(&L.fz[ib], -gz);
@@ -96,29 +99,30 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             for (int m = tid; m < M; m += T) {
                 float fx = L.fx[m], fy = L.fy[m], fz = L.fz[m] - c.weight;
                 L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
-                float4 x = L.pos[m], v = L.vel[m];
-                if (c.ground_on && x.z < 0.f) {
-                    const float fn = c.k_ground * (-x.z);
+                float4 u = L.u[m], v = L.vel[m];
+                const float z = u.w + u.z;
+                if (c.ground_on && z < 0.f) {
+                    const float fn = c.k_ground * (-z);
                     fz += fn;
                     const float fh = sqrtf(fx * fx + fy * fy);
                     if (fh <= c.mu_s * fn) {
                         fx = 0.f; fy = 0.f; v.x = 0.f; v.y = 0.f;
                     } else {
-                        const float sc2 = 1.0f - c.mu_k * fn / fh;
-                        fx *= sc2; fy *= sc2;
+                        const float s2 = 1.0f - c.mu_k * fn / fh;
+                        fx *= s2; fy *= s2;
                     }
                 }
                 v.x = c.damping * (v.x + c.dt_over_m * fx);
                 v.y = c.damping * (v.y + c.dt_over_m * fy);
                 v.z = c.damping * (v.z + c.dt_over_m * fz);
-                x.x += c.dt * v.x; x.y += c.dt * v.y; x.z += c.dt * v.z;
-                L.pos[m] = x;
+                u.x += c.dt * v.x; u.y += c.dt * v.y; u.z += c.dt * v.z;
+                L.u[m] = u;
                 L.vel[m] = v;
             }
             __syncthreads();
         }
         for (int m = tid; m < M; m += T) {
-            a.x[mo + m] = L.pos[m];
+            a.x[mo + m] = L.u[m];
             a.v[mo + m] = L.vel[m];
         }
         __syncthreads();

@@ -17,6 +17,7 @@ constexpr int kTopoThreads = 1024;
 
 // The 13 corner offsets (dx, dy, dz) that point to a larger corner id, in increasing order of
 // (dz, dy, dx): from a fixed corner they reach larger corners in increasing corner-id order.
+// The step kernels use the same numbering (lattice_dir in common.cuh).
 __constant__ int8_t c_dir[13][3] = {
     {1, 0, 0},   {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1},
     {-1, 0, 1},  {0, 0, 1},  {1, 0, 1},  {-1, 1, 1}, {0, 1, 1},   {1, 1, 1}};
@@ -50,10 +51,6 @@ __device__ __forceinline__ int block_exclusive_scan(int val, int* sh, int* total
     __syncthreads();
     return base + x - val;
 }
-
-struct Springs13 {
-    int n;           // springs found for this mass
-};
 
 // Spring between corner (ci, cj, ck) and its neighbour along direction d: number of kept voxels
 // containing both corners and the sums of their parameters.
@@ -110,8 +107,8 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
            const float* __restrict__ w_all, const float* __restrict__ kappa_all,
            const float* __restrict__ phi_all, MatConst mc, double edge, int* label_all,
            int* count_all, int* corner_mass_all, int* mass_corner_all, int2* spr_ab_all,
-           float4* spr_p_all, float4* spr_pack_all, float4* x_all, float4* v_all, double* x0c,
-           int* status)
+           float4* spr_p_all, float4* spr_pack_all, float4* x0_all, float4* x_all,
+           float4* v_all, double* x0c, int* status)
 {
     __shared__ int sh_scan[32];
     __shared__ int sh_changed;
@@ -209,7 +206,9 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
     }
     if (tid == 0) { sh_zmin = INT_MAX; pv.n_mass[r] = M; }
     __syncthreads();
-    // 6. initial pose: lattice with the lowest mass at z = 0, at rest
+    // 6. initial pose: lattice with the lowest mass at z = 0, at rest.  The state is kept as
+    //    the displacement u from this rest lattice (small, hence precise in float32), with the
+    //    rest height z0 of the mass in the fourth lane: u = (ux, uy, uz, z0).
     for (int m = tid; m < M; m += T) atomicMin(&sh_zmin, mass_corner[m] / (cx * cy));
     __syncthreads();
     const int zmin = sh_zmin;
@@ -218,7 +217,8 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
         int c = mass_corner[m];
         int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
         float4 p = make_float4((float)(ci * edge), (float)(cj * edge), (float)((ck - zmin) * edge), 0.f);
-        x_all[mo + m] = p;
+        x0_all[mo + m] = p;
+        x_all[mo + m] = make_float4(0.f, 0.f, 0.f, p.z);
         v_all[mo + m] = make_float4(0.f, 0.f, 0.f, 0.f);
         xs += (double)p.x;
     }
@@ -263,14 +263,47 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
             float L0 = (float)(cls == 1 ? e1 : (cls == 2 ? e2 : e3));
             spr_ab_all[so + sbase] = make_int2(m, b);
             spr_p_all[so + sbase] = make_float4(L0, k, al, be);
-            if (spr_pack_all) {
-                unsigned bits = (unsigned)m | ((unsigned)b << 15) | ((unsigned)cls << 30);
-                spr_pack_all[so + sbase] = make_float4(k, al * L0, be * L0, __uint_as_float(bits));
-            }
             ++sbase;
         }
     }
     if (tid == 0) pv.n_spring[r] = S;
+    if (!spr_pack_all) return;
+    // 8. the resident path's copy, direction-major: all springs of direction 0 by ascending a,
+    //    then direction 1, ...  Within a warp the endpoints of one direction are distinct masses,
+    //    so the force accumulation does not collide.  Packed as (k, alpha L0, beta L0,
+    //    a | b << 14 | direction << 28).
+    int dbase = 0;
+    for (int d = 0; d < 13; ++d) {
+        int nd = 0;
+        for (int m = m_beg; m < m_end; ++m) {
+            int c = mass_corner[m];
+            int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
+            int bi = ci + c_dir[d][0], bj = cj + c_dir[d][1], bk = ck + c_dir[d][2];
+            if (bi < 0 || bj < 0 || bi >= cx || bj >= cy || bk >= cz) continue;
+            if (spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, nullptr,
+                                 nullptr, nullptr) > 0)
+                ++nd;
+        }
+        int total;
+        int pos = dbase + block_exclusive_scan(nd, sh_scan, &total);
+        const int cls = (c_dir[d][0] != 0) + (c_dir[d][1] != 0) + (c_dir[d][2] != 0);
+        const float L0 = (float)(cls == 1 ? e1 : (cls == 2 ? e2 : e3));
+        for (int m = m_beg; m < m_end; ++m) {
+            int c = mass_corner[m];
+            int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
+            int bi = ci + c_dir[d][0], bj = cj + c_dir[d][1], bk = ck + c_dir[d][2];
+            if (bi < 0 || bj < 0 || bi >= cx || bj >= cy || bk >= cz) continue;
+            float k, al, be;
+            if (spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, &k, &al,
+                                 &be) == 0)
+                continue;
+            int b = corner_mass[bi + cx * (bj + cy * bk)];
+            unsigned bits = (unsigned)m | ((unsigned)b << 14) | ((unsigned)d << 28);
+            spr_pack_all[so + pos] = make_float4(k, al * L0, be * L0, __uint_as_float(bits));
+            ++pos;
+        }
+        dbase += total;
+    }
 }
 
 }  // namespace
@@ -278,14 +311,14 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
 cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, const float* w,
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
-                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x, float4* v,
-                            double* x0c, int* status, int max_threads, cudaStream_t s)
+                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x0, float4* x,
+                            float4* v, double* x0c, int* status, int max_threads, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
     int T = max_threads > 0 && max_threads < kTopoThreads ? max_threads : kTopoThreads;
     k_topology<<<pv.P, T, 0, s>>>(pv, mat_raw, mat, w, kappa, phi, mc, edge, label, count,
-                                  corner_mass, mass_corner, spr_ab, spr_p, spr_pack, x, v, x0c,
-                                  status);
+                                  corner_mass, mass_corner, spr_ab, spr_p, spr_pack, x0, x, v,
+                                  x0c, status);
     return cudaGetLastError();
 }
 
