@@ -71,6 +71,12 @@ enum {
     SIM_PATH_STREAMED = 2   /* structure-of-arrays state in device memory, one pass per step */
 };
 
+/* MLP query kernel. */
+enum {
+    SIM_MLP_TENSOR = 0, /* tcgen05 tensor-core kernel, accumulators in TMEM, operands by TMA */
+    SIM_MLP_SIMT = 1    /* CUDA-core kernel with the same bfloat16 rounding points */
+};
+
 /* Physics constants (Table II; the workload configurations override some of them) and
  * execution choices. */
 typedef struct {
@@ -91,6 +97,8 @@ typedef struct {
     int32_t accumulate; /* SIM_ACC_* */
     int32_t path;       /* SIM_PATH_* */
     int32_t threads;    /* threads per robot on the resident path; 0 = autotuned */
+    int32_t mlp_kernel; /* SIM_MLP_TENSOR (tcgen05, default) or SIM_MLP_SIMT (CUDA cores) */
+    int32_t pad_;
 } sim_params;
 
 /* Per-voxel parametrisation for SIM_MODE_PARAMS (all arrays cover every voxel of every grid):

@@ -375,8 +375,13 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
             }
             VX_CK(ctx->d_pe.ensure((size_t)Q * kPeDim * 2));
             VX_LAUNCH(ctx, launch_pe_table(d[0], d[1], d[2], bsrc, ctx->d_pe.p, s));
-            VX_LAUNCH(ctx, launch_mlp_query_simt(P, Q, ctx->d_pe.p, gsrc, mc, ctx->d_mat_raw.p, ctx->d_w.p,
-                                        ctx->d_kappa.p, ctx->d_phi.p, s));
+            if (ctx->p.mlp_kernel == SIM_MLP_SIMT)
+                VX_LAUNCH(ctx, launch_mlp_query_simt(P, Q, ctx->d_pe.p, gsrc, mc, ctx->d_mat_raw.p, ctx->d_w.p,
+                                                     ctx->d_kappa.p, ctx->d_phi.p, s));
+            else
+                VX_LAUNCH(ctx, launch_mlp_query(P, Q, ctx->d_pe.p, gsrc, mc, ctx->d_mat_raw.p, ctx->d_w.p,
+                                                ctx->d_kappa.p, ctx->d_phi.p, ctx->d_status.p + 1,
+                                                ctx->num_sms, s));
         }
         // topology
         VX_LAUNCH(ctx, launch_topology(ctx->view(), ctx->d_mat_raw.p, ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p,

@@ -81,7 +81,9 @@ cudaError_t launch_decode_params(const uint8_t* mats, const float* w_in, const f
 cudaError_t launch_pe_table(int nx, int ny, int nz, const float* B, void* pe_bf16,
                             cudaStream_t s);
 cudaError_t launch_mlp_query(int P, int Q, const void* pe_bf16, const float* genomes, MatConst mc,
-                             uint8_t* mat, float* w, float* kappa, float* phi, cudaStream_t s);
+                             uint8_t* mat, float* w, float* kappa, float* phi, int* status,
+                             int num_sms, cudaStream_t s);
+size_t mlp_tc_smem_bytes();
 cudaError_t launch_mlp_query_simt(int P, int Q, const void* pe_bf16, const float* genomes,
                                   MatConst mc, uint8_t* mat, float* w, float* kappa, float* phi,
                                   cudaStream_t s);

@@ -1,0 +1,397 @@
+// MLP spatial query on the 5th-generation tensor cores (Section II-C: "the material score from
+// the model's Softmax branch will determine the material category and the material weight from
+// the model's Sigmoid branch will be multiplied by the material parameters"; Eq. (1) gives the
+// input encoding).
+//
+// Per genome: gamma [Q x 256] -> ReLU(. W1^T + b1) [Q x 64] -> ReLU(. W2^T + b2) [Q x 64]
+// -> (. W3^T + b3) [Q x 6]; material = argmax of outputs 0..4 (softmax is monotone; ties to the
+// lowest id), weight = sigmoid(output 5).
+//
+// One CTA (4 warps) per genome at a time, persistent over genomes.  Operands are bfloat16 in
+// shared memory in the 128-byte-swizzled K-major layout the tensor core reads directly:
+//   * gamma tiles of 128 queries arrive by TMA (double-buffered, the next tile prefetched while
+//     the current one is multiplied);
+//   * W1, W2, W3 are converted from the float32 genome by the CTA's threads into the same
+//     layout (W3 padded to 16 rows);
+//   * the three layers are tcgen05.mma kind::f16 (M = 128; N = 64, 64, 16) accumulating in
+//     TMEM; one thread issues them; completion is signalled on an mbarrier by tcgen05.commit;
+//   * each epilogue reads its accumulator rows with tcgen05.ld (warp w owns TMEM lanes
+//     32w..32w+31 = queries of the tile), adds the bias, applies ReLU, rounds to bfloat16 and
+//     writes the next layer's A operand back to shared memory; the last epilogue computes the
+//     heads and writes material, weight, stiffness and phase per voxel.
+// Every mbarrier wait is bounded: on timeout the kernel raises a status bit, abandons the
+// remaining work and still releases its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace vx {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kKBlock = 64;                                  // bf16 per 128-byte swizzle row
+constexpr int kABytes = kTileM * kPeDim * 2;                 // 64 KB: one gamma tile
+constexpr int kW1Bytes = kHidden * kPeDim * 2;               // 32 KB
+constexpr int kW2Bytes = kHidden * kHidden * 2;              // 8 KB
+constexpr int kW3Rows = 16;
+constexpr int kW3Bytes = kW3Rows * kHidden * 2;              // 2 KB
+constexpr int kHBytes = kTileM * kHidden * 2;                // 16 KB
+constexpr int kTmemCols = 256;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+struct __align__(1024) Smem {
+    unsigned char a[2][kABytes];
+    unsigned char w1[kW1Bytes];
+    unsigned char w2[kW2Bytes];
+    unsigned char h[kHBytes];
+    unsigned char w3[kW3Bytes];
+    float b1[kHidden];
+    float b2[kHidden];
+    float b3[kW3Rows];
+    uint64_t tma_bar[2];
+    uint64_t mma_bar;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row, k) of a K-major bfloat16 operand stored as 64-wide K blocks of
+// `rows` x 128 bytes, with the 128-byte swizzle (16-byte chunk j of row r at chunk j ^ (r % 8)).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k, int rows)
+{
+    const int kb = k / kKBlock, kk = k % kKBlock;
+    const int chunk = (kk >> 3) ^ (row & 7);
+    return (uint32_t)(kb * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (kk & 7) * 2);
+}
+
+// Shared-memory matrix descriptor of a 128-byte-swizzled K-major operand starting at `addr`
+// (rows grouped by 8 at a 1024-byte stride).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);     // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, bfloat16 A and B (K-major), float32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; gives up (and flags the CTA) after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, Smem& s, int* status)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (*(volatile int*)&s.abort) return false;
+    }
+    *(volatile int*)&s.abort = 1;
+    atomicOr(status, 4);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                     uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive 32-bit columns of TMEM into 16 registers of each thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&p);
+}
+
+// Convert a float32 [rows][K] weight block (8-byte aligned) into the swizzled bf16 layout.
+__device__ __forceinline__ void load_weights(const float* __restrict__ src, int rows, int K,
+                                             int valid_rows, unsigned char* dst)
+{
+    const int chunks = rows * (K / 8);
+    for (int c = threadIdx.x; c < chunks; c += kThreads) {
+        const int row = c / (K / 8), k0 = (c % (K / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (row < valid_rows) {
+            const float2* p = reinterpret_cast<const float2*>(src + (size_t)row * K + k0);
+            const float2 a = p[0], b = p[1], cc = p[2], d = p[3];
+            v = make_uint4(pack_bf16(a.x, a.y), pack_bf16(b.x, b.y), pack_bf16(cc.x, cc.y), pack_bf16(d.x, d.y));
+        }
+        *reinterpret_cast<uint4*>(dst + sw128_offset(row, k0, rows)) = v;
+    }
+}
+
+// Bias + ReLU of a 64-wide accumulator row block, rounded to bfloat16 into the A operand
+// of the next layer (row = query of the tile).
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bias, unsigned char* h, int row)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < kHidden; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr + c0, v);
+        uint32_t p[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            p[i] = pack_bf16(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f), fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
+        *reinterpret_cast<uint4*>(h + sw128_offset(row, c0, kTileM)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(h + sw128_offset(row, c0 + 8, kTileM)) = make_uint4(p[4], p[5], p[6], p[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* __restrict__ genomes,
+         MatConst mc, uint8_t* __restrict__ mat, float* __restrict__ w_out, float* __restrict__ kappa,
+         float* __restrict__ phi, int* status)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s.tmem_base)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&s.tma_bar[0], 1);
+        mbar_init(&s.tma_bar[1], 1);
+        mbar_init(&s.mma_bar, 1);
+        s.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+    const uint32_t t_d1 = tmem, t_d2 = tmem + 64, t_d3 = tmem + 128;
+    const uint32_t lane_sel = (uint32_t)(warp * 32) << 16;    // this warp's TMEM lane quarter
+    const int ntiles = (Q + kTileM - 1) / kTileM;
+    uint32_t tma_phase[2] = {0, 0}, mma_phase = 0;
+    int buf = 0;
+    constexpr uint32_t id_h = idesc_bf16(kTileM, kHidden);
+    constexpr uint32_t id_o = idesc_bf16(kTileM, kW3Rows);
+
+    for (int g = blockIdx.x; g < P; g += gridDim.x) {
+        const float* G = genomes + (size_t)g * kGenome;
+        load_weights(G + kOffW1, kHidden, kPeDim, kHidden, s.w1);
+        load_weights(G + kOffW2, kHidden, kHidden, kHidden, s.w2);
+        load_weights(G + kOffW3, kW3Rows, kHidden, kOut, s.w3);
+        for (int i = tid; i < kHidden; i += kThreads) {
+            s.b1[i] = G[kOffB1 + i];
+            s.b2[i] = G[kOffB2 + i];
+        }
+        if (tid < kW3Rows) s.b3[tid] = tid < kOut ? G[kOffB3 + tid] : 0.f;
+        proxy_fence();
+        __syncthreads();
+        if (tid == 0 && !s.abort) {
+            mbar_expect_tx(&s.tma_bar[buf], kABytes);
+            for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
+                tma_load_2d(s.a[buf] + kb * kTileM * 128, &pe_map, &s.tma_bar[buf], kb * kKBlock, 0);
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            const int cur = buf;
+            if (tid == 0 && t + 1 < ntiles && !s.abort) {   // prefetch the next gamma tile
+                mbar_expect_tx(&s.tma_bar[cur ^ 1], kABytes);
+                for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
+                    tma_load_2d(s.a[cur ^ 1] + kb * kTileM * 128, &pe_map, &s.tma_bar[cur ^ 1],
+                                kb * kKBlock, (t + 1) * kTileM);
+            }
+            // layer 1: D1 = gamma_tile . W1^T  (K = 256: 4 swizzle blocks x 4 steps of 16)
+            if (tid == 0) {
+                if (mbar_wait(&s.tma_bar[cur], tma_phase[cur], s, status)) {
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(s.a[cur]), b0 = smem_u32(s.w1);
+#pragma unroll
+                    for (int k = 0; k < kPeDim / 16; ++k) {
+                        const uint32_t ao = (k / 4) * (kTileM * 128) + (k % 4) * 32;
+                        const uint32_t bo = (k / 4) * (kHidden * 128) + (k % 4) * 32;
+                        umma(t_d1, sw128_desc(a0 + ao), sw128_desc(b0 + bo), id_h, k > 0);
+                    }
+                    umma_commit(&s.mma_bar);
+                }
+            }
+            tma_phase[cur] ^= 1;
+            buf ^= 1;
+            const int row = warp * 32 + lane;
+            // epilogue 1 -> H
+            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            mma_phase ^= 1;
+            tc_fence_after();
+            if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, s.h, row);
+            proxy_fence();
+            tc_fence_before();
+            __syncthreads();
+            // layer 2: D2 = H . W2^T
+            if (tid == 0 && !s.abort) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(s.h), b0 = smem_u32(s.w2);
+#pragma unroll
+                for (int k = 0; k < kHidden / 16; ++k)
+                    umma(t_d2, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_h, k > 0);
+                umma_commit(&s.mma_bar);
+            }
+            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            mma_phase ^= 1;
+            tc_fence_after();
+            if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, s.h, row);
+            proxy_fence();
+            tc_fence_before();
+            __syncthreads();
+            // layer 3: D3 = H . W3^T (N = 16, rows 6..15 of W3 are zero)
+            if (tid == 0 && !s.abort) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(s.h), b0 = smem_u32(s.w3);
+#pragma unroll
+                for (int k = 0; k < kHidden / 16; ++k)
+                    umma(t_d3, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_o, k > 0);
+                umma_commit(&s.mma_bar);
+            }
+            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            mma_phase ^= 1;
+            tc_fence_after();
+            if (!s.abort) {
+                float o[16];
+                tmem_ld16(t_d3 + lane_sel, o);
+                const int q = t * kTileM + row;
+                if (q < Q) {
+                    int best = 0;
+                    float bv = o[0] + s.b3[0];
+#pragma unroll
+                    for (int c = 1; c < kNumMat; ++c) {
+                        const float x = o[c] + s.b3[c];
+                        if (x > bv) { bv = x; best = c; }
+                    }
+                    const float wt = 1.0f / (1.0f + expf(-(o[5] + s.b3[5])));
+                    const size_t idx = (size_t)g * Q + q;
+                    mat[idx] = (uint8_t)best;
+                    w_out[idx] = wt;
+                    kappa[idx] = mc.k[best];
+                    phi[idx] = mc.phase[best];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t mlp_tc_smem_bytes() { return sizeof(Smem) + 1024; }
+
+cudaError_t launch_mlp_query(int P, int Q, const void* pe_bf16, const float* genomes, MatConst mc,
+                             uint8_t* mat, float* w, float* kappa, float* phi, int* status,
+                             int num_sms, cudaStream_t s)
+{
+    if (P == 0 || Q == 0) return cudaSuccess;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // gamma table [Q][256] bfloat16, row stride 512 B; boxes of 64 x 128, 128-byte swizzle
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)kPeDim, (cuuint64_t)Q};
+    const cuuint64_t strides[1] = {(cuuint64_t)kPeDim * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKBlock, (cuuint32_t)kTileM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(pe_bf16), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const size_t smem = mlp_tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = P < num_sms ? P : num_sms;
+    k_mlp_tc<<<grid, kThreads, smem, s>>>(map, P, Q, genomes, mc, mat, w, kappa, phi, status);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

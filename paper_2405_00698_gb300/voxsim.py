@@ -18,6 +18,7 @@ SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ESTATE, SIM_ETIMEOUT, SIM_ENUMERI
 MEM_HOST, MEM_DEVICE = 0, 1
 MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS = 0, 1, 2, 3
 ACC_AUTO, ACC_ATOMIC, ACC_GATHER = 0, 1, 2
+MLP_TENSOR, MLP_SIMT = 0, 1
 PATH_AUTO, PATH_RESIDENT, PATH_STREAMED = 0, 1, 2
 GENOME_LEN = 20998
 
@@ -38,10 +39,11 @@ class SimParams(C.Structure):
                                            "mu_s", "mu_k", "freq", "dead_bound")] + [
         ("k_mat", C.c_double * 5), ("amp_mat", C.c_double * 5), ("phase_mat", C.c_double * 5),
         ("ground_on", C.c_int32), ("accumulate", C.c_int32), ("path", C.c_int32),
-        ("threads", C.c_int32)]
+        ("threads", C.c_int32), ("mlp_kernel", C.c_int32), ("pad_", C.c_int32)]
 
     @classmethod
-    def of(cls, phys, accumulate: int = ACC_AUTO, path: int = PATH_AUTO, threads: int = 0):
+    def of(cls, phys, accumulate: int = ACC_AUTO, path: int = PATH_AUTO, threads: int = 0,
+           mlp_kernel: int = 0):
         p = cls()
         for n in ("dt", "gravity", "mass", "edge", "damping", "k_ground", "mu_s", "mu_k", "freq",
                   "dead_bound"):
@@ -51,6 +53,7 @@ class SimParams(C.Structure):
         p.phase_mat = (C.c_double * 5)(*map(float, phys.phase_mat))
         p.ground_on = 1 if phys.ground_on else 0
         p.accumulate, p.path, p.threads = int(accumulate), int(path), int(threads)
+        p.mlp_kernel = int(mlp_kernel)
         return p
 
 
@@ -122,11 +125,11 @@ class Simulator:
     """One library context on one GPU, enqueueing on a torch CUDA stream."""
 
     def __init__(self, phys, device: int = 0, stream=None, accumulate: int = ACC_AUTO,
-                 path: int = PATH_AUTO, threads: int = 0):
+                 path: int = PATH_AUTO, threads: int = 0, mlp_kernel: int = MLP_TENSOR):
         import torch
         self.device = int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.params = SimParams.of(phys, accumulate, path, threads)
+        self.params = SimParams.of(phys, accumulate, path, threads, mlp_kernel)
         h = C.c_void_p()
         _check(lib().sim_create(C.byref(self.params), self.device, C.c_void_p(self.stream.cuda_stream),
                                 C.byref(h)))
