@@ -107,9 +107,17 @@ void orc_pe_table(int nx, int ny, int nz, const float* B, double* out)
  * Biases stay float32.  Outputs per query: the six raw outputs (logits_out, optional), the
  * chosen material = argmax of the five scores taken on the float32-rounded scores (softmax is
  * monotone, so it does not change the choice; ties go to the lowest material id), the material
- * weight w = sigmoid(o5), and an argmax guard band (guard_out, optional): the bound
- * 2^-6 * max_c sum_j |W3[c][j] h2[j]| on how far bfloat16 re-roundings of the hidden
- * activations can move a score. */
+ * weight w = sigmoid(o5), and a guard band (guard_out, optional) on how far a float32
+ * implementation with the same rounding points can move the six outputs.  A float32 sum of K
+ * terms differs from the exact one by at most delta = 2 (K + 2) 2^-24 sum |terms|; a hidden
+ * activation h = bf16(relu(x)) can then change only if bf16(relu(x - delta)) differs from
+ * bf16(relu(x + delta)), by at most that difference.  The bound is carried through the layers
+ * (a changed h1 widens the next layer's delta by |W2| times its change) and the guard is the
+ * largest output bound. */
+static double relu_bf16(double x) { return orc_round_bf16(x > 0.0 ? x : 0.0); }
+
+static double acc_err(int K, double mag) { return 2.0 * (K + 2) * ldexp(mag, -24); }
+
 void orc_mlp_query(int nx, int ny, int nz, const float* B, const float* genome,
                    uint8_t* mat_out, double* w_out, double* logits_out, double* guard_out)
 {
@@ -122,28 +130,46 @@ void orc_mlp_query(int nx, int ny, int nz, const float* B, const float* genome,
     double g[ORC_PE_D], h1[ORC_H], h2[ORC_H], o[ORC_OUT];
     for (int q = 0; q < Q; ++q) {
         for (int c = 0; c < ORC_PE_D; ++c) g[c] = orc_round_bf16(pe[(size_t)q * ORC_PE_D + c]);
+        double dh1[ORC_H], dh2[ORC_H];
         for (int r = 0; r < ORC_H; ++r) {
-            double acc = 0.0;
-            for (int c = 0; c < ORC_PE_D; ++c) acc += orc_round_bf16(W1[r * ORC_PE_D + c]) * g[c];
-            acc += (double)b1[r];
-            h1[r] = orc_round_bf16(acc > 0.0 ? acc : 0.0);
-        }
-        for (int r = 0; r < ORC_H; ++r) {
-            double acc = 0.0;
-            for (int c = 0; c < ORC_H; ++c) acc += orc_round_bf16(W2[r * ORC_H + c]) * h1[c];
-            acc += (double)b2[r];
-            h2[r] = orc_round_bf16(acc > 0.0 ? acc : 0.0);
-        }
-        double spread = 0.0;
-        for (int r = 0; r < ORC_OUT; ++r) {
             double acc = 0.0, mag = 0.0;
-            for (int c = 0; c < ORC_H; ++c) {
-                double t = orc_round_bf16(W3[r * ORC_H + c]) * h2[c];
+            for (int c = 0; c < ORC_PE_D; ++c) {
+                double t = orc_round_bf16(W1[r * ORC_PE_D + c]) * g[c];
                 acc += t;
                 mag += fabs(t);
             }
+            acc += (double)b1[r];
+            mag += fabs((double)b1[r]);
+            h1[r] = relu_bf16(acc);
+            double d = acc_err(ORC_PE_D, mag);
+            dh1[r] = fabs(relu_bf16(acc + d) - relu_bf16(acc - d));
+        }
+        for (int r = 0; r < ORC_H; ++r) {
+            double acc = 0.0, mag = 0.0, prop = 0.0;
+            for (int c = 0; c < ORC_H; ++c) {
+                double wq = orc_round_bf16(W2[r * ORC_H + c]);
+                acc += wq * h1[c];
+                mag += fabs(wq * h1[c]);
+                prop += fabs(wq) * dh1[c];
+            }
+            acc += (double)b2[r];
+            mag += fabs((double)b2[r]);
+            h2[r] = relu_bf16(acc);
+            double d = prop + acc_err(ORC_H, mag);
+            dh2[r] = fabs(relu_bf16(acc + d) - relu_bf16(acc - d));
+        }
+        double spread = 0.0;
+        for (int r = 0; r < ORC_OUT; ++r) {
+            double acc = 0.0, mag = 0.0, prop = 0.0;
+            for (int c = 0; c < ORC_H; ++c) {
+                double wq = orc_round_bf16(W3[r * ORC_H + c]);
+                acc += wq * h2[c];
+                mag += fabs(wq * h2[c]);
+                prop += fabs(wq) * dh2[c];
+            }
             o[r] = acc + (double)b3[r];
-            if (r < 5 && mag > spread) spread = mag;
+            double bound = prop + acc_err(ORC_H, mag + fabs((double)b3[r]));
+            if (bound > spread) spread = bound;
         }
         int best = 0;
         float bestv = (float)o[0];
@@ -152,7 +178,7 @@ void orc_mlp_query(int nx, int ny, int nz, const float* B, const float* genome,
         mat_out[q] = (uint8_t)best;
         w_out[q] = 1.0 / (1.0 + exp(-o[5]));
         if (logits_out) for (int r = 0; r < ORC_OUT; ++r) logits_out[(size_t)q * ORC_OUT + r] = o[r];
-        if (guard_out) guard_out[q] = ldexp(spread, -6);
+        if (guard_out) guard_out[q] = spread;
     }
     free(pe);
 }

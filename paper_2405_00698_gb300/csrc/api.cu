@@ -111,10 +111,16 @@ struct voxsim_ctx {
     int max_corner = 0;
     int64_t max_spring_cap = 0;
     int64_t step = 0;
+    // lattice work items (robots up to lattice_max_threads() corners) and the rest
+    int n_items = 0, n_big = 0, max_big_corner = 0;
+    int64_t max_big_spring_cap = 0;
     // device buffers
     DevBuf<int> d_dims;
     DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
-    DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status;
+    DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big;
+    DevBuf<int4> d_items;
+    DevBuf<uint32_t> d_cflags;
+    DevBuf<float> d_prm;
     DevBuf<uint8_t> d_in_u8, d_mat_raw, d_mat;
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
     DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
@@ -172,6 +178,10 @@ struct voxsim_ctx {
         return c;
     }
 };
+
+extern "C" {
+static sim_status build_work_items(voxsim_ctx* ctx);
+}
 
 namespace {
 
@@ -284,9 +294,9 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     }
     if (P > 0 && !genomes) return fail(SIM_EINVAL, "null genomes");
     const int64_t V = voff[P], Mc = moff[P], Sc = soff[P];
-    const bool packed = max_corner <= kResidentMaxMass;
+    const bool packed = max_corner <= kResidentMaxCorner;
     if (!packed && ctx->p.path == SIM_PATH_RESIDENT)
-        return fail(SIM_EINVAL, "robots with more than %d corners need the streamed path", kResidentMaxMass);
+        return fail(SIM_EINVAL, "robots with more than %d corners need the streamed path", kResidentMaxCorner);
     // host-side validation of host materials
     if (mem == SIM_MEM_HOST && (mode == SIM_MODE_MATERIALS || mode == SIM_MODE_PARAMS)) {
         const uint8_t* m = mode == SIM_MODE_MATERIALS ? (const uint8_t*)genomes
@@ -305,7 +315,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     VX_CK(ctx->d_voff.ensure(P + 1)); VX_CK(ctx->d_moff.ensure(P + 1)); VX_CK(ctx->d_soff.ensure(P + 1));
     VX_CK(ctx->d_tmp_off.ensure(P + 1));
     VX_CK(ctx->d_nm.ensure(P)); VX_CK(ctx->d_ns.ensure(P)); VX_CK(ctx->d_lpt.ensure(P));
-    VX_CK(ctx->d_queue.ensure(1)); VX_CK(ctx->d_status.ensure(4));
+    VX_CK(ctx->d_queue.ensure(2)); VX_CK(ctx->d_status.ensure(4));
     VX_CK(ctx->d_mat_raw.ensure(V)); VX_CK(ctx->d_mat.ensure(V));
     VX_CK(ctx->d_w.ensure(V)); VX_CK(ctx->d_kappa.ensure(V)); VX_CK(ctx->d_phi.ensure(V));
     VX_CK(ctx->d_label.ensure(V)); VX_CK(ctx->d_count.ensure(V));
@@ -313,6 +323,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     VX_CK(ctx->d_sab.ensure(Sc)); VX_CK(ctx->d_sp.ensure(Sc));
     if (packed) VX_CK(ctx->d_spack.ensure(Sc));
     VX_CK(ctx->d_x0.ensure(Mc)); VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
+    VX_CK(ctx->d_cflags.ensure(Mc)); VX_CK(ctx->d_prm.ensure(39 * (size_t)Mc));
     VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
     ctx->dims = d; ctx->voff = voff; ctx->moff = moff; ctx->soff = soff;
     ctx->P = P; ctx->V_tot = V; ctx->M_cap = Mc; ctx->S_cap = Sc;
@@ -387,15 +398,85 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         VX_LAUNCH(ctx, launch_topology(ctx->view(), ctx->d_mat_raw.p, ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p,
                               ctx->d_phi.p, mc, ctx->p.edge, ctx->d_label.p, ctx->d_count.p,
                               ctx->d_corner_mass.p, ctx->d_mass_corner.p, ctx->d_sab.p, ctx->d_sp.p,
-                              packed ? ctx->d_spack.p : nullptr, ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
+                              packed ? ctx->d_spack.p : nullptr, ctx->d_cflags.p, ctx->d_prm.p,
+                              ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
                               ctx->d_x0c.p, ctx->d_status.p, 0, s));
         // longest-first processing order (by spring count, ties by index)
         k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
         VX_LAUNCH(ctx, cudaGetLastError());
         VX_LAUNCH(ctx, launch_evo_rank(ctx->d_keys.p, P, ctx->d_lpt.p, s));
+        if (sim_status st = build_work_items(ctx)) return st;
     }
     ctx->step = 0;
     ctx->have_pop = true;
+    return SIM_OK;
+}
+
+// Work items of the lattice path: robots grouped by corner count into classes of
+// 64, 128, 192, 256, 384 or 768 threads per robot (each divides the 768-thread block), several
+// robots per block for the small classes; items ordered largest class first, robots within a
+// class by descending corner count (longest-processing-time first).  Robots with more corners
+// go to the atomic kernel.  Everything is known from the grid shapes, so no device data is read.
+static sim_status build_work_items(voxsim_ctx* ctx)
+{
+    static const int kClass[6] = {64, 128, 192, 256, 384, 768};
+    const int block = lattice_max_threads();
+    std::vector<std::vector<std::pair<int, int>>> byclass(6);
+    std::vector<int> big;
+    ctx->max_big_corner = 0;
+    ctx->max_big_spring_cap = 0;
+    const bool lattice = ctx->p.accumulate != SIM_ACC_ATOMIC;
+    for (int r = 0; r < ctx->P; ++r) {
+        const int nx = ctx->dims[3 * r], ny = ctx->dims[3 * r + 1], nz = ctx->dims[3 * r + 2];
+        const int C = (nx + 1) * (ny + 1) * (nz + 1);
+        int cls = -1;
+        if (lattice)
+            for (int k = 0; k < 6; ++k)
+                if (C <= kClass[k]) { cls = k; break; }
+        if (cls < 0) {
+            big.push_back(r);
+            ctx->max_big_corner = std::max(ctx->max_big_corner, C);
+            ctx->max_big_spring_cap = std::max(ctx->max_big_spring_cap, full_springs(nx, ny, nz));
+        } else {
+            byclass[cls].push_back({-C, r});
+        }
+    }
+    if (!big.empty() && ctx->p.accumulate == SIM_ACC_GATHER)
+        return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners", block);
+    std::vector<int4> items;
+    std::vector<int> robots;
+    for (int k = 5; k >= 0; --k) {
+        auto& v = byclass[k];
+        std::sort(v.begin(), v.end());
+        const int per = block / kClass[k];
+        for (size_t i = 0; i < v.size(); i += per) {
+            const int n = (int)std::min<size_t>(per, v.size() - i);
+            items.push_back(make_int4((int)robots.size(), n, kClass[k], 0));
+            for (int j = 0; j < n; ++j) robots.push_back(v[i + j].second);
+        }
+    }
+    ctx->n_items = (int)items.size();
+    ctx->n_big = (int)big.size();
+    cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_items.ensure(items.size()));
+    VX_CK(ctx->d_item_robots.ensure(robots.size()));
+    VX_CK(ctx->d_big.ensure(big.size()));
+    if (!items.empty()) {
+        VX_CK(cudaMemcpyAsync(ctx->d_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_item_robots.p, robots.data(), sizeof(int) * robots.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (!big.empty()) {
+        // longest first by capacity (corner count)
+        std::sort(big.begin(), big.end(), [&](int a, int b) {
+            auto corners = [&](int r) {
+                return (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
+            };
+            return corners(a) != corners(b) ? corners(a) > corners(b) : a < b;
+        });
+        VX_CK(cudaMemcpyAsync(ctx->d_big.p, big.data(), sizeof(int) * big.size(), cudaMemcpyHostToDevice, s));
+    }
+    // the host vectors are copied from pageable memory: wait so they may go out of scope
+    VX_CK(cudaStreamSynchronize(s));
     return SIM_OK;
 }
 
@@ -413,42 +494,68 @@ static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
     return SIM_OK;
 }
 
+static sim_status step_lattice(voxsim_ctx* ctx, int n)
+{
+    if (ctx->n_items == 0) return SIM_OK;
+    LatticeArgs a{};
+    a.pv = ctx->view();
+    a.cflags = ctx->d_cflags.p;
+    a.prm = ctx->d_prm.p;
+    a.u = ctx->d_x.p;
+    a.v = ctx->d_v.p;
+    a.sc = ctx->d_sc.p;
+    a.nsteps = n;
+    a.c = ctx->stepconst();
+    a.items = ctx->d_items.p;
+    a.item_robots = ctx->d_item_robots.p;
+    a.n_items = ctx->n_items;
+    a.queue = ctx->d_queue.p;
+    const int threads = lattice_max_threads();
+    const size_t smem = sizeof(float) * kLatticeSlotFloats * (size_t)threads;
+    const int grid = std::min(ctx->n_items, ctx->num_sms);
+    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), ctx->stream));
+    VX_LAUNCH(ctx, launch_step_lattice(a, grid, threads, smem, ctx->stream));
+    return SIM_OK;
+}
+
 static sim_status step_resident(voxsim_ctx* ctx, int n)
 {
+    if (ctx->n_big == 0) return SIM_OK;
     cudaStream_t s = ctx->stream;
     ResidentArgs a{};
     a.pv = ctx->view();
     a.spr_pack = ctx->d_spack.p;
+    a.cflags = ctx->d_cflags.p;
     a.x = ctx->d_x.p;
     a.v = ctx->d_v.p;
     a.sc = ctx->d_sc.p;
     a.nsteps = n;
     a.c = ctx->stepconst();
-    a.order = ctx->d_lpt.p;
-    a.queue = ctx->d_queue.p;
+    a.order = ctx->d_big.p;
+    a.n_robots = ctx->n_big;
+    a.queue = ctx->d_queue.p + 1;
     a.accumulate = SIM_ACC_ATOMIC;
     // launch shape: threads per robot and blocks per SM from the largest robot's capacity
     int threads = ctx->p.threads;
-    const int64_t sc = ctx->max_spring_cap;
+    const int64_t sc = ctx->max_big_spring_cap;
     if (threads <= 0) threads = sc <= 1536 ? 256 : (sc <= 6144 ? 512 : 1024);
     threads = std::max(32, std::min(1024, (threads + 31) / 32 * 32));
-    const size_t mass_bytes = resident_smem_bytes(ctx->max_corner, 0, a.accumulate);
+    const size_t mass_bytes = resident_smem_bytes(ctx->max_big_corner, 0, a.accumulate);
     const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
     if (mass_bytes > budget) return fail(SIM_EINVAL, "robot too large for the resident path");
     int64_t spr_fit = (int64_t)((budget - mass_bytes) / sizeof(float4));
     // several blocks per SM when everything of the largest robot fits in a fraction of it
     int per_sm = 1;
     const size_t need = mass_bytes + sizeof(float4) * (size_t)sc;
-    while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin &&
-           threads * (per_sm + 1) <= 2048)
+    while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin && threads * (per_sm + 1) <= 2048)
         ++per_sm;
     if (per_sm > 1) spr_fit = sc;
-    a.max_mass = ctx->max_corner;
+    a.max_mass = ctx->max_big_corner;
     a.max_spring_smem = (int)std::min<int64_t>(sc, spr_fit);
     const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
-    int grid = std::min<int64_t>(ctx->P, (int64_t)ctx->num_sms * per_sm);
+    int grid = (int)std::min<int64_t>(ctx->n_big, (int64_t)ctx->num_sms * per_sm);
     if (grid < 1) grid = 1;
-    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+    VX_CK(cudaMemsetAsync(ctx->d_queue.p + 1, 0, sizeof(int), s));
     VX_LAUNCH(ctx, launch_step_resident(a, grid, threads, smem, s));
     return SIM_OK;
 }
@@ -464,11 +571,12 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
     VX_CK(ctx->d_sc.ensure(n_steps));
     VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->step, n_steps,
                               ctx->d_sc.p, s));
-    if (ctx->max_corner > kResidentMaxMass || ctx->p.path == SIM_PATH_STREAMED)
+    if (ctx->max_corner > kResidentMaxCorner || ctx->p.path == SIM_PATH_STREAMED)
         return fail(SIM_EINVAL, "streamed path not available for this population");
     cudaEvent_t ev[2];
     if (sim_status st = timing_pair(ctx, ev)) return st;
     VX_CK(cudaEventRecord(ev[0], s));
+    if (sim_status st = step_lattice(ctx, n_steps)) return st;
     if (sim_status st = step_resident(ctx, n_steps)) return st;
     VX_CK(cudaEventRecord(ev[1], s));
     ctx->step += n_steps;
@@ -483,7 +591,8 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem)
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     double* dst = mem == SIM_MEM_DEVICE ? out : ctx->d_fit.p;
-    VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_x.p, ctx->d_x0.p, (float)ctx->p.dead_bound, dst, s));
+    VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_mass_corner.p, ctx->d_x.p, ctx->d_x0.p,
+                                  (float)ctx->p.dead_bound, dst, s));
     if (mem == SIM_MEM_HOST) return copy_out(out, ctx->d_fit.p, sizeof(double) * ctx->P, mem, s);
     return SIM_OK;
 }
@@ -565,7 +674,8 @@ sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* m
     for (int i = 0; i < 2; ++i) {
         if (!outs[i]) continue;
         float* dst = mem == SIM_MEM_DEVICE ? outs[i] : ctx->d_compact.p;
-        VX_LAUNCH(ctx, launch_compact_state(ctx->view(), srcs[i], adds[i], dst, ctx->d_tmp_off.p, s));
+        VX_LAUNCH(ctx, launch_compact_state(ctx->view(), ctx->d_mass_corner.p, srcs[i], adds[i], dst,
+                                            ctx->d_tmp_off.p, s));
         if (mem == SIM_MEM_HOST)
             if (sim_status st = copy_out(outs[i], ctx->d_compact.p, sizeof(float) * 3 * Mt, mem, s)) return st;
     }

@@ -24,7 +24,7 @@ constexpr int kOut = 6;
 constexpr int kOffW1 = 0, kOffB1 = 16384, kOffW2 = 16448, kOffB2 = 20544, kOffW3 = 20608,
               kOffB3 = 20992;
 constexpr int kMaxAxis = 64;          // largest grid extent per axis
-constexpr int kResidentMaxMass = 16383;  // packed 14-bit mass indices on the resident path
+constexpr int kResidentMaxCorner = 16383;  // packed 14-bit corner ids on the resident path
 
 // The 13 lattice directions (dx, dy, dz) of springs from a corner to a larger corner id, in
 // increasing (dz, dy, dx) order: (1,0,0) (-1,1,0) (0,1,0) (1,1,0) (-1,-1,1) (0,-1,1) (1,-1,1)
@@ -91,21 +91,25 @@ cudaError_t launch_mlp_query_simt(int P, int Q, const void* pe_bf16, const float
 cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, const float* w,
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
-                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x0, float4* x,
-                            float4* v, double* x0c, int* status, int max_threads, cudaStream_t s);
+                            int2* spr_ab, float4* spr_p, float4* spr_pack, uint32_t* cflags,
+                            float* prm, float4* x0, float4* x, float4* v, double* x0c, int* status,
+                            int max_threads, cudaStream_t s);
 
 cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, float2* out,
                                 cudaStream_t s);
 
 struct ResidentArgs {
     PopView pv;
-    const float4* spr_pack;  // packed springs (k, alpha L0, beta L0, a | b << 14 | dir << 28)
-    float4* x;               // displacement from the rest lattice, rest height in .w
+    const float4* spr_pack;  // packed springs (k, alpha L0, beta L0, a | b << 14 | dir << 28),
+                             // a and b corner ids
+    const uint32_t* cflags;  // per corner: bit 31 set where a mass sits
+    float4* x;               // per corner: displacement from the rest lattice, rest height in .w
     float4* v;
     const float2* sc;        // sin / cos of w t per step of this call
     int nsteps;
     StepConst c;
-    const int* order;        // robot processing order (longest first) or NULL
+    const int* order;        // robots to process, longest first
+    int n_robots;            // entries of order
     int* queue;              // work counter (zeroed by the launcher) or NULL for static split
     int max_mass;            // smem layout: masses per robot slot
     int max_spring_smem;     // springs cached in shared memory per robot
@@ -116,17 +120,37 @@ struct ResidentArgs {
 };
 cudaError_t launch_step_resident(const ResidentArgs& a, int grid, int threads, size_t smem,
                                  cudaStream_t s);
+
+// Lattice-gather path (deterministic): work items of robots of one size class.
+struct LatticeArgs {
+    PopView pv;
+    const uint32_t* cflags;  // per corner: forward mask bits 0..12, backward 16..28, mass bit 31
+    const float* prm;        // per robot at 39 * moff: [3][13][C] (k, alpha L0, beta L0)
+    float4* u;               // per corner displacement (rest height in .w)
+    float4* v;               // per corner velocity
+    const float2* sc;        // sin / cos of w t per step of this call
+    int nsteps;
+    StepConst c;
+    const int4* items;       // (first robot in item_robots, robots, threads per robot, 0)
+    const int* item_robots;
+    int n_items;
+    int* queue;              // work counter, zeroed before the launch
+};
+int lattice_max_threads();
+constexpr int kLatticeSlotFloats = 42;   // shared floats per corner slot: u (3) + forces (39)
+cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
+                                cudaStream_t s);
 size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);
 
-cudaError_t launch_fitness(PopView pv, const float4* u, const float4* x0, float dead_bound,
-                           double* out, cudaStream_t s);
+cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, const float4* x0,
+                           float dead_bound, double* out, cudaStream_t s);
 
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s);
 cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
                                 int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
                                 int* parents, uint8_t* mask, cudaStream_t s);
 
-cudaError_t launch_compact_state(PopView pv, const float4* src, const float4* add, float* dst,
-                                 const int64_t* dst_off, cudaStream_t s);
+cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float4* src,
+                                 const float4* add, float* dst, const int64_t* dst_off, cudaStream_t s);
 
 }  // namespace vx

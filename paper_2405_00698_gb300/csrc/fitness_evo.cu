@@ -15,8 +15,8 @@ namespace {
 constexpr int kFitThreads = 256;
 
 __global__ void __launch_bounds__(kFitThreads)
-k_fitness(PopView pv, const float4* __restrict__ u, const float4* __restrict__ x0,
-          float dead_bound, double* __restrict__ out)
+k_fitness(PopView pv, const int* __restrict__ mass_corner, const float4* __restrict__ u,
+          const float4* __restrict__ x0, float dead_bound, double* __restrict__ out)
 {
     __shared__ double sh_sum[kFitThreads / 32];
     __shared__ int sh_dead;
@@ -28,7 +28,8 @@ k_fitness(PopView pv, const float4* __restrict__ u, const float4* __restrict__ x
     double s = 0.0;
     int dead = 0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 d = u[mo + m], r0 = x0[mo + m];
+        const int64_t c = mo + mass_corner[mo + m];
+        const float4 d = u[c], r0 = x0[c];
         const float px = r0.x + d.x, py = r0.y + d.y, pz = r0.z + d.z;
         if (!(fabsf(px) <= dead_bound) || !(fabsf(py) <= dead_bound) || !(fabsf(pz) <= dead_bound))
             dead = 1;   // catches NaN too
@@ -160,16 +161,18 @@ __global__ void k_sincos(double omega, double dt, int64_t step0, int n, float2* 
 
 // Gather a per-mass float4 state into packed float[3] rows; `add` (optional) is added first
 // (rest lattice + displacement = position).
-__global__ void k_compact(PopView pv, const float4* __restrict__ src, const float4* __restrict__ add,
+__global__ void k_compact(PopView pv, const int* __restrict__ mass_corner,
+                          const float4* __restrict__ src, const float4* __restrict__ add,
                           float* __restrict__ dst, const int64_t* __restrict__ dst_off)
 {
     const int r = blockIdx.x;
     const int M = pv.n_mass[r];
     const int64_t mo = pv.moff[r], d = dst_off[r];
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        float4 p = src[mo + m];
+        const int64_t c = mo + mass_corner[mo + m];
+        float4 p = src[c];
         if (add) {
-            const float4 q = add[mo + m];
+            const float4 q = add[c];
             p.x += q.x; p.y += q.y; p.z += q.z;
         }
         dst[3 * (d + m) + 0] = p.x;
@@ -180,11 +183,11 @@ __global__ void k_compact(PopView pv, const float4* __restrict__ src, const floa
 
 }  // namespace
 
-cudaError_t launch_fitness(PopView pv, const float4* u, const float4* x0, float dead_bound,
-                           double* out, cudaStream_t s)
+cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, const float4* x0,
+                           float dead_bound, double* out, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
-    k_fitness<<<pv.P, kFitThreads, 0, s>>>(pv, u, x0, dead_bound, out);
+    k_fitness<<<pv.P, kFitThreads, 0, s>>>(pv, mass_corner, u, x0, dead_bound, out);
     return cudaGetLastError();
 }
 
@@ -216,11 +219,11 @@ cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, f
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_state(PopView pv, const float4* src, const float4* add, float* dst,
-                                 const int64_t* dst_off, cudaStream_t s)
+cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float4* src,
+                                 const float4* add, float* dst, const int64_t* dst_off, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
-    k_compact<<<pv.P, 256, 0, s>>>(pv, src, add, dst, dst_off);
+    k_compact<<<pv.P, 256, 0, s>>>(pv, mass_corner, src, add, dst, dst_off);
     return cudaGetLastError();
 }
 

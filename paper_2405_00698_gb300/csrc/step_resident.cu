@@ -1,9 +1,10 @@
 // Resident time stepping (Section II-C: one thread per spring for the force update, one thread
 // per mass for the integration; Table II constants).  One thread block owns one robot at a
 // time and keeps its whole state in shared memory for every step of the call:
-//   u       float4[M]   displacement from the rest lattice (ux, uy, uz) and rest height z0
-//   v       float4[M]   velocity
-//   F       float[3][M] accumulated by the spring phase, consumed and cleared by the mass phase
+//   u       float4[C]   per grid corner: displacement from the rest lattice (ux, uy, uz) and
+//                       rest height z0 (corners without a mass are carried along unchanged)
+//   v       float4[C]   velocity
+//   F       float[3][C] accumulated by the spring phase, consumed and cleared by the mass phase
 //   springs float4[S]   when they fit, otherwise streamed from device memory (L2) every step:
 //                       (k, alpha L0, beta L0, a | b << 14 | direction << 28), ordered by
 //                       direction then a, so a warp's atomic updates hit distinct masses.
@@ -57,13 +58,15 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
     for (;;) {
         if (tid == 0) {
             int idx = a.queue ? atomicAdd(a.queue, 1) : blockIdx.x + iter * gridDim.x;
-            sh_robot = idx < a.pv.P ? (a.order ? a.order[idx] : idx) : -1;
+            sh_robot = idx < a.n_robots ? a.order[idx] : -1;
         }
         ++iter;
         __syncthreads();
         const int r = sh_robot;
         if (r < 0) break;
-        const int M = a.pv.n_mass[r], S = a.pv.n_spring[r];
+        const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
+        const int M = (nx + 1) * (ny + 1) * (nz + 1);   // corners: state is indexed by corner
+        const int S = a.pv.n_spring[r];
         const int64_t mo = a.pv.moff[r], so = a.pv.soff[r];
         for (int m = tid; m < M; m += T) {
             L.u[m] = a.x[mo + m];
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             }
             __syncthreads();
             for (int m = tid; m < M; m += T) {
+                if (!(a.cflags[mo + m] >> 31)) continue;   // a corner without a mass
                 float fx = L.fx[m], fy = L.fy[m], fz = L.fz[m] - c.weight;
                 L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
                 float4 u = L.u[m], v = L.vel[m];

@@ -107,8 +107,8 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
            const float* __restrict__ w_all, const float* __restrict__ kappa_all,
            const float* __restrict__ phi_all, MatConst mc, double edge, int* label_all,
            int* count_all, int* corner_mass_all, int* mass_corner_all, int2* spr_ab_all,
-           float4* spr_p_all, float4* spr_pack_all, float4* x0_all, float4* x_all,
-           float4* v_all, double* x0c, int* status)
+           float4* spr_p_all, float4* spr_pack_all, uint32_t* cflags_all, float* prm_all,
+           float4* x0_all, float4* x_all, float4* v_all, double* x0c, int* status)
 {
     __shared__ int sh_scan[32];
     __shared__ int sh_changed;
@@ -206,21 +206,21 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
     }
     if (tid == 0) { sh_zmin = INT_MAX; pv.n_mass[r] = M; }
     __syncthreads();
-    // 6. initial pose: lattice with the lowest mass at z = 0, at rest.  The state is kept as
-    //    the displacement u from this rest lattice (small, hence precise in float32), with the
-    //    rest height z0 of the mass in the fourth lane: u = (ux, uy, uz, z0).
+    // 6. initial pose: lattice with the lowest mass at z = 0, at rest.  State is indexed by
+    //    corner (all corners of the grid; corners without a mass carry no spring).  It is kept
+    //    as the displacement u from this rest lattice (small, hence precise in float32), with
+    //    the rest height z0 in the fourth lane: u = (ux, uy, uz, z0).
     for (int m = tid; m < M; m += T) atomicMin(&sh_zmin, mass_corner[m] / (cx * cy));
     __syncthreads();
-    const int zmin = sh_zmin;
+    const int zmin = sh_zmin == INT_MAX ? 0 : sh_zmin;
     double xs = 0.0;
-    for (int m = tid; m < M; m += T) {
-        int c = mass_corner[m];
+    for (int c = tid; c < C; c += T) {
         int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
         float4 p = make_float4((float)(ci * edge), (float)(cj * edge), (float)((ck - zmin) * edge), 0.f);
-        x0_all[mo + m] = p;
-        x_all[mo + m] = make_float4(0.f, 0.f, 0.f, p.z);
-        v_all[mo + m] = make_float4(0.f, 0.f, 0.f, 0.f);
-        xs += (double)p.x;
+        x0_all[mo + c] = p;
+        x_all[mo + c] = make_float4(0.f, 0.f, 0.f, p.z);
+        v_all[mo + c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (corner_mass[c] >= 0) xs += (double)p.x;
     }
     for (int o = 16; o > 0; o >>= 1) xs += __shfl_down_sync(0xffffffffu, xs, o);
     if ((tid & 31) == 0) sh_sum[tid >> 5] = xs;
@@ -267,11 +267,11 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
         }
     }
     if (tid == 0) pv.n_spring[r] = S;
-    if (!spr_pack_all) return;
-    // 8. the resident path's copy, direction-major: all springs of direction 0 by ascending a,
-    //    then direction 1, ...  Within a warp the endpoints of one direction are distinct masses,
+    if (spr_pack_all) {
+    // 8. the atomic kernel's copy, direction-major: all springs of direction 0 by ascending
+    //    corner, then direction 1, ...  Within a warp the endpoints of one direction are distinct,
     //    so the force accumulation does not collide.  Packed as (k, alpha L0, beta L0,
-    //    a | b << 14 | direction << 28).
+    //    corner a | corner b << 14 | direction << 28).
     int dbase = 0;
     for (int d = 0; d < 13; ++d) {
         int nd = 0;
@@ -297,12 +297,53 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
             if (spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, &k, &al,
                                  &be) == 0)
                 continue;
-            int b = corner_mass[bi + cx * (bj + cy * bk)];
-            unsigned bits = (unsigned)m | ((unsigned)b << 14) | ((unsigned)d << 28);
+            const unsigned ca = (unsigned)c, cb = (unsigned)(bi + cx * (bj + cy * bk));
+            unsigned bits = ca | (cb << 14) | ((unsigned)d << 28);
             spr_pack_all[so + pos] = make_float4(k, al * L0, be * L0, __uint_as_float(bits));
             ++pos;
         }
         dbase += total;
+    }
+    }
+    if (!cflags_all) return;
+    // 9. the lattice kernel's tables, indexed by corner: forward-spring mask (bits 0..12),
+    //    backward-spring mask (bits 16..28: a spring from corner c - offset(d) to c), mass bit 31,
+    //    and the forward springs' (k, alpha L0, beta L0) as [3][13][C] planes.
+    uint32_t* cflags = cflags_all + mo;
+    float* prm = prm_all + 39 * mo;
+    __syncthreads();
+    for (int c = tid; c < C; c += T) {
+        int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
+        uint32_t fl = corner_mass[c] >= 0 ? 0x80000000u : 0u;
+        for (int d = 0; d < 13; ++d) {
+            float k = 0.f, al = 0.f, be = 0.f;
+            int bi = ci + c_dir[d][0], bj = cj + c_dir[d][1], bk = ck + c_dir[d][2];
+            if (corner_mass[c] >= 0 && bi >= 0 && bj >= 0 && bi < cx && bj < cy && bk < cz &&
+                spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, &k, &al, &be) > 0) {
+                fl |= 1u << d;
+                const int cls = (c_dir[d][0] != 0) + (c_dir[d][1] != 0) + (c_dir[d][2] != 0);
+                const float L0 = (float)(cls == 1 ? e1 : (cls == 2 ? e2 : e3));
+                al *= L0;
+                be *= L0;
+            } else {
+                k = 0.f; al = 0.f; be = 0.f;
+            }
+            prm[(0 * 13 + d) * C + c] = k;
+            prm[(1 * 13 + d) * C + c] = al;
+            prm[(2 * 13 + d) * C + c] = be;
+        }
+        cflags[c] = fl;
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += T) {
+        int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
+        uint32_t bw = 0;
+        for (int d = 0; d < 13; ++d) {
+            int ai = ci - c_dir[d][0], aj = cj - c_dir[d][1], ak = ck - c_dir[d][2];
+            if (ai < 0 || aj < 0 || ak < 0 || ai >= cx || aj >= cy) continue;
+            if ((cflags[ai + cx * (aj + cy * ak)] >> d) & 1u) bw |= 1u << (16 + d);
+        }
+        cflags[c] |= bw;
     }
 }
 
@@ -311,14 +352,15 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
 cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, const float* w,
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
-                            int2* spr_ab, float4* spr_p, float4* spr_pack, float4* x0, float4* x,
-                            float4* v, double* x0c, int* status, int max_threads, cudaStream_t s)
+                            int2* spr_ab, float4* spr_p, float4* spr_pack, uint32_t* cflags,
+                            float* prm, float4* x0, float4* x, float4* v, double* x0c, int* status,
+                            int max_threads, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
     int T = max_threads > 0 && max_threads < kTopoThreads ? max_threads : kTopoThreads;
     k_topology<<<pv.P, T, 0, s>>>(pv, mat_raw, mat, w, kappa, phi, mc, edge, label, count,
-                                  corner_mass, mass_corner, spr_ab, spr_p, spr_pack, x0, x, v,
-                                  x0c, status);
+                                  corner_mass, mass_corner, spr_ab, spr_p, spr_pack, cflags, prm,
+                                  x0, x, v, x0c, status);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ def decode_gpu(vs, genomes, B, dims, kernel):
     return sim, vox
 
 
-def check_decode(orc, genomes, B, dims, vox, max_band_frac=0.05):
+def check_decode(orc, genomes, B, dims, vox, max_band_frac=0.15):
     Q = int(np.prod(dims))
     banded = 0
     for g in range(genomes.shape[0]):

@@ -198,3 +198,33 @@ def test_invalid_inputs_rejected(vs):
     with pytest.raises(vs.VoxsimError):
         sim.set_population([[65, 1, 1]], np.zeros(65, np.uint8))
     sim.close()
+
+
+def test_gather_stepping_is_bit_reproducible(vs):
+    """The lattice-gather path sums every mass's forces in a fixed order: two runs agree bitwise."""
+    pop = W.population_uneven(30, seed=24, sizes=(2, 4, 6, 8))
+    out = []
+    for _ in range(2):
+        sim = vs.Simulator(PHYS, accumulate=vs.ACC_GATHER)
+        sim.set_population_from(pop)
+        sim.step(700)
+        x, v, _ = sim.state()
+        out.append((x, v, sim.fitness()))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_atomic_path_matches_oracle(vs, orc):
+    """Every robot on the shared-memory-atomic kernel (the path of robots with more corners than a
+    lattice block holds)."""
+    pop = W.population_uneven(20, seed=25, sizes=(3, 5, 8, 12))
+    g, ref = run_both(vs, orc, pop, PHYS, 500, accumulate=vs.ACC_ATOMIC)
+    check_population(orc, pop, PHYS, 500, g["f"], g["x"], g["off"], ref)
+
+
+def test_gather_mode_rejects_robots_beyond_the_lattice_block(vs):
+    sim = vs.Simulator(PHYS, accumulate=vs.ACC_GATHER)
+    with pytest.raises(vs.VoxsimError):
+        sim.set_population([[12, 12, 12]], np.full(1728, 4, np.uint8))
+    sim.close()
