@@ -133,6 +133,14 @@ struct voxsim_ctx {
     // evolution scratch
     DevBuf<int> d_order;
     DevBuf<float> d_gcopy;
+    // checkpointing and the adjoint
+    int ckpt_every = 0;          // K (0 = off)
+    bool rec_valid = false;      // a recorded call is available
+    int64_t rec_step0 = 0;
+    int rec_n = 0;
+    DevBuf<float4> d_ckpt_u, d_ckpt_v, d_rec_u;
+    DevBuf<float2> d_rec_f, d_sc_rec;
+    DevBuf<float> d_gk, d_ga, d_gb;
     // timing: one event pair per stepping call since the last sim_get_timing
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
@@ -408,6 +416,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         if (sim_status st = build_work_items(ctx)) return st;
     }
     ctx->step = 0;
+    ctx->rec_valid = false;
     ctx->have_pop = true;
     return SIM_OK;
 }
@@ -510,8 +519,17 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     a.item_robots = ctx->d_item_robots.p;
     a.n_items = ctx->n_items;
     a.queue = ctx->d_queue.p;
+    if (ctx->ckpt_every > 0) {
+        const int nseg = (n + ctx->ckpt_every - 1) / ctx->ckpt_every;
+        VX_CK(ctx->d_ckpt_u.ensure((size_t)nseg * ctx->M_cap));
+        VX_CK(ctx->d_ckpt_v.ensure((size_t)nseg * ctx->M_cap));
+        a.ckpt_u = ctx->d_ckpt_u.p;
+        a.ckpt_v = ctx->d_ckpt_v.p;
+        a.ckpt_stride = ctx->M_cap;
+        a.ckpt_every = ctx->ckpt_every;
+    }
     const int threads = lattice_max_threads();
-    const size_t smem = sizeof(float) * kLatticeSlotFloats * (size_t)threads;
+    const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
     const int grid = std::min(ctx->n_items, ctx->num_sms);
     VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), ctx->stream));
     VX_LAUNCH(ctx, launch_step_lattice(a, grid, threads, smem, ctx->stream));
@@ -573,12 +591,22 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
                               ctx->d_sc.p, s));
     if (ctx->max_corner > kResidentMaxCorner || ctx->p.path == SIM_PATH_STREAMED)
         return fail(SIM_EINVAL, "streamed path not available for this population");
+    if (ctx->ckpt_every > 0 && ctx->n_big > 0)
+        return fail(SIM_EINVAL, "checkpointing for the adjoint needs robots of at most %d corners",
+                    lattice_max_threads());
     cudaEvent_t ev[2];
     if (sim_status st = timing_pair(ctx, ev)) return st;
     VX_CK(cudaEventRecord(ev[0], s));
     if (sim_status st = step_lattice(ctx, n_steps)) return st;
     if (sim_status st = step_resident(ctx, n_steps)) return st;
     VX_CK(cudaEventRecord(ev[1], s));
+    if (ctx->ckpt_every > 0) {
+        ctx->rec_valid = true;
+        ctx->rec_step0 = ctx->step;
+        ctx->rec_n = n_steps;
+    } else {
+        ctx->rec_valid = false;
+    }
     ctx->step += n_steps;
     return SIM_OK;
 }
@@ -630,13 +658,62 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
 {
     if (sim_status st = check_ctx(ctx)) return st;
     if (k_steps < 0) return fail(SIM_EINVAL, "k_steps must be >= 0");
-    return fail(SIM_ESTATE, "checkpointing is not available in this build");
+    if (k_steps > 0 && ctx->p.accumulate == SIM_ACC_ATOMIC)
+        return fail(SIM_EINVAL, "checkpointing needs the bit-reproducible stepping (not SIM_ACC_ATOMIC)");
+    ctx->ckpt_every = k_steps;
+    ctx->rec_valid = false;
+    return SIM_OK;
 }
 
-sim_status sim_backward(voxsim_ctx* ctx, const double*, float*, float*, float*)
+sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa, float* g_phi)
 {
     if (sim_status st = check_ctx(ctx)) return st;
-    return fail(SIM_ESTATE, "no recorded forward run");
+    if (!ctx->have_pop || !ctx->rec_valid) return fail(SIM_ESTATE, "no recorded forward run");
+    if (ctx->P > 0 && (!dL_df || !g_w || !g_kappa || !g_phi)) return fail(SIM_EINVAL, "null argument");
+    if (ctx->P == 0 || ctx->rec_n == 0) return SIM_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int K = ctx->ckpt_every;
+    const size_t V = ctx->V_tot;
+    VX_CK(ctx->d_gk.ensure(V)); VX_CK(ctx->d_ga.ensure(V)); VX_CK(ctx->d_gb.ensure(V));
+    VX_CK(cudaMemsetAsync(ctx->d_gk.p, 0, sizeof(float) * V, s));
+    VX_CK(cudaMemsetAsync(ctx->d_ga.p, 0, sizeof(float) * V, s));
+    VX_CK(cudaMemsetAsync(ctx->d_gb.p, 0, sizeof(float) * V, s));
+    VX_CK(ctx->d_sc_rec.ensure(ctx->rec_n));
+    VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->rec_step0,
+                                       ctx->rec_n, ctx->d_sc_rec.p, s));
+    const int threads = lattice_max_threads();
+    const int grid = std::min(ctx->n_items, ctx->num_sms);
+    VX_CK(ctx->d_rec_u.ensure((size_t)grid * K * threads));
+    VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
+    AdjointArgs a{};
+    a.pv = ctx->view();
+    a.cflags = ctx->d_cflags.p;
+    a.prm = ctx->d_prm.p;
+    a.mat = ctx->d_mat.p;
+    a.ckpt_u = ctx->d_ckpt_u.p;
+    a.ckpt_v = ctx->d_ckpt_v.p;
+    a.ckpt_stride = ctx->M_cap;
+    a.K = K;
+    a.nsteps = ctx->rec_n;
+    a.sc = ctx->d_sc_rec.p;
+    a.c = ctx->stepconst();
+    a.dL_df = dL_df;
+    a.items = ctx->d_items.p;
+    a.item_robots = ctx->d_item_robots.p;
+    a.n_items = ctx->n_items;
+    a.queue = ctx->d_queue.p;
+    a.rec_u = ctx->d_rec_u.p;
+    a.rec_f = ctx->d_rec_f.p;
+    a.g_k = ctx->d_gk.p;
+    a.g_a = ctx->d_ga.p;
+    a.g_b = ctx->d_gb.p;
+    const size_t smem = sizeof(float) * kAdjointSlotFloats * (size_t)threads;
+    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+    VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
+    VX_LAUNCH(ctx, launch_adjoint_voxels(ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p, ctx->d_phi.p, ctx->matconst(),
+                                         ctx->d_gk.p, ctx->d_ga.p, ctx->d_gb.p, (int64_t)V, g_w, g_kappa, g_phi, s));
+    return SIM_OK;
 }
 
 sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs)

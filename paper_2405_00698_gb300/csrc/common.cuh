@@ -135,9 +135,47 @@ struct LatticeArgs {
     const int* item_robots;
     int n_items;
     int* queue;              // work counter, zeroed before the launch
+    // checkpoints for the adjoint (NULL when off): state at steps 0, K, 2K, ... of the call
+    float4* ckpt_u;
+    float4* ckpt_v;
+    int64_t ckpt_stride;     // corners per checkpoint (sum over robots)
+    int ckpt_every;          // K
 };
+
+// Adjoint of the lattice stepping over one recorded call (see adjoint.cu).
+struct AdjointArgs {
+    PopView pv;
+    const uint32_t* cflags;
+    const float* prm;
+    const uint8_t* mat;      // kept material per voxel
+    const float4* ckpt_u;
+    const float4* ckpt_v;
+    int64_t ckpt_stride;
+    int K;
+    int nsteps;              // steps of the recorded call
+    const float2* sc;        // sin / cos of w t per step of the recorded call
+    StepConst c;
+    const double* dL_df;     // [P]
+    const int4* items;
+    const int* item_robots;
+    int n_items;
+    int* queue;
+    float4* rec_u;           // per block: [K][block threads] state and contact mode per step
+    float2* rec_f;           // per block: [K][block threads] horizontal force before contact
+    float* g_k;              // per voxel: dL/dk_v, dL/d(alpha_v), dL/d(beta_v) accumulators
+    float* g_a;
+    float* g_b;
+};
+constexpr int kAdjointSlotVec4 = 2;     // float4 per corner slot: u, adjoint force
+constexpr int kAdjointSlotFloats = 8 + 39;   // + 39 parameter floats per corner
+cudaError_t launch_adjoint_lattice(const AdjointArgs& a, int grid, int threads, size_t smem,
+                                   cudaStream_t s);
+cudaError_t launch_adjoint_voxels(const uint8_t* mat, const float* w, const float* kappa,
+                                  const float* phi, MatConst mc, const float* g_k, const float* g_a,
+                                  const float* g_b, int64_t n, float* g_w, float* g_kappa,
+                                  float* g_phi, cudaStream_t s);
 int lattice_max_threads();
-constexpr int kLatticeSlotFloats = 42;   // shared floats per corner slot: u (3) + forces (39)
+constexpr int kLatticeSlotVec4 = 14;     // shared float4 per corner slot: u + 13 force planes
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s);
 size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);

@@ -1,0 +1,123 @@
+// Per-spring and per-mass arithmetic of one time step (Section II-C; Table II constants), shared
+// by the lattice stepping kernel, the checkpoint replay of the adjoint and the adjoint itself.
+// Every operation is an explicitly rounded intrinsic, so the compiler cannot contract or reorder
+// it differently in different kernels: a replay from a checkpoint reproduces the forward run bit
+// for bit, and the contact modes the adjoint holds fixed are the ones the forward run took.
+#pragma once
+
+#include "common.cuh"
+
+namespace vx {
+
+// Force on the first endpoint a of a spring (the second endpoint b receives its negative).
+//   du = u_b - u_a (displacements from the rest lattice), d = d0 + du with d0 the lattice
+//   offset, l = |d|; extension without cancellation e0 = l - L0 = (2 d0.du + du.du) / (l + L0);
+//   actuated rest length L = L0 + act with act = (alpha L0) sin(w t) + (beta L0) cos(w t);
+//   f = k (l - L) d / l.
+// Outputs the force g (on a), and for the adjoint the unit-free pieces ext = l - L and inv = 1/l.
+struct SpringEval {
+    float dx, dy, dz;   // spring vector a -> b
+    float inv;          // 1 / l
+    float ext;          // l - L
+    float gx, gy, gz;   // force on a
+};
+
+// Spring along lattice direction D (compile-time): the zero components of the lattice offset d0
+// drop out of the arithmetic statically.
+template <int D>
+__device__ __forceinline__ SpringEval spring_eval_dir(float dux, float duy, float duz, float edge,
+                                                      float L0, float k, float pa, float pb, float sn,
+                                                      float cs)
+{
+    constexpr int ox = lattice_dir(D, 0), oy = lattice_dir(D, 1), oz = lattice_dir(D, 2);
+    SpringEval e;
+    e.dx = ox ? __fadd_rn(ox > 0 ? edge : -edge, dux) : dux;
+    e.dy = oy ? __fadd_rn(oy > 0 ? edge : -edge, duy) : duy;
+    e.dz = oz ? __fadd_rn(oz > 0 ? edge : -edge, duz) : duz;
+    const float l2 = __fmaf_rn(e.dz, e.dz, __fmaf_rn(e.dy, e.dy, __fmul_rn(e.dx, e.dx)));
+    e.inv = rsqrtf(l2);
+    const float l = __fmul_rn(l2, e.inv);
+    // d0 . du over the non-zero components of d0 (each +-edge)
+    float d0du = 0.0f;
+    if (ox) d0du = __fmaf_rn(ox > 0 ? edge : -edge, dux, d0du);
+    if (oy) d0du = __fmaf_rn(oy > 0 ? edge : -edge, duy, d0du);
+    if (oz) d0du = __fmaf_rn(oz > 0 ? edge : -edge, duz, d0du);
+    const float dudu = __fmaf_rn(duz, duz, __fmaf_rn(duy, duy, __fmul_rn(dux, dux)));
+    const float num = __fmaf_rn(2.0f, d0du, dudu);
+    const float act = __fmaf_rn(pa, sn, __fmul_rn(pb, cs));
+    e.ext = __fsub_rn(__fdividef(num, __fadd_rn(l, L0)), act);
+    const float f = l2 > 1e-30f ? __fmul_rn(__fmul_rn(k, e.ext), e.inv) : 0.0f;
+    e.gx = __fmul_rn(f, e.dx);
+    e.gy = __fmul_rn(f, e.dy);
+    e.gz = __fmul_rn(f, e.dz);
+    return e;
+}
+
+// Rest length of lattice direction D (compile-time class: edge, face or body diagonal).
+template <int D>
+__device__ __forceinline__ float lattice_rest(const StepConst& c)
+{
+    constexpr int cls = (lattice_dir(D, 0) != 0) + (lattice_dir(D, 1) != 0) + (lattice_dir(D, 2) != 0);
+    return cls == 1 ? c.edge : (cls == 2 ? c.edge_sqrt2 : c.edge_sqrt3);
+}
+
+// Corner-index offset of lattice direction D on a grid with X corners per row and XY per layer.
+template <int D>
+__device__ __forceinline__ int lattice_offset(int X, int XY)
+{
+    return lattice_dir(D, 0) + X * lattice_dir(D, 1) + XY * lattice_dir(D, 2);
+}
+
+// Compile-time loop over the 13 directions: f(std::integral_constant-like tag).
+template <int D>
+struct DirTag {
+    static constexpr int value = D;
+};
+template <int D = 0, class F>
+__device__ __forceinline__ void for_each_dir(F&& f)
+{
+    if constexpr (D < 13) {
+        f(DirTag<D>{});
+        for_each_dir<D + 1>(f);
+    }
+}
+
+// Contact modes of a mass in one step.
+enum : unsigned { kFree = 0u, kStick = 1u, kSlip = 2u };
+
+// Gravity, ground contact with static / kinetic friction, and the semi-implicit Euler update of
+// one mass, given the summed spring force F.  Returns the contact mode.
+//   below the ground (z = z0 + uz < 0): normal force F_n = k_g (-z) added to F_z; with
+//   F_h = (F_x, F_y): stick (|F_h| <= mu_s F_n) zeroes F_h and the horizontal velocity, slip
+//   removes mu_k F_n along F_h;
+//   v <- c (v + dt F / m), u <- u + dt v.
+__device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, float Fy, float Fz,
+                                                const StepConst& c)
+{
+    unsigned mode = kFree;
+    Fz = __fsub_rn(Fz, c.weight);
+    const float z = __fadd_rn(u.w, u.z);
+    if (c.ground_on && z < 0.f) {
+        const float fn = __fmul_rn(c.k_ground, -z);
+        Fz = __fadd_rn(Fz, fn);
+        const float fh = __fsqrt_rn(__fmaf_rn(Fy, Fy, __fmul_rn(Fx, Fx)));
+        if (fh <= __fmul_rn(c.mu_s, fn)) {
+            mode = kStick;
+            Fx = 0.f; Fy = 0.f; v.x = 0.f; v.y = 0.f;
+        } else {
+            mode = kSlip;
+            const float s = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(c.mu_k, fn), fh));
+            Fx = __fmul_rn(Fx, s);
+            Fy = __fmul_rn(Fy, s);
+        }
+    }
+    v.x = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fx, v.x));
+    v.y = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fy, v.y));
+    v.z = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fz, v.z));
+    u.x = __fmaf_rn(c.dt, v.x, u.x);
+    u.y = __fmaf_rn(c.dt, v.y, u.y);
+    u.z = __fmaf_rn(c.dt, v.z, u.z);
+    return mode;
+}
+
+}  // namespace vx

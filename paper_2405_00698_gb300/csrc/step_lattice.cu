@@ -13,11 +13,12 @@
 //            registers and publishes its new u.
 // Two block barriers per step, no atomics, and a fixed summation order (own forward springs by
 // direction, then backward springs by direction): bit-reproducible.
-// Shared memory per robot slot: u as 3 float planes of C corners + 13 x 3 force planes.
+// Shared memory per robot slot: u (float4 per corner) + 13 float4 force planes.
 // The state is the displacement from the rest lattice (rest height z0 in u.w), so a spring
 // vector is d0 + (u_b - u_a) with d0 the exact lattice offset and the extension is formed without
 // cancellation: l - L0 = (2 d0.du + du.du) / (l + L0).
 #include "common.cuh"
+#include "physics.cuh"
 
 namespace vx {
 namespace {
@@ -31,7 +32,7 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(16) float4 sm4[];
     __shared__ int sh_item[4];
     const int tid = threadIdx.x;
     const StepConst c = a.c;
@@ -56,85 +57,57 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
-            // shared-memory slot of this group (gthreads corners): u planes then 13 x 3 force planes
-            const int sc_n = gthreads;
-            float* slot = sm + (size_t)group * kLatticeSlotFloats * sc_n;
-            float* sx = slot;
-            float* sy = sx + sc_n;
-            float* sz = sy + sc_n;
-            float* fb = sz + sc_n;   // plane (3d + axis) at fb + (3d + axis) * sc_n
+            // shared-memory slot of this group (S = gthreads corners): u, then 13 force planes
+            const int S = gthreads;
+            float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
+            float4* fb = su + S;               // plane d at fb + d * S: force on b of spring (c, d)
             const int cidx = lt;
             const bool in = cidx < C;
-            uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
+            const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
             float pk[13], pa[13], pb[13];
             const float* prm = a.prm + 39 * mo;
-#pragma unroll
-            for (int d = 0; d < 13; ++d) {
+            for_each_dir([&](auto t) {
+                constexpr int d = decltype(t)::value;
                 const bool has = (fl >> d) & 1u;
                 pk[d] = has ? prm[(0 * 13 + d) * C + cidx] : 0.f;
                 pa[d] = has ? prm[(1 * 13 + d) * C + cidx] : 0.f;
                 pb[d] = has ? prm[(2 * 13 + d) * C + cidx] : 0.f;
-            }
+            });
             float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             const bool mass = (fl >> 31) & 1u;
-            if (in) { sx[cidx] = u.x; sy[cidx] = u.y; sz[cidx] = u.z; }
+            if (in) su[cidx] = u;
             group_sync(bar, gthreads);
             for (int n = 0; n < a.nsteps; ++n) {
+                if (a.ckpt_u && in && n % a.ckpt_every == 0) {   // state at the start of segment n / K
+                    const int64_t o = (int64_t)(n / a.ckpt_every) * a.ckpt_stride + mo + cidx;
+                    a.ckpt_u[o] = u;
+                    a.ckpt_v[o] = v;
+                }
                 const float2 sc = a.sc[n];
                 float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-                // phase A: forward springs
-#pragma unroll
-                for (int d = 0; d < 13; ++d) {
-                    if (!((fl >> d) & 1u)) continue;
-                    const int ox = lattice_dir(d, 0), oy = lattice_dir(d, 1), oz = lattice_dir(d, 2);
-                    const int nb = cidx + ox + X * oy + XY * oz;
-                    const float dux = sx[nb] - u.x, duy = sy[nb] - u.y, duz = sz[nb] - u.z;
-                    const float d0x = c.edge * ox, d0y = c.edge * oy, d0z = c.edge * oz;
-                    const int cls = (ox != 0) + (oy != 0) + (oz != 0);
-                    const float L0 = cls == 1 ? c.edge : (cls == 2 ? c.edge_sqrt2 : c.edge_sqrt3);
-                    const float dx = d0x + dux, dy = d0y + duy, dz = d0z + duz;
-                    const float l2 = dx * dx + dy * dy + dz * dz;
-                    const float inv = rsqrtf(l2);
-                    const float l = l2 * inv;
-                    const float num = 2.0f * (d0x * dux + d0y * duy + d0z * duz) + (dux * dux + duy * duy + duz * duz);
-                    const float ext = __fdividef(num, l + L0) - (pa[d] * sc.x + pb[d] * sc.y);
-                    const float f = l2 > 1e-30f ? pk[d] * ext * inv : 0.f;
-                    const float gx = f * dx, gy = f * dy, gz = f * dz;
-                    Fx += gx; Fy += gy; Fz += gz;
-                    fb[(3 * d + 0) * sc_n + cidx] = -gx;
-                    fb[(3 * d + 1) * sc_n + cidx] = -gy;
-                    fb[(3 * d + 2) * sc_n + cidx] = -gz;
-                }
+                // phase A: forward springs (c, c + offset(d))
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> d) & 1u)) return;
+                    const float4 ub = su[cidx + lattice_offset<d>(X, XY)];
+                    const SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
+                                                            __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c),
+                                                            pk[d], pa[d], pb[d], sc.x, sc.y);
+                    Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
+                    fb[d * S + cidx] = make_float4(-e.gx, -e.gy, -e.gz, 0.f);
+                });
                 group_sync(bar, gthreads);
-                // phase B: backward springs, then the mass update
-#pragma unroll
-                for (int d = 0; d < 13; ++d) {
-                    if (!((fl >> (16 + d)) & 1u)) continue;
-                    const int nb = cidx - (lattice_dir(d, 0) + X * lattice_dir(d, 1) + XY * lattice_dir(d, 2));
-                    Fx += fb[(3 * d + 0) * sc_n + nb];
-                    Fy += fb[(3 * d + 1) * sc_n + nb];
-                    Fz += fb[(3 * d + 2) * sc_n + nb];
-                }
+                // phase B: backward springs (c - offset(d), c), then the mass update
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> (16 + d)) & 1u)) return;
+                    const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];
+                    Fx = __fadd_rn(Fx, g.x); Fy = __fadd_rn(Fy, g.y); Fz = __fadd_rn(Fz, g.z);
+                });
                 if (mass) {
-                    Fz -= c.weight;
-                    const float z = u.w + u.z;
-                    if (c.ground_on && z < 0.f) {
-                        const float fn = c.k_ground * (-z);
-                        Fz += fn;
-                        const float fh = sqrtf(Fx * Fx + Fy * Fy);
-                        if (fh <= c.mu_s * fn) {
-                            Fx = 0.f; Fy = 0.f; v.x = 0.f; v.y = 0.f;
-                        } else {
-                            const float s2 = 1.0f - c.mu_k * fn / fh;
-                            Fx *= s2; Fy *= s2;
-                        }
-                    }
-                    v.x = c.damping * (v.x + c.dt_over_m * Fx);
-                    v.y = c.damping * (v.y + c.dt_over_m * Fy);
-                    v.z = c.damping * (v.z + c.dt_over_m * Fz);
-                    u.x += c.dt * v.x; u.y += c.dt * v.y; u.z += c.dt * v.z;
-                    sx[cidx] = u.x; sy[cidx] = u.y; sz[cidx] = u.z;
+                    mass_update(u, v, Fx, Fy, Fz, c);
+                    su[cidx] = u;
                 }
                 group_sync(bar, gthreads);
             }

@@ -259,3 +259,39 @@ class Simulator:
         _check(lib().evo_generation(self._h, _ptr(fitness)[0], _ptr(genomes_in)[0],
                                     _ptr(genomes_out)[0], int(P), int(G), C.byref(e),
                                     int(generation), _ptr(parents)[0], _ptr(mask)[0]))
+
+
+def fitness_function():
+    """torch.autograd.Function: fitness of a population under the per-voxel parametrisation
+    (materials, w, kappa, phi) after n steps, differentiable in (w, kappa, phi) through the
+    library's checkpointed adjoint.
+
+        f = fitness_function().apply(sim, dims, mats, w, kappa, phi, n_steps, k_ckpt)
+
+    mats (uint8) and w, kappa, phi (float32) are CUDA tensors over all voxels; f is float64 [P]."""
+    import torch
+
+    class _Fitness(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, sim, dims, mats, w, kappa, phi, n_steps, k_ckpt):
+            sim.set_checkpointing(int(k_ckpt))
+            sim.set_population(dims, (mats, w.detach().contiguous(), kappa.detach().contiguous(),
+                                      phi.detach().contiguous()), MODE_PARAMS)
+            sim.step(int(n_steps))
+            out = torch.empty(sim.P, dtype=torch.float64, device=w.device)
+            sim.fitness(out)
+            ctx.sim = sim
+            ctx.nvox = w.numel()
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            sim = ctx.sim
+            dev = grad.device
+            gw = torch.empty(ctx.nvox, dtype=torch.float32, device=dev)
+            gk = torch.empty_like(gw)
+            gp = torch.empty_like(gw)
+            sim.backward(grad.detach().to(torch.float64).contiguous(), gw, gk, gp)
+            return None, None, None, gw, gk, gp, None, None
+
+    return _Fitness
