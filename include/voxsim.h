@@ -68,7 +68,10 @@ enum {
     SIM_PATH_AUTO = 0,      /* resident for robots whose masses fit on chip, streamed otherwise */
     SIM_PATH_RESIDENT = 1,  /* one thread-block group per robot, state in shared memory for all
                                steps of a call */
-    SIM_PATH_STREAMED = 2   /* structure-of-arrays state in device memory, one pass per step */
+    SIM_PATH_STREAMED = 2,  /* structure-of-arrays state in device memory, one pass per step */
+    SIM_PATH_PLAIN = 3      /* the paper's organisation, kept as a baseline: per robot and step one
+                               launch with a thread per spring (atomic force sums in device
+                               memory) and one with a thread per mass */
 };
 
 /* MLP query kernel. */

@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
             const int S = gthreads;                       // plane stride of this slot
-            float4* su = sm4 + (size_t)group * kAdjointSlotVec4 * S;   // u at step n
+            // slot of this group: u (float4), lambda_F (float4), 39 parameter floats per corner
+            float4* su = reinterpret_cast<float4*>(reinterpret_cast<char*>(sm4) +
+                                                   (size_t)group * sizeof(float) * kAdjointSlotFloats * S);
             float4* sg = su + S;                                       // lambda_F at step n
             float* prm = reinterpret_cast<float*>(sg + S);             // [3][13][S] parameters
             const int cidx = lt;

@@ -111,9 +111,13 @@ struct voxsim_ctx {
     int max_corner = 0;
     int64_t max_spring_cap = 0;
     int64_t step = 0;
-    // lattice work items (robots up to lattice_max_threads() corners) and the rest
+    // lattice work items (robots up to lattice_max_threads() corners), robots on the atomic
+    // resident kernel (larger, state still fits one SM) and streamed robots (the rest)
     int n_items = 0, n_big = 0, max_big_corner = 0;
     int64_t max_big_spring_cap = 0;
+    int n_stream = 0, max_stream_corner = 0;
+    std::vector<int> stream_robots;
+    DevBuf<int> d_stream;
     // device buffers
     DevBuf<int> d_dims;
     DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
@@ -125,7 +129,8 @@ struct voxsim_ctx {
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
     DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
     DevBuf<int2> d_sab;
-    DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v;
+    DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v, d_x_alt;
+    DevBuf<float> d_plain_f;       // force accumulators of the plain path (3 per corner)
     DevBuf<double> d_x0c, d_keys, d_fit;
     DevBuf<float2> d_sc;
     DevBuf<unsigned char> d_pe;
@@ -305,6 +310,8 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     const bool packed = max_corner <= kResidentMaxCorner;
     if (!packed && ctx->p.path == SIM_PATH_RESIDENT)
         return fail(SIM_EINVAL, "robots with more than %d corners need the streamed path", kResidentMaxCorner);
+    if (mode == SIM_MODE_MLP && !packed)
+        return fail(SIM_EINVAL, "MLP decoding supports grids of at most %d corners", kResidentMaxCorner);
     // host-side validation of host materials
     if (mem == SIM_MEM_HOST && (mode == SIM_MODE_MATERIALS || mode == SIM_MODE_PARAMS)) {
         const uint8_t* m = mode == SIM_MODE_MATERIALS ? (const uint8_t*)genomes
@@ -435,9 +442,26 @@ static sim_status build_work_items(voxsim_ctx* ctx)
     ctx->max_big_corner = 0;
     ctx->max_big_spring_cap = 0;
     const bool lattice = ctx->p.accumulate != SIM_ACC_ATOMIC;
+    const bool all_streamed = ctx->p.path == SIM_PATH_STREAMED;
+    if (ctx->p.path == SIM_PATH_PLAIN) {       // every robot on the baseline kernels
+        ctx->n_items = ctx->n_big = ctx->n_stream = 0;
+        VX_CK(ctx->d_plain_f.ensure(3 * (size_t)ctx->M_cap));
+        VX_CK(cudaMemsetAsync(ctx->d_plain_f.p, 0, sizeof(float) * 3 * (size_t)ctx->M_cap, ctx->stream));
+        return SIM_OK;
+    }
+    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    std::vector<int> streamed;
+    ctx->max_stream_corner = 0;
     for (int r = 0; r < ctx->P; ++r) {
         const int nx = ctx->dims[3 * r], ny = ctx->dims[3 * r + 1], nz = ctx->dims[3 * r + 2];
         const int C = (nx + 1) * (ny + 1) * (nz + 1);
+        const bool fits_sm = C <= kResidentMaxCorner && resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget;
+        if (all_streamed || (!fits_sm && ctx->p.path != SIM_PATH_RESIDENT)) {
+            streamed.push_back(r);
+            ctx->max_stream_corner = std::max(ctx->max_stream_corner, C);
+            continue;
+        }
+        if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
         int cls = -1;
         if (lattice)
             for (int k = 0; k < 6; ++k)
@@ -466,7 +490,17 @@ static sim_status build_work_items(voxsim_ctx* ctx)
     }
     ctx->n_items = (int)items.size();
     ctx->n_big = (int)big.size();
+    ctx->n_stream = (int)streamed.size();
+    ctx->stream_robots = streamed;
     cudaStream_t s = ctx->stream;
+    if (!streamed.empty()) {
+        VX_CK(ctx->d_stream.ensure(streamed.size()));
+        VX_CK(cudaMemcpyAsync(ctx->d_stream.p, streamed.data(), sizeof(int) * streamed.size(),
+                              cudaMemcpyHostToDevice, s));
+        // both position buffers start equal (corners without a mass are never rewritten)
+        VX_CK(ctx->d_x_alt.ensure(ctx->M_cap));
+        VX_CK(cudaMemcpyAsync(ctx->d_x_alt.p, ctx->d_x.p, sizeof(float4) * ctx->M_cap, cudaMemcpyDeviceToDevice, s));
+    }
     VX_CK(ctx->d_items.ensure(items.size()));
     VX_CK(ctx->d_item_robots.ensure(robots.size()));
     VX_CK(ctx->d_big.ensure(big.size()));
@@ -578,6 +612,53 @@ static sim_status step_resident(voxsim_ctx* ctx, int n)
     return SIM_OK;
 }
 
+// The paper's organisation: for every step and robot, a spring launch and a mass launch.
+static sim_status step_plain(voxsim_ctx* ctx, int n)
+{
+    cudaStream_t s = ctx->stream;
+    std::vector<int32_t> M(ctx->P), S(ctx->P);
+    if (sim_status st = sim_get_counts(ctx, M.data(), S.data())) return st;
+    const StepConst c = ctx->stepconst();
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < ctx->P; ++r) {
+            const int64_t mo = ctx->moff[r], so = ctx->soff[r];
+            VX_CK(launch_step_plain_robot(ctx->d_sab.p + so, ctx->d_sp.p + so, ctx->d_mass_corner.p + mo,
+                                          ctx->d_x.p + mo, ctx->d_v.p + mo, ctx->d_plain_f.p + 3 * mo, S[r], M[r],
+                                          ctx->dims[3 * r], ctx->dims[3 * r + 1], ctx->d_sc.p, i, c, s));
+            ctx->launches += (S[r] > 0) + (M[r] > 0);
+        }
+    return SIM_OK;
+}
+
+// Streamed robots: one launch per step, positions double-buffered; an odd number of steps
+// leaves the newest positions in the alternate buffer, which are copied back per robot.
+static sim_status step_streamed(voxsim_ctx* ctx, int n)
+{
+    if (ctx->n_stream == 0) return SIM_OK;
+    cudaStream_t s = ctx->stream;
+    StreamArgs a{};
+    a.pv = ctx->view();
+    a.cflags = ctx->d_cflags.p;
+    a.prm = ctx->d_prm.p;
+    a.v = ctx->d_v.p;
+    a.sc = ctx->d_sc.p;
+    a.c = ctx->stepconst();
+    a.robots = ctx->d_stream.p;
+    a.n_robots = ctx->n_stream;
+    for (int i = 0; i < n; ++i) {
+        a.u_in = (i & 1) ? ctx->d_x_alt.p : ctx->d_x.p;
+        a.u_out = (i & 1) ? ctx->d_x.p : ctx->d_x_alt.p;
+        VX_LAUNCH(ctx, launch_step_streamed(a, i, ctx->max_stream_corner, s));
+    }
+    if (n & 1)
+        for (int r : ctx->stream_robots) {
+            const size_t o = (size_t)ctx->moff[r], len = (size_t)(ctx->moff[r + 1] - ctx->moff[r]);
+            VX_CK(cudaMemcpyAsync(ctx->d_x.p + o, ctx->d_x_alt.p + o, sizeof(float4) * len,
+                                  cudaMemcpyDeviceToDevice, s));
+        }
+    return SIM_OK;
+}
+
 sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
 {
     if (sim_status st = check_ctx(ctx)) return st;
@@ -589,16 +670,19 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
     VX_CK(ctx->d_sc.ensure(n_steps));
     VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->step, n_steps,
                               ctx->d_sc.p, s));
-    if (ctx->max_corner > kResidentMaxCorner || ctx->p.path == SIM_PATH_STREAMED)
-        return fail(SIM_EINVAL, "streamed path not available for this population");
-    if (ctx->ckpt_every > 0 && ctx->n_big > 0)
+    if (ctx->ckpt_every > 0 && (ctx->n_big > 0 || ctx->n_stream > 0))
         return fail(SIM_EINVAL, "checkpointing for the adjoint needs robots of at most %d corners",
                     lattice_max_threads());
     cudaEvent_t ev[2];
     if (sim_status st = timing_pair(ctx, ev)) return st;
     VX_CK(cudaEventRecord(ev[0], s));
-    if (sim_status st = step_lattice(ctx, n_steps)) return st;
-    if (sim_status st = step_resident(ctx, n_steps)) return st;
+    if (ctx->p.path == SIM_PATH_PLAIN) {
+        if (sim_status st = step_plain(ctx, n_steps)) return st;
+    } else {
+        if (sim_status st = step_lattice(ctx, n_steps)) return st;
+        if (sim_status st = step_resident(ctx, n_steps)) return st;
+        if (sim_status st = step_streamed(ctx, n_steps)) return st;
+    }
     VX_CK(cudaEventRecord(ev[1], s));
     if (ctx->ckpt_every > 0) {
         ctx->rec_valid = true;

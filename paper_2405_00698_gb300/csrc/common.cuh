@@ -142,6 +142,26 @@ struct LatticeArgs {
     int ckpt_every;          // K
 };
 
+// Streamed path (robots too large for one SM): one launch per step over all their corners.
+struct StreamArgs {
+    PopView pv;
+    const uint32_t* cflags;
+    const float* prm;
+    const float4* u_in;      // positions at the start of the step (per corner)
+    float4* u_out;           // positions at its end
+    float4* v;               // velocities (updated in place)
+    const float2* sc;        // sin / cos of w t per step of this call (indexed by the step)
+    StepConst c;
+    const int* robots;       // streamed robots (grid.y)
+    int n_robots;
+};
+cudaError_t launch_step_streamed(const StreamArgs& a, int n, int max_corners, cudaStream_t s);
+
+// The paper's organisation (baseline): one launch per robot per pass, two passes per step.
+cudaError_t launch_step_plain_robot(const int2* ab, const float4* prm, const int* mass_corner, float4* u,
+                                    float4* v, float* F, int S, int M, int nx, int ny, const float2* sc, int n,
+                                    StepConst c, cudaStream_t s);
+
 // Adjoint of the lattice stepping over one recorded call (see adjoint.cu).
 struct AdjointArgs {
     PopView pv;
@@ -166,8 +186,7 @@ struct AdjointArgs {
     float* g_a;
     float* g_b;
 };
-constexpr int kAdjointSlotVec4 = 2;     // float4 per corner slot: u, adjoint force
-constexpr int kAdjointSlotFloats = 8 + 39;   // + 39 parameter floats per corner
+constexpr int kAdjointSlotFloats = 8 + 39;   // per corner: u, adjoint force (float4 each), 39 parameters
 cudaError_t launch_adjoint_lattice(const AdjointArgs& a, int grid, int threads, size_t smem,
                                    cudaStream_t s);
 cudaError_t launch_adjoint_voxels(const uint8_t* mat, const float* w, const float* kappa,

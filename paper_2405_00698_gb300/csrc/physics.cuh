@@ -53,6 +53,33 @@ __device__ __forceinline__ SpringEval spring_eval_dir(float dux, float duy, floa
     return e;
 }
 
+// The same spring evaluation for a lattice offset (ox, oy, oz) known only at run time.
+__device__ __forceinline__ SpringEval spring_eval_rt(float dux, float duy, float duz, int ox, int oy, int oz,
+                                                     float edge, float L0, float k, float pa, float pb,
+                                                     float sn, float cs)
+{
+    SpringEval e;
+    e.dx = ox ? __fadd_rn(ox > 0 ? edge : -edge, dux) : dux;
+    e.dy = oy ? __fadd_rn(oy > 0 ? edge : -edge, duy) : duy;
+    e.dz = oz ? __fadd_rn(oz > 0 ? edge : -edge, duz) : duz;
+    const float l2 = __fmaf_rn(e.dz, e.dz, __fmaf_rn(e.dy, e.dy, __fmul_rn(e.dx, e.dx)));
+    e.inv = rsqrtf(l2);
+    const float l = __fmul_rn(l2, e.inv);
+    float d0du = 0.0f;
+    if (ox) d0du = __fmaf_rn(ox > 0 ? edge : -edge, dux, d0du);
+    if (oy) d0du = __fmaf_rn(oy > 0 ? edge : -edge, duy, d0du);
+    if (oz) d0du = __fmaf_rn(oz > 0 ? edge : -edge, duz, d0du);
+    const float dudu = __fmaf_rn(duz, duz, __fmaf_rn(duy, duy, __fmul_rn(dux, dux)));
+    const float num = __fmaf_rn(2.0f, d0du, dudu);
+    const float act = __fmaf_rn(pa, sn, __fmul_rn(pb, cs));
+    e.ext = __fsub_rn(__fdividef(num, __fadd_rn(l, L0)), act);
+    const float f = l2 > 1e-30f ? __fmul_rn(__fmul_rn(k, e.ext), e.inv) : 0.0f;
+    e.gx = __fmul_rn(f, e.dx);
+    e.gy = __fmul_rn(f, e.dy);
+    e.gz = __fmul_rn(f, e.dz);
+    return e;
+}
+
 // Rest length of lattice direction D (compile-time class: edge, face or body diagonal).
 template <int D>
 __device__ __forceinline__ float lattice_rest(const StepConst& c)

@@ -1,0 +1,74 @@
+// Streamed time stepping for robots too large to keep on one SM (Section II-C: the spring and
+// mass updates of one step; Table II constants).  State lives in device memory as per-corner
+// float4 arrays (structure of arrays over the whole lattice of every robot); one launch advances
+// every corner of every streamed robot by one step:
+//   thread = one grid corner (consecutive threads = consecutive corners, coalesced);
+//   it evaluates its forward springs (own parameters) and its backward springs (the lower
+//   endpoint's parameters, read from the same coalesced planes at corner c - offset(d)), each
+//   with the shared arithmetic of physics.cuh and in the same order as the lattice kernel, so a
+//   robot stepped here follows the resident path's trajectory bit for bit;
+//   positions are double-buffered (read u_in, write u_out), so one launch needs no grid-wide
+//   barrier.
+// Per spring update it moves the spring's parameters twice (once per endpoint, 24 B) and the
+// endpoint states through L2; per corner 16 B in + 32 B out (u, v) + 16 B v in + 4 B flags.
+#include "common.cuh"
+#include "physics.cuh"
+
+namespace vx {
+namespace {
+
+constexpr int kStreamThreads = 256;
+
+__global__ void __launch_bounds__(kStreamThreads)
+k_step_streamed(StreamArgs a, int n)
+{
+    const int r = a.robots[blockIdx.y];
+    const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
+    const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
+    const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cidx >= C) return;
+    const int64_t mo = a.pv.moff[r];
+    const uint32_t fl = a.cflags[mo + cidx];
+    if (!(fl >> 31)) return;                    // no mass here: nothing moves
+    const float4* __restrict__ uin = a.u_in + mo;
+    float4 u = uin[cidx];
+    float4 v = a.v[mo + cidx];
+    const float* __restrict__ prm = a.prm + 39 * mo;
+    const float2 sc = a.sc[n];
+    const StepConst c = a.c;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    for_each_dir([&](auto t) {                 // forward springs (c, c + offset(d))
+        constexpr int d = decltype(t)::value;
+        if (!((fl >> d) & 1u)) return;
+        const float4 ub = uin[cidx + lattice_offset<d>(X, XY)];
+        const SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z),
+                                                c.edge, lattice_rest<d>(c), prm[d * C + cidx],
+                                                prm[(13 + d) * C + cidx], prm[(26 + d) * C + cidx], sc.x, sc.y);
+        Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
+    });
+    for_each_dir([&](auto t) {                 // backward springs (c - offset(d), c)
+        constexpr int d = decltype(t)::value;
+        if (!((fl >> (16 + d)) & 1u)) return;
+        const int na = cidx - lattice_offset<d>(X, XY);
+        const float4 ua = uin[na];
+        const SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z),
+                                                c.edge, lattice_rest<d>(c), prm[d * C + na],
+                                                prm[(13 + d) * C + na], prm[(26 + d) * C + na], sc.x, sc.y);
+        Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
+    });
+    mass_update(u, v, Fx, Fy, Fz, c);
+    a.u_out[mo + cidx] = u;
+    a.v[mo + cidx] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_step_streamed(const StreamArgs& a, int n, int max_corners, cudaStream_t s)
+{
+    if (a.n_robots == 0) return cudaSuccess;
+    dim3 grid((max_corners + kStreamThreads - 1) / kStreamThreads, a.n_robots);
+    k_step_streamed<<<grid, kStreamThreads, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

@@ -19,12 +19,11 @@ MEM_HOST, MEM_DEVICE = 0, 1
 MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS = 0, 1, 2, 3
 ACC_AUTO, ACC_ATOMIC, ACC_GATHER = 0, 1, 2
 MLP_TENSOR, MLP_SIMT = 0, 1
-PATH_AUTO, PATH_RESIDENT, PATH_STREAMED = 0, 1, 2
+PATH_AUTO, PATH_RESIDENT, PATH_STREAMED, PATH_PLAIN = 0, 1, 2, 3
 GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
-           "sim_fitness", "evo_generation", "sim_set_checkpointing", "sim_backward",
-           "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_fitness", "evo_generation", "sim_set_checkpointing", "sim_backward", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 

@@ -1,0 +1,60 @@
+"""The streamed path (state in device memory, one launch per step) for robots too large for one
+SM: bit-identical to the resident lattice path where both apply (same arithmetic, same
+summation order), and within tolerance of the oracle on large robots."""
+import numpy as np
+import pytest
+
+from paper_2405_00698_gb300 import workloads as W
+from tests.parity import check_population
+
+pytestmark = pytest.mark.gpu
+PHYS = W.CONFIG
+
+
+@pytest.fixture(scope="module")
+def vs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00698_gb300 import build, voxsim
+    build.build()
+    return voxsim
+
+
+def run(vs, pop, nsteps, **kw):
+    sim = vs.Simulator(PHYS, **kw)
+    sim.set_population_from(pop)
+    sim.step(nsteps)
+    x, v, off = sim.state()
+    f = sim.fitness()
+    sim.close()
+    return x, v, off, f
+
+
+@pytest.mark.parametrize("nsteps", [301, 400])
+def test_streamed_equals_resident_lattice_bitwise(vs, nsteps):
+    pop = W.population_uneven(12, seed=70, sizes=(2, 4, 6, 8))
+    a = run(vs, pop, nsteps)
+    b = run(vs, pop, nsteps, path=vs.PATH_STREAMED)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
+
+
+def test_large_robots_match_oracle(vs, orc):
+    """Bernoulli(0.7) grids of 16^3 and 20x18x22 voxels (more corners than one SM holds)."""
+    grids = [W.bernoulli_grid(np.random.default_rng(71), (16, 16, 16), 0.7),
+             W.bernoulli_grid(np.random.default_rng(72), (20, 18, 22), 0.7)]
+    pop = W.make_population([(16, 16, 16), (20, 18, 22)], grids)
+    x, v, off, f = run(vs, pop, 300)
+    ref = orc.run_population(pop, PHYS, 300, want_x=True)
+    check_population(orc, pop, PHYS, 300, f, x, off, ref)
+
+
+def test_mixed_population_all_paths(vs, orc):
+    """One population with lattice (small), atomic-resident (12^3) and streamed (18^3) robots."""
+    rng = np.random.default_rng(73)
+    dims = [(4, 4, 4), (8, 8, 8), (12, 12, 12), (18, 18, 18), (3, 5, 2)]
+    grids = [W.bernoulli_grid(rng, d, 0.75) for d in dims]
+    pop = W.make_population(dims, grids)
+    x, v, off, f = run(vs, pop, 251)
+    ref = orc.run_population(pop, PHYS, 251, want_x=True)
+    check_population(orc, pop, PHYS, 251, f, x, off, ref)
