@@ -183,6 +183,27 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
                           float* genomes_out, int32_t P, int32_t G, const evo_params* e,
                           uint64_t generation, int32_t* parents_out, uint8_t* mask_out);
 
+/* evo_generation without any device allocation, for callers that cannot call cudaMalloc: a
+ * serving or control process whose memory pool already owns the whole device, code that must not
+ * allocate once its loop is running, or work being recorded into a CUDA graph (an allocation
+ * would synchronise the device or be refused).  The paper has no counterpart; it is the same
+ * operation as evo_generation (same kernels, same results) with two differences:
+ *   - it needs no context: the caller passes the CUDA stream (NULL = legacy default stream) and
+ *     the work runs on the current device;
+ *   - its only scratch (the rank order of the population) is a fixed device array of 16384
+ *     entries (64 KB) built into the library, which every GPU that loads the library keeps until
+ *     the process exits.  P above 16384 is rejected with SIM_EINVAL, and so are overlapping
+ *     genomes_in / genomes_out (there is no room for a copy).
+ * Every call on a device shares that array and leaves its contents behind (each call overwrites
+ * all the entries it reads, so nothing needs clearing); calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  Errors as for evo_generation. */
+sim_status evo_generation_static(const double* fitness, const float* genomes_in,
+                                 float* genomes_out, int32_t P, int32_t G, const evo_params* e,
+                                 uint64_t generation, int32_t* parents_out, uint8_t* mask_out,
+                                 void* cuda_stream);
+
 /* Turn state checkpointing on (every k_steps steps, k_steps >= 1) or off (0).  While on, each
  * sim_step_n call records the state at its start and every k_steps steps after, which
  * sim_backward replays.  Errors: SIM_EINVAL, SIM_ENOMEM. */

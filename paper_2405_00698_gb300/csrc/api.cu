@@ -25,6 +25,21 @@ sim_status fail(sim_status st, const char* fmt, ...)
     return st;
 }
 
+}  // namespace
+
+sim_status vx::vx_fail(sim_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+namespace {
+
 sim_status cuda_fail(cudaError_t e, const char* what)
 {
     return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA, "%s: %s", what,

@@ -210,4 +210,7 @@ cudaError_t launch_evo_children(const float* gin, float* gout, const int* order,
 cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float4* src,
                                  const float4* add, float* dst, const int64_t* dst_off, cudaStream_t s);
 
+// Record a failure message for sim_last_error() on this thread and return `st`.
+sim_status vx_fail(sim_status st, const char* fmt, ...);
+
 }  // namespace vx

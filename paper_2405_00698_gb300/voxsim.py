@@ -23,7 +23,8 @@ PATH_AUTO, PATH_RESIDENT, PATH_STREAMED, PATH_PLAIN = 0, 1, 2, 3
 GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
-           "sim_fitness", "evo_generation", "sim_set_checkpointing", "sim_backward", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_fitness", "evo_generation", "evo_generation_static", "sim_set_checkpointing",
+           "sim_backward", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 
@@ -83,6 +84,7 @@ def lib():
             "sim_step_n": [vp, i32],
             "sim_fitness": [vp, vp, i32],
             "evo_generation": [vp, vp, vp, vp, i32, i32, vp, u64, vp, vp],
+            "evo_generation_static": [vp, vp, vp, i32, i32, vp, u64, vp, vp, vp],
             "sim_set_checkpointing": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
             "sim_get_counts": [vp, vp, vp],
