@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--robots", type=int, default=P_ROBOTS, help=argparse.SUPPRESS)
     ap.add_argument("--sim-steps", type=int, default=SIM_STEPS, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven-population, adjoint and large-robot measurements")
     return ap.parse_args()
 
 
@@ -268,9 +270,113 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(genomes_h, Bmat_h, N, budget_s=12.0)
+    if not args.no_extras and world == 1:
+        sim.close()
+        rec["batched_vs_plain"] = measure_uneven(vs, stream, args)
+        rec["adjoint"] = measure_adjoint(vs, stream, args)
+        rec["streamed"] = measure_streamed(vs, stream, args, peaks)
     if rank == 0:
         print(json.dumps(rec))
     sim.close()
+
+
+# ------------------------------------------------------------------------------------------
+# the other components of the metric: batched vs plain, adjoint, large robots
+# ------------------------------------------------------------------------------------------
+
+def _timed(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_steps=100):
+    """4096 robots, axes from {4,...,12}, occupancy U[0.3, 0.9]: the persistent batched launch
+    for 5000 steps, against the plain form (one launch per robot per pass) on a stratified
+    sample of 64 robots for 100 steps (a rate: spring updates per second)."""
+    pop = W.workload_uneven(P, seed=2)
+    sim = vs.Simulator(W.CONFIG, stream=stream)
+    sim.set_population_from(pop)
+    M, S = sim.counts()
+    sim.step(50)                                # warm-up
+    sim.timing()
+    ms = _timed(stream, lambda: sim.step(N))
+    kms, launches = sim.timing()
+    batched = float(S.astype(np.int64).sum()) * N / (ms * 1e-3)
+    sim.close()
+    sub = pop.subset(W.stratified_subset(S, plain_robots))
+    res = {}
+    for name, path in (("plain", vs.PATH_PLAIN), ("batched_same_sample", vs.PATH_AUTO)):
+        s2 = vs.Simulator(W.CONFIG, stream=stream, path=path)
+        s2.set_population_from(sub)
+        _, S2 = s2.counts()
+        s2.step(5)
+        ms2 = _timed(stream, lambda: s2.step(plain_steps))
+        res[name] = float(S2.astype(np.int64).sum()) * plain_steps / (ms2 * 1e-3)
+        s2.close()
+    return {"workload": f"{P} robots, axes from {{4,6,8,10,12}}, occupancy U[0.3,0.9], connected, "
+                        f"{N} steps", "unit": "spring-updates/s", "batched": batched,
+            "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
+            "plain": res["plain"], "batched_on_plain_sample": res["batched_same_sample"],
+            "plain_sample": f"{plain_robots} robots stratified by spring count, {plain_steps} steps",
+            "speedup_vs_plain": batched / res["plain"]}
+
+
+def measure_adjoint(vs, stream, args, P=512, N=2000, K=100):
+    """512 robots 8x8x8, per-voxel (w, kappa, phi), 2000 steps with checkpoints every 100:
+    forward with recording plus the reverse sweep, as gradient evaluations per second."""
+    import torch
+    rng = np.random.default_rng(3)
+    pop = W.population_uniform(P, (8, 8, 8), seed=3)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(W.CONFIG, stream=stream)
+    sim.set_checkpointing(K)
+    args_pop = (t(pop.mats), t(w), t(kappa), t(phi))
+    n = pop.mats.size
+    gw = torch.empty(n, device="cuda"); gk = torch.empty_like(gw); gp = torch.empty_like(gw)
+    dl = torch.ones(P, dtype=torch.float64, device="cuda")
+
+    def run():
+        sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
+        sim.step(N)
+        sim.backward(dl, gw, gk, gp)
+    run()                                          # warm-up
+    fwd = _timed(stream, lambda: (sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS), sim.step(N)))
+    bwd = _timed(stream, lambda: sim.backward(dl, gw, gk, gp))
+    _, S = sim.counts()
+    sim.close()
+    return {"workload": f"{P} robots 8x8x8, {N} steps, checkpoints every {K}", "grads_per_s": P / ((fwd + bwd) * 1e-3),
+            "unit": "robot gradients/s (forward with checkpoints + reverse sweep)", "forward_ms": fwd,
+            "backward_ms": bwd, "backward_spring_updates_per_s": float(S.sum()) * N / (bwd * 1e-3)}
+
+
+def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=1000):
+    """64 robots 40x40x40 at occupancy 0.7 (Bernoulli, largest component), state in HBM, one
+    launch per step; a 1000-step sample of the 5000-step workload."""
+    pop = W.workload_large(P, seed=5, n=n)
+    sim = vs.Simulator(W.CONFIG, stream=stream)
+    sim.set_population_from(pop)
+    M, S = sim.counts()
+    sim.step(20)
+    sim.timing()
+    ms = _timed(stream, lambda: sim.step(N))
+    kms, launches = sim.timing()
+    sim.close()
+    ups = float(S.astype(np.int64).sum()) * N / (ms * 1e-3)
+    # algorithmic bytes per step: per spring its 12 B of parameters, per mass u and v read and
+    # written (4 x 16 B)
+    alg = (12.0 * S.astype(np.int64).sum() + 64.0 * M.astype(np.int64).sum()) * N
+    gbs = alg / (kms * 1e-3) / 1e9
+    return {"workload": f"{P} robots {n}^3, occupancy 0.7, {N} steps (sample of 5000)", "unit": "spring-updates/s",
+            "value": ups, "springs_per_robot": float(S.mean()), "masses_per_robot": float(M.mean()),
+            "launches": launches, "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                                               "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]}}
 
 
 # ------------------------------------------------------------------------------------------

@@ -58,3 +58,11 @@ def test_mixed_population_all_paths(vs, orc):
     x, v, off, f = run(vs, pop, 251)
     ref = orc.run_population(pop, PHYS, 251, want_x=True)
     check_population(orc, pop, PHYS, 251, f, x, off, ref)
+
+
+def test_plain_baseline_path_matches_oracle(vs, orc):
+    """The paper's organisation (one launch per robot per pass) kept as the measured baseline."""
+    pop = W.population_uneven(10, seed=74, sizes=(2, 4, 7))
+    x, v, off, f = run(vs, pop, 300, path=vs.PATH_PLAIN)
+    ref = orc.run_population(pop, PHYS, 300, want_x=True)
+    check_population(orc, pop, PHYS, 300, f, x, off, ref)
