@@ -38,6 +38,12 @@ WORKLOAD = dict(workload="mlp-encoded population: 1024 genomes, 8x8x8 grid, 10,0
 P_ROBOTS, GRID, SIM_STEPS = 1024, (8, 8, 8), 10000
 SMEM_PEAK_NOTE = "152 SMs x 128 B/clk x 2.07 GHz (unit counts and maximum SM clock)"
 SMEM_PEAK_GBS = 152 * 128 * 2.07
+# DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
+# 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
+# stays in shared memory, so traffic grows with the robots, not with the steps.
+LATTICE_DRAM_BYTES_PER_ROBOT = 18.93e6 / 152
+LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of k_step_lattice (152 robots, 1000 steps) scaled by robots; "
+                        "independent of the step count")
 
 
 def parse():
@@ -55,12 +61,14 @@ def parse():
 
 
 # ------------------------------------------------------------------------------------------
-# distributed plumbing (barrier and max-over-ranks only)
+# distributed plumbing: barrier and the max / sum over ranks (paper_2405_00698_gb300.shards)
 # ------------------------------------------------------------------------------------------
 
+from paper_2405_00698_gb300 import shards  # noqa: E402
+
+
 def dist_env():
-    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
-            int(os.environ.get("LOCAL_RANK", 0)))
+    return shards.env()
 
 
 def dist_init(world, backend):
@@ -71,19 +79,12 @@ def dist_init(world, backend):
 
 
 def dist_max(x: float, world: int, device=None) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return shards.max_over_ranks(x, device) if world > 1 else x
 
 
 def dist_barrier(world):
     if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+        shards.barrier()
 
 
 # ------------------------------------------------------------------------------------------
@@ -165,7 +166,7 @@ def run_ours(args):
     P, N = args.robots, args.sim_steps
     phys = W.CONFIG
     evo = W.Evolution()
-    genomes_h, Bmat_h = W.workload_mlp(P, seed=1 + 1000 * rank)
+    genomes_h, Bmat_h = W.workload_mlp(P, seed=shards.shard_seed(1, rank))
     dims = np.tile(np.asarray(GRID, np.int32), (P, 1))
     stream = torch.cuda.current_stream()
     sim = vs.Simulator(phys, device=local, stream=stream)
@@ -215,8 +216,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     dist_barrier(world)
     clk = clocks.stop()
-    total_ms = dist_max(total_ms, world, "cuda")
-    updates_all = int(dist_max(float(updates), world, "cuda")) * world if world > 1 else updates
+    value, updates_all, secs = shards.job_throughput(float(updates), total_ms * 1e-3, "cuda")
+    total_ms = secs * 1e3
 
     # end to end through the public API: pinned host genomes in, fitness out, every step
     pinned = torch.from_numpy(genomes_h).pin_memory()
@@ -234,7 +235,7 @@ def run_ours(args):
         M, S = sim.counts()
         e2e_updates += int(S.astype(np.int64).sum()) * N
         sim.timing()
-    e2e_ms = dist_max(e2e_ms, world, "cuda")
+    e2e_value, _, _ = shards.job_throughput(float(e2e_updates), e2e_ms * 1e-3, "cuda")
 
     peaks, peak_src = measured_peaks()
     # dominant kernel: the resident step kernel; algorithmic shared-memory bytes per step
@@ -243,7 +244,7 @@ def run_ours(args):
     achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else 0.0
     rec = {
         "metric": METRIC,
-        "value": updates_all / (total_ms * 1e-3),
+        "value": value,
         "unit": "spring-updates/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -256,13 +257,14 @@ def run_ours(args):
         "data": "synthetic (seeded MLP genomes, U(-1/sqrt(fan_in), 1/sqrt(fan_in)); B ~ N(0, 2^2))",
         "config": dict(WORKLOAD, l2="flushed between timed steps (256 MB write)",
                        parallelism=f"population shards x{world}" if world > 1 else "single GPU"),
-        "e2e": {"value": e2e_updates * world / (e2e_ms * 1e-3), "unit": "spring-updates/s",
+        "e2e": {"value": e2e_value, "unit": "spring-updates/s",
                 "h2d_bytes_per_step": int(genomes_h.nbytes),
                 "d2h_bytes_per_step": int(P * 8)},
         "gpu_launches": launches,
-        "roofline": {"bound": "smem", "kernel": "k_step_resident_atomic",
+        "roofline": {"bound": "smem", "kernel": "k_step_lattice",
                      "achieved": achieved_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
-                     "frac": achieved_gbs / SMEM_PEAK_GBS, "traffic": None,
+                     "frac": achieved_gbs / SMEM_PEAK_GBS, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
+                     "traffic_source": LATTICE_TRAFFIC_NOTE,
                      "peak_source": SMEM_PEAK_NOTE,
                      "kernel_ms_per_step": kernel_ms / args.steps},
         "clocks": clk,

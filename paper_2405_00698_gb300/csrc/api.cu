@@ -133,6 +133,19 @@ struct voxsim_ctx {
     int n_stream = 0, max_stream_corner = 0;
     std::vector<int> stream_robots;
     DevBuf<int> d_stream;
+    // CUDA graph of the streamed N-step loop, cached by step count (captured on a private
+    // non-blocking stream, replayed on the context's stream)
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t stream_graph = nullptr;
+    int stream_graph_n = -1;
+    const void* stream_graph_key = nullptr;   // buffers the graph was captured with
+    void drop_graph()
+    {
+        if (stream_graph) cudaGraphExecDestroy(stream_graph);
+        stream_graph = nullptr;
+        stream_graph_n = -1;
+        stream_graph_key = nullptr;
+    }
     // device buffers
     DevBuf<int> d_dims;
     DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
@@ -280,6 +293,8 @@ sim_status sim_destroy(voxsim_ctx* ctx)
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    ctx->drop_graph();
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;   // device buffers are released by their destructors
     return SIM_OK;
 }
@@ -439,6 +454,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     }
     ctx->step = 0;
     ctx->rec_valid = false;
+    ctx->drop_graph();
     ctx->have_pop = true;
     return SIM_OK;
 }
@@ -647,10 +663,8 @@ static sim_status step_plain(voxsim_ctx* ctx, int n)
 
 // Streamed robots: one launch per step, positions double-buffered; an odd number of steps
 // leaves the newest positions in the alternate buffer, which are copied back per robot.
-static sim_status step_streamed(voxsim_ctx* ctx, int n)
+static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
 {
-    if (ctx->n_stream == 0) return SIM_OK;
-    cudaStream_t s = ctx->stream;
     StreamArgs a{};
     a.pv = ctx->view();
     a.cflags = ctx->d_cflags.p;
@@ -663,7 +677,7 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n)
     for (int i = 0; i < n; ++i) {
         a.u_in = (i & 1) ? ctx->d_x_alt.p : ctx->d_x.p;
         a.u_out = (i & 1) ? ctx->d_x.p : ctx->d_x_alt.p;
-        VX_LAUNCH(ctx, launch_step_streamed(a, i, ctx->max_stream_corner, s));
+        VX_CK(launch_step_streamed(a, i, ctx->max_stream_corner, s));
     }
     if (n & 1)
         for (int r : ctx->stream_robots) {
@@ -671,6 +685,34 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n)
             VX_CK(cudaMemcpyAsync(ctx->d_x.p + o, ctx->d_x_alt.p + o, sizeof(float4) * len,
                                   cudaMemcpyDeviceToDevice, s));
         }
+    return SIM_OK;
+}
+
+// Streamed robots: one launch per step, positions double-buffered (an odd number of steps
+// leaves the newest positions in the alternate buffer, copied back per robot).  The sequence is
+// captured once into a CUDA graph per step count and replayed.
+static sim_status step_streamed(voxsim_ctx* ctx, int n)
+{
+    if (ctx->n_stream == 0) return SIM_OK;
+    cudaStream_t s = ctx->stream;
+    const void* key = ctx->d_sc.p;   // the step table may move when it grows
+    if (!(ctx->stream_graph && ctx->stream_graph_n == n && ctx->stream_graph_key == key)) {
+        ctx->drop_graph();
+        if (!ctx->capture_stream) VX_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        VX_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        sim_status st = enqueue_streamed(ctx, n, ctx->capture_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (st != SIM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx->stream_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        ctx->stream_graph_n = n;
+        ctx->stream_graph_key = key;
+    }
+    VX_CK(cudaGraphLaunch(ctx->stream_graph, s));
+    ctx->launches += n;
     return SIM_OK;
 }
 
