@@ -152,6 +152,7 @@ struct voxsim_ctx {
     DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big;
     DevBuf<int4> d_items;
     DevBuf<uint32_t> d_cflags;
+    DevBuf<int> d_corner_order;
     DevBuf<float> d_prm;
     DevBuf<uint8_t> d_in_u8, d_mat_raw, d_mat;
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
@@ -369,6 +370,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     if (packed) VX_CK(ctx->d_spack.ensure(Sc));
     VX_CK(ctx->d_x0.ensure(Mc)); VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
     VX_CK(ctx->d_cflags.ensure(Mc)); VX_CK(ctx->d_prm.ensure(39 * (size_t)Mc));
+    VX_CK(ctx->d_corner_order.ensure(Mc));
     VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
     ctx->dims = d; ctx->voff = voff; ctx->moff = moff; ctx->soff = soff;
     ctx->P = P; ctx->V_tot = V; ctx->M_cap = Mc; ctx->S_cap = Sc;
@@ -444,7 +446,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
                               ctx->d_phi.p, mc, ctx->p.edge, ctx->d_label.p, ctx->d_count.p,
                               ctx->d_corner_mass.p, ctx->d_mass_corner.p, ctx->d_sab.p, ctx->d_sp.p,
                               packed ? ctx->d_spack.p : nullptr, ctx->d_cflags.p, ctx->d_prm.p,
-                              ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
+                              ctx->d_corner_order.p, ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
                               ctx->d_x0c.p, ctx->d_status.p, 0, s));
         // longest-first processing order (by spring count, ties by index)
         k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
@@ -573,6 +575,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     if (ctx->n_items == 0) return SIM_OK;
     LatticeArgs a{};
     a.pv = ctx->view();
+    a.corner_order = ctx->d_corner_order.p;
     a.cflags = ctx->d_cflags.p;
     a.prm = ctx->d_prm.p;
     a.u = ctx->d_x.p;
@@ -829,6 +832,7 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
     AdjointArgs a{};
     a.pv = ctx->view();
+    a.corner_order = ctx->d_corner_order.p;
     a.cflags = ctx->d_cflags.p;
     a.prm = ctx->d_prm.p;
     a.mat = ctx->d_mat.p;

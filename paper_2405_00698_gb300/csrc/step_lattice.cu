@@ -6,9 +6,9 @@
 // one corner for the whole call and keeps in registers its displacement u, velocity v and the
 // (k, alpha L0, beta L0) of its up-to-13 forward springs.  Per step:
 //   phase A: for each forward spring (c, c + off(d)) the owner computes the force f from its own
-//            u and the neighbour's u (shared memory), adds f to its own total and writes -f to
+//            u and the neighbour's u (shared memory), adds f to its own total and writes f to
 //            the force plane d of shared memory at index c;
-//   phase B: each thread adds the plane-d entries at c - off(d) of its backward springs, then
+//   phase B: each thread subtracts the plane-d entries at c - off(d) of its backward springs, then
 //            applies gravity, ground contact with friction and the semi-implicit Euler update in
 //            registers and publishes its new u.
 // Two block barriers per step, no atomics, and a fixed summation order (own forward springs by
@@ -60,9 +60,12 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             // shared-memory slot of this group (S = gthreads corners): u, then 13 force planes
             const int S = gthreads;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
-            float4* fb = su + S;               // plane d at fb + d * S: force on b of spring (c, d)
-            const int cidx = lt;
-            const bool in = cidx < C;
+            float4* fb = su + S;               // plane d at fb + d * S: force on a of spring (a, d)
+            // thread lt owns the lt-th mass in the robot's thread order (masses grouped by their
+            // spring masks); threads past the mass count only take part in the barriers
+            const int M = a.pv.n_mass[r];
+            const bool in = lt < M;
+            const int cidx = in ? a.corner_order[mo + lt] : 0;
             const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
             float pk[13], pa[13], pb[13];
             const float* prm = a.prm + 39 * mo;
@@ -95,15 +98,15 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                                                             __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c),
                                                             pk[d], pa[d], pb[d], sc.x, sc.y);
                     Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
-                    fb[d * S + cidx] = make_float4(-e.gx, -e.gy, -e.gz, 0.f);
+                    fb[d * S + cidx] = make_float4(e.gx, e.gy, e.gz, 0.f);
                 });
                 group_sync(bar, gthreads);
                 // phase B: backward springs (c - offset(d), c), then the mass update
                 for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> (16 + d)) & 1u)) return;
-                    const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];
-                    Fx = __fadd_rn(Fx, g.x); Fy = __fadd_rn(Fy, g.y); Fz = __fadd_rn(Fz, g.z);
+                    const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];   // force on a
+                    Fx = __fsub_rn(Fx, g.x); Fy = __fsub_rn(Fy, g.y); Fz = __fsub_rn(Fz, g.z);
                 });
                 if (mass) {
                     mass_update(u, v, Fx, Fy, Fz, c);
