@@ -307,6 +307,9 @@ def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_step
     sim = vs.Simulator(W.CONFIG, stream=stream)
     sim.set_population_from(pop)
     M, S = sim.counts()
+    t0 = time.perf_counter()
+    kinds, threads = sim.autotune(20)           # per-size-class kernel choice, state restored
+    tune_s = time.perf_counter() - t0
     sim.step(50)                                # warm-up
     sim.timing()
     ms = _timed(stream, lambda: sim.step(N))
@@ -326,6 +329,9 @@ def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_step
     return {"workload": f"{P} robots, axes from {{4,6,8,10,12}}, occupancy U[0.3,0.9], connected, "
                         f"{N} steps", "unit": "spring-updates/s", "batched": batched,
             "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
+            "autotune": {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
+                         "kind (0 lattice, 1 atomic, 2 streamed)": kinds.tolist(),
+                         "atomic_threads": threads.tolist(), "seconds": tune_s},
             "plain": res["plain"], "batched_on_plain_sample": res["batched_same_sample"],
             "plain_sample": f"{plain_robots} robots stratified by spring count, {plain_steps} steps",
             "speedup_vs_plain": batched / res["plain"]}

@@ -220,6 +220,19 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
                         float* g_phi);
 
+/* Per-size autotuner of the stepping kernels (project-written; the paper has no counterpart).
+ * Robots are grouped by grid-corner count into 10 classes (up to 64, 128, 192, 256, 384, 768,
+ * 1536, 2560, 5120 corners, and more).  For every class present in the population, each
+ * admissible kernel (the lattice-gather kernel, the atomic resident kernel at three block sizes,
+ * the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
+ * the current state (CUDA events), and the fastest is kept for that class.  The state is
+ * restored afterwards; the choices persist for later populations of this context.  Modes that
+ * require bit-reproducibility (SIM_ACC_GATHER, checkpointing) only consider deterministic
+ * kernels.  kind_out / threads_out: int32 [10] host arrays (either may be NULL) receiving per
+ * class 0 = lattice, 1 = atomic resident, 2 = streamed, and the atomic kernel's block size.
+ * Synchronises the stream.  Errors: SIM_ESTATE without a population, SIM_EINVAL. */
+sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out);
+
 /* Mass and spring count of every robot (host arrays of P int32; either may be NULL).
  * Synchronises the stream.  Errors: SIM_ESTATE without a population. */
 sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs);

@@ -111,6 +111,18 @@ int64_t full_springs(int nx, int ny, int nz)
 
 }  // namespace
 
+// Size classes by grid-corner count: the six lattice slot sizes, then larger bands.
+constexpr int kNumClasses = 10;
+constexpr int kClassCorners[kNumClasses] = {64, 128, 192, 256, 384, 768, 1536, 2560, 5120, 1 << 30};
+enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2 };
+
+static int class_of(int corners)
+{
+    for (int k = 0; k < kNumClasses; ++k)
+        if (corners <= kClassCorners[k]) return k;
+    return kNumClasses - 1;
+}
+
 struct voxsim_ctx {
     sim_params p{};
     int device = 0;
@@ -130,6 +142,14 @@ struct voxsim_ctx {
     // resident kernel (larger, state still fits one SM) and streamed robots (the rest)
     int n_items = 0, n_big = 0, max_big_corner = 0;
     int64_t max_big_spring_cap = 0;
+    // per size class (by corner count): kind (0 lattice, 1 atomic, 2 streamed) and threads per
+    // robot of the atomic kernel (0 = from the robot size); set by sim_autotune
+    int class_kind[kNumClasses];
+    int class_threads[kNumClasses];
+    bool tuned = false;
+    // atomic-kernel groups (one persistent launch each): robots of one thread count
+    struct AtomicGroup { int threads; int first; int count; int max_corner; int64_t max_spring_cap; };
+    std::vector<AtomicGroup> atomic_groups;
     int n_stream = 0, max_stream_corner = 0;
     std::vector<int> stream_robots;
     DevBuf<int> d_stream;
@@ -152,7 +172,6 @@ struct voxsim_ctx {
     DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big;
     DevBuf<int4> d_items;
     DevBuf<uint32_t> d_cflags;
-    DevBuf<int> d_corner_order;
     DevBuf<float> d_prm;
     DevBuf<uint8_t> d_in_u8, d_mat_raw, d_mat;
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
@@ -222,7 +241,7 @@ struct voxsim_ctx {
 };
 
 extern "C" {
-static sim_status build_work_items(voxsim_ctx* ctx);
+static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subset = nullptr);
 }
 
 namespace {
@@ -370,7 +389,6 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     if (packed) VX_CK(ctx->d_spack.ensure(Sc));
     VX_CK(ctx->d_x0.ensure(Mc)); VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
     VX_CK(ctx->d_cflags.ensure(Mc)); VX_CK(ctx->d_prm.ensure(39 * (size_t)Mc));
-    VX_CK(ctx->d_corner_order.ensure(Mc));
     VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
     ctx->dims = d; ctx->voff = voff; ctx->moff = moff; ctx->soff = soff;
     ctx->P = P; ctx->V_tot = V; ctx->M_cap = Mc; ctx->S_cap = Sc;
@@ -446,7 +464,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
                               ctx->d_phi.p, mc, ctx->p.edge, ctx->d_label.p, ctx->d_count.p,
                               ctx->d_corner_mass.p, ctx->d_mass_corner.p, ctx->d_sab.p, ctx->d_sp.p,
                               packed ? ctx->d_spack.p : nullptr, ctx->d_cflags.p, ctx->d_prm.p,
-                              ctx->d_corner_order.p, ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
+                              ctx->d_x0.p, ctx->d_x.p, ctx->d_v.p,
                               ctx->d_x0c.p, ctx->d_status.p, 0, s));
         // longest-first processing order (by spring count, ties by index)
         k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
@@ -461,21 +479,34 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     return SIM_OK;
 }
 
-// Work items of the lattice path: robots grouped by corner count into classes of
-// 64, 128, 192, 256, 384 or 768 threads per robot (each divides the 768-thread block), several
-// robots per block for the small classes; items ordered largest class first, robots within a
-// class by descending corner count (longest-processing-time first).  Robots with more corners
-// go to the atomic kernel.  Everything is known from the grid shapes, so no device data is read.
-static sim_status build_work_items(voxsim_ctx* ctx)
+// Default kind of a size class: the lattice kernel up to its block size, then the atomic
+// resident kernel while the robot's state fits one SM, then the streamed path.
+static void default_choices(voxsim_ctx* ctx)
 {
-    static const int kClass[6] = {64, 128, 192, 256, 384, 768};
+    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    for (int k = 0; k < kNumClasses; ++k) {
+        const int C = std::min(kClassCorners[k], kResidentMaxCorner);
+        const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
+        ctx->class_kind[k] = k < 6 ? kKindLattice : (fits ? kKindAtomic : kKindStreamed);
+        ctx->class_threads[k] = 0;
+    }
+}
+
+// Execution plan of the population from the per-class choices:
+//   lattice: work items of robots grouped by corner count into 64..768-thread slots of a
+//   768-thread block (several small robots per block), largest class first, robots by
+//   descending corner count (longest processing time first);
+//   atomic: one persistent launch per thread count, robots longest first;
+//   streamed: the rest.
+// Everything is known from the grid shapes, so no device data is read.
+static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subset)
+{
+    static const int kSlot[6] = {64, 128, 192, 256, 384, 768};
     const int block = lattice_max_threads();
-    std::vector<std::vector<std::pair<int, int>>> byclass(6);
-    std::vector<int> big;
+    if (!ctx->tuned) default_choices(ctx);
     ctx->max_big_corner = 0;
     ctx->max_big_spring_cap = 0;
-    const bool lattice = ctx->p.accumulate != SIM_ACC_ATOMIC;
-    const bool all_streamed = ctx->p.path == SIM_PATH_STREAMED;
+    ctx->atomic_groups.clear();
     if (ctx->p.path == SIM_PATH_PLAIN) {       // every robot on the baseline kernels
         ctx->n_items = ctx->n_big = ctx->n_stream = 0;
         VX_CK(ctx->d_plain_f.ensure(3 * (size_t)ctx->M_cap));
@@ -483,49 +514,79 @@ static sim_status build_work_items(voxsim_ctx* ctx)
         return SIM_OK;
     }
     const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    std::vector<std::vector<std::pair<int, int>>> lattice(6);
+    std::vector<std::pair<int, std::pair<int, int>>> atomic;   // (threads, (-corners, robot))
     std::vector<int> streamed;
     ctx->max_stream_corner = 0;
-    for (int r = 0; r < ctx->P; ++r) {
+    const int nrob = subset ? (int)subset->size() : ctx->P;
+    for (int ri = 0; ri < nrob; ++ri) {
+        const int r = subset ? (*subset)[ri] : ri;
         const int nx = ctx->dims[3 * r], ny = ctx->dims[3 * r + 1], nz = ctx->dims[3 * r + 2];
         const int C = (nx + 1) * (ny + 1) * (nz + 1);
+        const int k = class_of(C);
         const bool fits_sm = C <= kResidentMaxCorner && resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget;
-        if (all_streamed || (!fits_sm && ctx->p.path != SIM_PATH_RESIDENT)) {
+        int kind = ctx->class_kind[k];
+        if (ctx->p.path == SIM_PATH_STREAMED) kind = kKindStreamed;
+        else if (ctx->p.accumulate == SIM_ACC_ATOMIC && kind == kKindLattice) kind = kKindAtomic;
+        else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? kKindLattice : kKindStreamed;
+        if (kind == kKindLattice && C > block) kind = fits_sm ? kKindAtomic : kKindStreamed;
+        if (kind == kKindAtomic && !fits_sm) kind = kKindStreamed;
+        if (kind == kKindStreamed && ctx->p.path == SIM_PATH_RESIDENT) {
+            if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
+            kind = C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC ? kKindLattice : kKindAtomic;
+        }
+        if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER)
+            return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners on the resident path", block);
+        if (kind == kKindLattice) {
+            int slot = 0;
+            while (kSlot[slot] < C) ++slot;
+            lattice[slot].push_back({-C, r});
+        } else if (kind == kKindAtomic) {
+            int threads = ctx->class_threads[k] > 0 ? ctx->class_threads[k] : ctx->p.threads;
+            if (threads <= 0) {
+                const int64_t sc = full_springs(nx, ny, nz);
+                threads = sc <= 1536 ? 256 : (sc <= 6144 ? 512 : 1024);
+            }
+            threads = std::max(32, std::min(1024, (threads + 31) / 32 * 32));
+            atomic.push_back({threads, {-C, r}});
+        } else {
             streamed.push_back(r);
             ctx->max_stream_corner = std::max(ctx->max_stream_corner, C);
-            continue;
-        }
-        if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
-        int cls = -1;
-        if (lattice)
-            for (int k = 0; k < 6; ++k)
-                if (C <= kClass[k]) { cls = k; break; }
-        if (cls < 0) {
-            big.push_back(r);
-            ctx->max_big_corner = std::max(ctx->max_big_corner, C);
-            ctx->max_big_spring_cap = std::max(ctx->max_big_spring_cap, full_springs(nx, ny, nz));
-        } else {
-            byclass[cls].push_back({-C, r});
         }
     }
-    if (!big.empty() && ctx->p.accumulate == SIM_ACC_GATHER)
-        return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners", block);
     std::vector<int4> items;
     std::vector<int> robots;
     for (int k = 5; k >= 0; --k) {
-        auto& v = byclass[k];
+        auto& v = lattice[k];
         std::sort(v.begin(), v.end());
-        const int per = block / kClass[k];
+        const int per = block / kSlot[k];
         for (size_t i = 0; i < v.size(); i += per) {
             const int n = (int)std::min<size_t>(per, v.size() - i);
-            items.push_back(make_int4((int)robots.size(), n, kClass[k], 0));
+            items.push_back(make_int4((int)robots.size(), n, kSlot[k], 0));
             for (int j = 0; j < n; ++j) robots.push_back(v[i + j].second);
         }
+    }
+    std::sort(atomic.begin(), atomic.end());
+    std::vector<int> big;
+    for (size_t i = 0; i < atomic.size();) {
+        voxsim_ctx::AtomicGroup g{atomic[i].first, (int)big.size(), 0, 0, 0};
+        for (; i < atomic.size() && atomic[i].first == g.threads; ++i) {
+            const int r = atomic[i].second.second;
+            big.push_back(r);
+            g.max_corner = std::max(g.max_corner, -atomic[i].second.first);
+            g.max_spring_cap = std::max(g.max_spring_cap, full_springs(ctx->dims[3 * r], ctx->dims[3 * r + 1], ctx->dims[3 * r + 2]));
+        }
+        g.count = (int)big.size() - g.first;
+        ctx->max_big_corner = std::max(ctx->max_big_corner, g.max_corner);
+        ctx->max_big_spring_cap = std::max(ctx->max_big_spring_cap, g.max_spring_cap);
+        ctx->atomic_groups.push_back(g);
     }
     ctx->n_items = (int)items.size();
     ctx->n_big = (int)big.size();
     ctx->n_stream = (int)streamed.size();
     ctx->stream_robots = streamed;
     cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_queue.ensure(2 + ctx->atomic_groups.size()));
     if (!streamed.empty()) {
         VX_CK(ctx->d_stream.ensure(streamed.size()));
         VX_CK(cudaMemcpyAsync(ctx->d_stream.p, streamed.data(), sizeof(int) * streamed.size(),
@@ -541,18 +602,11 @@ static sim_status build_work_items(voxsim_ctx* ctx)
         VX_CK(cudaMemcpyAsync(ctx->d_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
         VX_CK(cudaMemcpyAsync(ctx->d_item_robots.p, robots.data(), sizeof(int) * robots.size(), cudaMemcpyHostToDevice, s));
     }
-    if (!big.empty()) {
-        // longest first by capacity (corner count)
-        std::sort(big.begin(), big.end(), [&](int a, int b) {
-            auto corners = [&](int r) {
-                return (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
-            };
-            return corners(a) != corners(b) ? corners(a) > corners(b) : a < b;
-        });
+    if (!big.empty())
         VX_CK(cudaMemcpyAsync(ctx->d_big.p, big.data(), sizeof(int) * big.size(), cudaMemcpyHostToDevice, s));
-    }
     // the host vectors are copied from pageable memory: wait so they may go out of scope
     VX_CK(cudaStreamSynchronize(s));
+    ctx->drop_graph();
     return SIM_OK;
 }
 
@@ -575,7 +629,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     if (ctx->n_items == 0) return SIM_OK;
     LatticeArgs a{};
     a.pv = ctx->view();
-    a.corner_order = ctx->d_corner_order.p;
+    a.corner_order = ctx->d_mass_corner.p;
     a.cflags = ctx->d_cflags.p;
     a.prm = ctx->d_prm.p;
     a.u = ctx->d_x.p;
@@ -604,45 +658,45 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     return SIM_OK;
 }
 
+// The atomic resident kernel: one persistent launch per thread count.
 static sim_status step_resident(voxsim_ctx* ctx, int n)
 {
-    if (ctx->n_big == 0) return SIM_OK;
     cudaStream_t s = ctx->stream;
-    ResidentArgs a{};
-    a.pv = ctx->view();
-    a.spr_pack = ctx->d_spack.p;
-    a.cflags = ctx->d_cflags.p;
-    a.x = ctx->d_x.p;
-    a.v = ctx->d_v.p;
-    a.sc = ctx->d_sc.p;
-    a.nsteps = n;
-    a.c = ctx->stepconst();
-    a.order = ctx->d_big.p;
-    a.n_robots = ctx->n_big;
-    a.queue = ctx->d_queue.p + 1;
-    a.accumulate = SIM_ACC_ATOMIC;
-    // launch shape: threads per robot and blocks per SM from the largest robot's capacity
-    int threads = ctx->p.threads;
-    const int64_t sc = ctx->max_big_spring_cap;
-    if (threads <= 0) threads = sc <= 1536 ? 256 : (sc <= 6144 ? 512 : 1024);
-    threads = std::max(32, std::min(1024, (threads + 31) / 32 * 32));
-    const size_t mass_bytes = resident_smem_bytes(ctx->max_big_corner, 0, a.accumulate);
-    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
-    if (mass_bytes > budget) return fail(SIM_EINVAL, "robot too large for the resident path");
-    int64_t spr_fit = (int64_t)((budget - mass_bytes) / sizeof(float4));
-    // several blocks per SM when everything of the largest robot fits in a fraction of it
-    int per_sm = 1;
-    const size_t need = mass_bytes + sizeof(float4) * (size_t)sc;
-    while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin && threads * (per_sm + 1) <= 2048)
-        ++per_sm;
-    if (per_sm > 1) spr_fit = sc;
-    a.max_mass = ctx->max_big_corner;
-    a.max_spring_smem = (int)std::min<int64_t>(sc, spr_fit);
-    const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
-    int grid = (int)std::min<int64_t>(ctx->n_big, (int64_t)ctx->num_sms * per_sm);
-    if (grid < 1) grid = 1;
-    VX_CK(cudaMemsetAsync(ctx->d_queue.p + 1, 0, sizeof(int), s));
-    VX_LAUNCH(ctx, launch_step_resident(a, grid, threads, smem, s));
+    for (size_t gi = 0; gi < ctx->atomic_groups.size(); ++gi) {
+        const voxsim_ctx::AtomicGroup& g = ctx->atomic_groups[gi];
+        ResidentArgs a{};
+        a.pv = ctx->view();
+        a.spr_pack = ctx->d_spack.p;
+        a.cflags = ctx->d_cflags.p;
+        a.x = ctx->d_x.p;
+        a.v = ctx->d_v.p;
+        a.sc = ctx->d_sc.p;
+        a.nsteps = n;
+        a.c = ctx->stepconst();
+        a.order = ctx->d_big.p + g.first;
+        a.n_robots = g.count;
+        a.queue = ctx->d_queue.p + 2 + gi;
+        a.accumulate = SIM_ACC_ATOMIC;
+        const int threads = g.threads;
+        const int64_t sc = g.max_spring_cap;
+        const size_t mass_bytes = resident_smem_bytes(g.max_corner, 0, a.accumulate);
+        const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+        if (mass_bytes > budget) return fail(SIM_EINVAL, "robot too large for the resident path");
+        int64_t spr_fit = (int64_t)((budget - mass_bytes) / sizeof(float4));
+        // several blocks per SM when everything of the largest robot fits in a fraction of it
+        int per_sm = 1;
+        const size_t need = mass_bytes + sizeof(float4) * (size_t)sc;
+        while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin && threads * (per_sm + 1) <= 2048)
+            ++per_sm;
+        if (per_sm > 1) spr_fit = sc;
+        a.max_mass = g.max_corner;
+        a.max_spring_smem = (int)std::min<int64_t>(sc, spr_fit);
+        const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
+        int grid = (int)std::min<int64_t>(g.count, (int64_t)ctx->num_sms * per_sm);
+        if (grid < 1) grid = 1;
+        VX_CK(cudaMemsetAsync(a.queue, 0, sizeof(int), s));
+        VX_LAUNCH(ctx, launch_step_resident(a, grid, threads, smem, s));
+    }
     return SIM_OK;
 }
 
@@ -832,7 +886,7 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
     AdjointArgs a{};
     a.pv = ctx->view();
-    a.corner_order = ctx->d_corner_order.p;
+    a.corner_order = ctx->d_mass_corner.p;
     a.cflags = ctx->d_cflags.p;
     a.prm = ctx->d_prm.p;
     a.mat = ctx->d_mat.p;
@@ -858,6 +912,91 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
     VX_LAUNCH(ctx, launch_adjoint_voxels(ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p, ctx->d_phi.p, ctx->matconst(),
                                          ctx->d_gk.p, ctx->d_ga.p, ctx->d_gb.p, (int64_t)V, g_w, g_kappa, g_phi, s));
+    return SIM_OK;
+}
+
+// Per size class, time every admissible kernel on a sample of the class's robots (up to two per
+// SM) for n_steps steps from the current state, keep the fastest, restore the state.
+sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    if (n_steps < 1) return fail(SIM_EINVAL, "n_steps must be >= 1");
+    if (ctx->p.path == SIM_PATH_PLAIN) return fail(SIM_EINVAL, "the plain path has nothing to tune");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const size_t Mc = ctx->M_cap;
+    DevBuf<float4> snap_u, snap_v;
+    VX_CK(snap_u.ensure(Mc));
+    VX_CK(snap_v.ensure(Mc));
+    VX_CK(cudaMemcpyAsync(snap_u.p, ctx->d_x.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+    VX_CK(cudaMemcpyAsync(snap_v.p, ctx->d_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+    VX_CK(ctx->d_sc.ensure(n_steps));
+    VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->step, n_steps,
+                                       ctx->d_sc.p, s));
+    if (!ctx->tuned) default_choices(ctx);
+    ctx->tuned = true;
+    std::vector<std::vector<std::pair<int, int>>> members(kNumClasses);
+    for (int r = 0; r < ctx->P; ++r) {
+        const int C = (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
+        members[class_of(C)].push_back({-C, r});
+    }
+    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    cudaEvent_t e0, e1;
+    VX_CK(cudaEventCreate(&e0));
+    VX_CK(cudaEventCreate(&e1));
+    sim_status result = SIM_OK;
+    for (int k = 0; k < kNumClasses && result == SIM_OK; ++k) {
+        if (members[k].empty()) continue;
+        std::sort(members[k].begin(), members[k].end());
+        std::vector<int> sample;
+        for (size_t i = 0; i < members[k].size() && (int)i < 2 * ctx->num_sms; ++i) sample.push_back(members[k][i].second);
+        const int Cmax = -members[k].front().first;
+        const bool fits = Cmax <= kResidentMaxCorner && resident_smem_bytes(Cmax, 0, SIM_ACC_ATOMIC) <= budget;
+        std::vector<std::pair<int, int>> cands;
+        if (k < 6 && ctx->p.accumulate != SIM_ACC_ATOMIC) cands.push_back({kKindLattice, 0});
+        if (fits && ctx->p.accumulate != SIM_ACC_GATHER) {
+            const int t3[3] = {k < 6 ? 128 : 256, k < 6 ? 256 : 512, k < 6 ? 512 : 1024};
+            for (int t : t3) cands.push_back({kKindAtomic, t});
+        }
+        if (k >= 6 && ctx->p.path != SIM_PATH_RESIDENT) cands.push_back({kKindStreamed, 0});
+        if (cands.size() < 2) continue;
+        float best_ms = 1e30f;
+        std::pair<int, int> best = cands.front();
+        for (const auto& cand : cands) {
+            ctx->class_kind[k] = cand.first;
+            ctx->class_threads[k] = cand.second;
+            if ((result = build_work_items(ctx, &sample)) != SIM_OK) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && result == SIM_OK; ++rep) {    // warm-up run, timed run
+                VX_CK(cudaMemcpyAsync(ctx->d_x.p, snap_u.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+                VX_CK(cudaMemcpyAsync(ctx->d_v.p, snap_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+                if (ctx->n_stream > 0)
+                    VX_CK(cudaMemcpyAsync(ctx->d_x_alt.p, snap_u.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+                VX_CK(cudaEventRecord(e0, s));
+                if ((result = step_lattice(ctx, n_steps)) != SIM_OK) break;
+                if ((result = step_resident(ctx, n_steps)) != SIM_OK) break;
+                if ((result = step_streamed(ctx, n_steps)) != SIM_OK) break;
+                VX_CK(cudaEventRecord(e1, s));
+                VX_CK(cudaEventSynchronize(e1));
+                VX_CK(cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (result == SIM_OK && ms < best_ms) { best_ms = ms; best = cand; }
+        }
+        ctx->class_kind[k] = best.first;
+        ctx->class_threads[k] = best.second;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    VX_CK(cudaMemcpyAsync(ctx->d_x.p, snap_u.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+    VX_CK(cudaMemcpyAsync(ctx->d_v.p, snap_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+    if (result == SIM_OK) result = build_work_items(ctx);   // also resets the alternate buffer
+    VX_CK(cudaStreamSynchronize(s));
+    if (result != SIM_OK) return result;
+    for (int k = 0; k < kNumClasses; ++k) {
+        if (kind_out) kind_out[k] = ctx->class_kind[k];
+        if (threads_out) threads_out[k] = ctx->class_threads[k];
+    }
     return SIM_OK;
 }
 

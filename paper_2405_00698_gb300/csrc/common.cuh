@@ -92,8 +92,8 @@ cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, co
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
                             int2* spr_ab, float4* spr_p, float4* spr_pack, uint32_t* cflags,
-                            float* prm, int* corner_order, float4* x0, float4* x, float4* v,
-                            double* x0c, int* status, int max_threads, cudaStream_t s);
+                            float* prm, float4* x0, float4* x, float4* v, double* x0c, int* status,
+                            int max_threads, cudaStream_t s);
 
 cudaError_t launch_sincos_table(double omega, double dt, int64_t step0, int n, float2* out,
                                 cudaStream_t s);
@@ -124,7 +124,7 @@ cudaError_t launch_step_resident(const ResidentArgs& a, int grid, int threads, s
 // Lattice-gather path (deterministic): work items of robots of one size class.
 struct LatticeArgs {
     PopView pv;
-    const int* corner_order; // per robot at moff: the mass corners in thread order
+    const int* corner_order; // per robot at moff: the mass corners (ascending), one per thread
     const uint32_t* cflags;  // per corner: forward mask bits 0..12, backward 16..28, mass bit 31
     const float* prm;        // per robot at 39 * moff: [3][13][C] (k, alpha L0, beta L0)
     float4* u;               // per corner displacement (rest height in .w)

@@ -61,8 +61,9 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             const int S = gthreads;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
             float4* fb = su + S;               // plane d at fb + d * S: force on a of spring (a, d)
-            // thread lt owns the lt-th mass in the robot's thread order (masses grouped by their
-            // spring masks); threads past the mass count only take part in the barriers
+            // thread lt owns the lt-th mass (ascending corner order: neighbouring threads touch
+            // neighbouring shared-memory rows); threads past the mass count only take part in the
+            // barriers
             const int M = a.pv.n_mass[r];
             const bool in = lt < M;
             const int cidx = in ? a.corner_order[mo + lt] : 0;

@@ -14,7 +14,6 @@ namespace vx {
 namespace {
 
 constexpr int kTopoThreads = 1024;
-constexpr int kSortCapacity = 1024;   // robots up to this many corners get a sorted thread order
 
 // The 13 corner offsets (dx, dy, dz) that point to a larger corner id, in increasing order of
 // (dz, dy, dx): from a fixed corner they reach larger corners in increasing corner-id order.
@@ -109,8 +108,7 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
            const float* __restrict__ phi_all, MatConst mc, double edge, int* label_all,
            int* count_all, int* corner_mass_all, int* mass_corner_all, int2* spr_ab_all,
            float4* spr_p_all, float4* spr_pack_all, uint32_t* cflags_all, float* prm_all,
-           int* corner_order_all, float4* x0_all, float4* x_all, float4* v_all, double* x0c,
-           int* status)
+           float4* x0_all, float4* x_all, float4* v_all, double* x0c, int* status)
 {
     __shared__ int sh_scan[32];
     __shared__ int sh_changed;
@@ -347,36 +345,6 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
         }
         cflags[c] |= bw;
     }
-    if (!corner_order_all || C > kSortCapacity) return;
-    // 10. thread order of the lattice kernels: the mass corners sorted by their spring masks, so
-    //     neighbouring threads take the same lattice directions (fewer idle lanes per warp).
-    //     Bitonic sort of (mask << 32 | corner) keys in shared memory; entries without a mass
-    //     sort last.
-    __shared__ unsigned long long sh_keys[kSortCapacity];
-    __syncthreads();
-    for (int i = tid; i < kSortCapacity; i += T) {
-        unsigned long long key = ~0ull;
-        if (i < C) {
-            const uint32_t f = cflags[i];
-            if (f >> 31) key = ((unsigned long long)((f & 0x1fffu) | ((f >> 16) & 0x1fffu) << 13) << 32) | (unsigned)i;
-        }
-        sh_keys[i] = key;
-    }
-    __syncthreads();
-    for (int k = 2; k <= kSortCapacity; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < kSortCapacity; i += T) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = sh_keys[i], b = sh_keys[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { sh_keys[i] = b; sh_keys[l] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    int* corner_order = corner_order_all + mo;
-    for (int i = tid; i < M; i += T) corner_order[i] = (int)(sh_keys[i] & 0xffffffffull);
 }
 
 }  // namespace
@@ -385,14 +353,14 @@ cudaError_t launch_topology(PopView pv, const uint8_t* mat_raw, uint8_t* mat, co
                             const float* kappa, const float* phi, MatConst mc, double edge,
                             int* label, int* count, int* corner_mass, int* mass_corner,
                             int2* spr_ab, float4* spr_p, float4* spr_pack, uint32_t* cflags,
-                            float* prm, int* corner_order, float4* x0, float4* x, float4* v,
-                            double* x0c, int* status, int max_threads, cudaStream_t s)
+                            float* prm, float4* x0, float4* x, float4* v, double* x0c, int* status,
+                            int max_threads, cudaStream_t s)
 {
     if (pv.P == 0) return cudaSuccess;
     int T = max_threads > 0 && max_threads < kTopoThreads ? max_threads : kTopoThreads;
     k_topology<<<pv.P, T, 0, s>>>(pv, mat_raw, mat, w, kappa, phi, mc, edge, label, count,
                                   corner_mass, mass_corner, spr_ab, spr_p, spr_pack, cflags, prm,
-                                  corner_order, x0, x, v, x0c, status);
+                                  x0, x, v, x0c, status);
     return cudaGetLastError();
 }
 

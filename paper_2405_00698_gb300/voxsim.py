@@ -24,7 +24,7 @@ GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "sim_set_checkpointing",
-           "sim_backward", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_backward", "sim_autotune", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 
@@ -87,6 +87,7 @@ def lib():
             "evo_generation_static": [vp, vp, vp, i32, i32, vp, u64, vp, vp, vp],
             "sim_set_checkpointing": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
+            "sim_autotune": [vp, i32, vp, vp],
             "sim_get_counts": [vp, vp, vp],
             "sim_get_state": [vp, vp, vp, vp, i32],
             "sim_get_voxels": [vp, vp, vp, vp, vp, vp],
@@ -205,6 +206,13 @@ class Simulator:
         p, mem = _ptr(out)
         _check(lib().sim_fitness(self._h, p, mem))
         return out
+
+    def autotune(self, n_steps: int = 50):
+        """Time the admissible stepping kernels per size class and keep the fastest; returns
+        (kind [10], threads [10]) with kind 0 lattice, 1 atomic resident, 2 streamed."""
+        kind = np.zeros(10, np.int32); threads = np.zeros(10, np.int32)
+        _check(lib().sim_autotune(self._h, int(n_steps), kind.ctypes.data, threads.ctypes.data))
+        return kind, threads
 
     def counts(self):
         M = np.empty(self.P, np.int32); S = np.empty(self.P, np.int32)
