@@ -59,7 +59,8 @@ enum {
 enum {
     SIM_ACC_AUTO = 0,   /* library choice (measured default) */
     SIM_ACC_ATOMIC = 1, /* per-spring threads add into per-mass accumulators atomically */
-    SIM_ACC_GATHER = 2  /* per-mass threads gather their springs' forces in a fixed order:
+    SIM_ACC_GATHER = 2  /* every mass sums its springs' forces in a fixed order (lattice-gather
+                           kernel, or the streamed path for robots too large for it):
                            bit-reproducible */
 };
 

@@ -487,7 +487,10 @@ static void default_choices(voxsim_ctx* ctx)
     for (int k = 0; k < kNumClasses; ++k) {
         const int C = std::min(kClassCorners[k], kResidentMaxCorner);
         const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
-        ctx->class_kind[k] = k < 6 ? kKindLattice : (fits ? kKindAtomic : kKindStreamed);
+        int kind = k < 6 ? kKindLattice : (fits ? kKindAtomic : kKindStreamed);
+        if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindStreamed;
+        if (kind == kKindLattice && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
+        ctx->class_kind[k] = kind;
         ctx->class_threads[k] = 0;
     }
 }

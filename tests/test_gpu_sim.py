@@ -223,8 +223,15 @@ def test_atomic_path_matches_oracle(vs, orc):
     check_population(orc, pop, PHYS, 500, g["f"], g["x"], g["off"], ref)
 
 
-def test_gather_mode_rejects_robots_beyond_the_lattice_block(vs):
-    sim = vs.Simulator(PHYS, accumulate=vs.ACC_GATHER)
-    with pytest.raises(vs.VoxsimError):
-        sim.set_population([[12, 12, 12]], np.full(1728, 4, np.uint8))
-    sim.close()
+def test_gather_mode_routes_large_robots_to_the_deterministic_streamed_path(vs):
+    """Under bit-reproducible stepping a robot larger than a lattice block runs streamed (the
+    same fixed summation order), and two runs agree bitwise."""
+    pop = W.population_uneven(3, seed=26, sizes=(12,))
+    out = []
+    for _ in range(2):
+        sim = vs.Simulator(PHYS, accumulate=vs.ACC_GATHER)
+        sim.set_population_from(pop)
+        sim.step(101)
+        out.append(sim.state()[0])
+        sim.close()
+    assert np.array_equal(out[0], out[1])
