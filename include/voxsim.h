@@ -221,6 +221,16 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
                         float* g_phi);
 
+/* Population diversity (Fig. 3(b) plots a "diversity curve" without defining it; these are the
+ * definitions used here), FP64 on the GPU:
+ *   out[0] genome diversity: root mean square of the pairwise Euclidean distances between the P
+ *          genomes (device float [P][G]; NULL skips it and leaves NaN);
+ *   out[1] morphology diversity: mean over robot pairs of the fraction of voxels whose kept
+ *          materials differ, for the current population when it has P robots on one grid shape
+ *          (NaN otherwise).
+ * out: host double [2].  Synchronises the stream.  Errors: SIM_EINVAL for P < 2. */
+sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32_t G, double* out);
+
 /* Per-size autotuner of the stepping kernels (project-written; the paper has no counterpart).
  * Robots are grouped by grid-corner count into 10 classes (up to 64, 128, 192, 256, 384, 768,
  * 1536, 2560, 5120 corners, and more).  For every class present in the population, each

@@ -88,6 +88,8 @@ def lib():
             L.orc_fitness_after.restype = d
             L.orc_robot_adjoint.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp, vp]
             L.orc_robot_adjoint.restype = d
+            L.orc_genome_diversity.argtypes = [i32, i32, vp]; L.orc_genome_diversity.restype = d
+            L.orc_morphology_diversity.argtypes = [i32, i32, vp]; L.orc_morphology_diversity.restype = d
             _lib = L
     return _lib
 
@@ -273,3 +275,18 @@ def adjoint(mat, dims, phys, nsteps, dL_df=1.0, w=None, kappa=None, phi=None, ap
                                 int(bool(apply_lcc)), int(nsteps), float(dL_df), _p(lxf),
                                 _p(gw), _p(gk), _p(gp))
     return f, gw, gk, gp
+
+
+# ------------------------------------------------------------------------------------------
+# Diversity
+# ------------------------------------------------------------------------------------------
+
+def genome_diversity(genomes) -> float:
+    g = np.ascontiguousarray(np.asarray(genomes, dtype=np.float32))
+    return lib().orc_genome_diversity(g.shape[0], g.shape[1], _p(g))
+
+
+def morphology_diversity(mats) -> float:
+    """mats: uint8 [P, V] material grids of one shape."""
+    m = np.ascontiguousarray(np.asarray(mats, dtype=np.uint8))
+    return lib().orc_morphology_diversity(m.shape[0], m.shape[1], _p(m))

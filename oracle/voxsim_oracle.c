@@ -867,3 +867,39 @@ double orc_robot_adjoint(int nx, int ny, int nz, const uint8_t* mat, const doubl
     orc_robot_free(R);
     return fit;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Population diversity (the paper's Fig. 3(b) "diversity curve"; definitions taken here).      */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Root mean square of the pairwise Euclidean distances between P genomes of G values, summed
+ * over all ordered pairs i != j (plain double loops). */
+double orc_genome_diversity(int P, int G, const float* g)
+{
+    double acc = 0.0;
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+            if (i == j) continue;
+            double d2 = 0.0;
+            for (int k = 0; k < G; ++k) {
+                double d = (double)g[(size_t)i * G + k] - (double)g[(size_t)j * G + k];
+                d2 += d * d;
+            }
+            acc += d2;
+        }
+    return sqrt(acc / ((double)P * (P - 1)));
+}
+
+/* Mean over unordered robot pairs of the fraction of voxels (V per robot) whose materials
+ * differ. */
+double orc_morphology_diversity(int P, int V, const uint8_t* mat)
+{
+    double acc = 0.0;
+    for (int i = 0; i < P; ++i)
+        for (int j = i + 1; j < P; ++j) {
+            int diff = 0;
+            for (int v = 0; v < V; ++v) diff += mat[(size_t)i * V + v] != mat[(size_t)j * V + v];
+            acc += (double)diff / V;
+        }
+    return acc / (0.5 * P * (P - 1));
+}

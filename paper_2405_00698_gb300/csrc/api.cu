@@ -918,6 +918,29 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     return SIM_OK;
 }
 
+// Diversity of a population: genomes (optional, device [P][G]) and the current population's
+// kept material grids (all robots on one grid shape).
+sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32_t G, double* out)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!out) return fail(SIM_EINVAL, "null output");
+    if (P < 2) return fail(SIM_EINVAL, "diversity needs at least two robots");
+    if (genomes && G < 1) return fail(SIM_EINVAL, "G must be >= 1");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    bool morph = ctx->have_pop && ctx->P == P && P > 0;
+    for (int r = 1; morph && r < P; ++r)
+        morph = ctx->dims[3 * r] == ctx->dims[0] && ctx->dims[3 * r + 1] == ctx->dims[1] && ctx->dims[3 * r + 2] == ctx->dims[2];
+    const int V = morph ? ctx->dims[0] * ctx->dims[1] * ctx->dims[2] : 0;
+    VX_CK(ctx->d_fit.ensure(std::max(2, ctx->P)));
+    VX_LAUNCH(ctx, launch_diversity(genomes, P, genomes ? G : 0, morph ? ctx->d_mat.p : nullptr, V, ctx->d_fit.p, s));
+    double tot[2];
+    if (sim_status st = copy_out(tot, ctx->d_fit.p, sizeof(tot), SIM_MEM_HOST, s)) return st;
+    out[0] = genomes ? std::sqrt(2.0 * tot[0] / (P - 1.0)) : NAN;
+    out[1] = morph ? tot[1] / (0.5 * P * (P - 1.0)) / V : NAN;
+    return SIM_OK;
+}
+
 // Per size class, time every admissible kernel on a sample of the class's robots (up to two per
 // SM) for n_steps steps from the current state, keep the fastest, restore the state.
 sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out)

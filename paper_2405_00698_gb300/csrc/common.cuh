@@ -212,6 +212,11 @@ cudaError_t launch_evo_children(const float* gin, float* gout, const int* order,
 cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float4* src,
                                  const float4* add, float* dst, const int64_t* dst_off, cudaStream_t s);
 
+// Population diversity totals (see fitness_evo.cu): totals[0] = sum of squared deviations of the
+// genomes from their mean, totals[1] = number of (robot pair, voxel) disagreements.
+cudaError_t launch_diversity(const float* genomes, int P, int G, const uint8_t* mat, int V, double* totals,
+                             cudaStream_t s);
+
 // Record a failure message for sim_last_error() on this thread and return `st`.
 sim_status vx_fail(sim_status st, const char* fmt, ...);
 

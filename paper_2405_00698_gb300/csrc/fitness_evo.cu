@@ -228,3 +228,58 @@ cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float
 }
 
 }  // namespace vx
+
+// ----------------------------------------------------------------------------------------------
+// Population diversity (logged per generation beside the fitness, Fig. 3(b) "diversity"):
+//   genome: root of the mean pairwise squared distance, from the identity
+//           mean_{i != j} |g_i - g_j|^2 = 2 P / (P - 1) * mean_i |g_i - mean g|^2;
+//   morphology: mean over robot pairs of the fraction of voxels whose kept materials differ,
+//           from per-voxel material counts c_k: differing pairs = (P^2 - sum_k c_k^2) / 2.
+// FP64 accumulation; one block per gene / voxel chunk, atomics into two FP64 totals.
+// ----------------------------------------------------------------------------------------------
+namespace vx {
+namespace {
+
+__global__ void k_genome_spread(const float* __restrict__ g, int P, int G, double* __restrict__ total)
+{
+    double acc = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G; j += gridDim.x * blockDim.x) {
+        double s = 0.0, s2 = 0.0;
+        for (int i = 0; i < P; ++i) {
+            const double x = (double)g[(size_t)i * G + j];
+            s += x;
+            s2 += x * x;
+        }
+        acc += s2 - s * s / P;             // sum_i (g_ij - mean_j)^2
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(total, acc);
+}
+
+__global__ void k_morph_spread(const uint8_t* __restrict__ mat, int P, int V, double* __restrict__ total)
+{
+    double acc = 0.0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        int c[kNumMat] = {0, 0, 0, 0, 0};
+        for (int i = 0; i < P; ++i) c[mat[(size_t)i * V + v] % kNumMat]++;
+        double eq = 0.0;
+        for (int k = 0; k < kNumMat; ++k) eq += (double)c[k] * c[k];
+        acc += ((double)P * P - eq) * 0.5;  // pairs of robots that differ at voxel v
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(total, acc);
+}
+
+}  // namespace
+
+cudaError_t launch_diversity(const float* genomes, int P, int G, const uint8_t* mat, int V, double* totals,
+                             cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(totals, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    if (genomes && G > 0) k_genome_spread<<<std::min((G + 255) / 256, 1024), 256, 0, s>>>(genomes, P, G, totals);
+    if (mat && V > 0) k_morph_spread<<<std::min((V + 255) / 256, 1024), 256, 0, s>>>(mat, P, V, totals + 1);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

@@ -24,7 +24,7 @@ GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "sim_set_checkpointing",
-           "sim_backward", "sim_autotune", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_backward", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 
@@ -88,6 +88,7 @@ def lib():
             "sim_set_checkpointing": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
             "sim_autotune": [vp, i32, vp, vp],
+            "sim_diversity": [vp, vp, i32, i32, vp],
             "sim_get_counts": [vp, vp, vp],
             "sim_get_state": [vp, vp, vp, vp, i32],
             "sim_get_voxels": [vp, vp, vp, vp, vp, vp],
@@ -213,6 +214,17 @@ class Simulator:
         kind = np.zeros(10, np.int32); threads = np.zeros(10, np.int32)
         _check(lib().sim_autotune(self._h, int(n_steps), kind.ctypes.data, threads.ctypes.data))
         return kind, threads
+
+    def diversity(self, genomes=None, P: Optional[int] = None):
+        """(genome RMS pairwise distance, morphology mean pairwise disagreement fraction)."""
+        out = np.empty(2, np.float64)
+        if genomes is not None:
+            P_, G = genomes.shape
+            ptr = _ptr(genomes)[0]
+        else:
+            P_, G, ptr = (P if P is not None else self.P), 0, None
+        _check(lib().sim_diversity(self._h, ptr, int(P_), int(G), out.ctypes.data))
+        return float(out[0]), float(out[1])
 
     def counts(self):
         M = np.empty(self.P, np.int32); S = np.empty(self.P, np.int32)

@@ -482,3 +482,18 @@ def test_adjoint_with_contact_matches_fd(orc):
     samples = [(n, int(v)) for n in ("w", "kappa", "phi") for v in rng.choice(occ, 8, replace=False)]
     checked = _fd_check(orc, mat, (3, 3, 3), PHYS, 400, w, kappa, phi, samples, tol=1e-4)
     assert checked >= len(samples) // 2
+
+
+# ------------------------------------------------------------------------------------------
+# Diversity: the library routine scipy.spatial.distance.pdist
+# ------------------------------------------------------------------------------------------
+
+def test_diversity_matches_pdist(orc):
+    from scipy.spatial.distance import pdist
+    rng = np.random.default_rng(18)
+    g = rng.standard_normal((23, 57)).astype(np.float32)
+    assert abs(orc.genome_diversity(g) - np.sqrt(np.mean(pdist(g.astype(np.float64)) ** 2))) < 1e-12
+    m = rng.integers(0, 5, size=(17, 64)).astype(np.uint8)
+    assert abs(orc.morphology_diversity(m) - np.mean(pdist(m, metric="hamming"))) < 1e-12
+    same = np.tile(m[:1], (5, 1))
+    assert orc.morphology_diversity(same) == 0.0 and orc.genome_diversity(np.tile(g[:1], (4, 1))) == 0.0
