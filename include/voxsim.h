@@ -103,6 +103,10 @@ typedef struct {
     int32_t threads;    /* threads per robot on the resident path; 0 = autotuned */
     int32_t mlp_kernel; /* SIM_MLP_TENSOR (tcgen05, default) or SIM_MLP_SIMT (CUDA cores) */
     int32_t pad_;
+    double spring_zeta; /* spring dashpot damping ratio (Table II: 0.1; 0 in the configurations):
+                           c_s ((v_b - v_a) . u) u with c_s = 2 zeta sqrt(k_s mass / 2) */
+    double ground_zeta; /* ground damping ratio (Table II: 0.1): -2 zeta sqrt(k_ground mass) v_z
+                           below the ground.  The adjoint requires both to be 0 */
 } sim_params;
 
 /* Per-voxel parametrisation for SIM_MODE_PARAMS (all arrays cover every voxel of every grid):
@@ -120,7 +124,9 @@ typedef struct {
     uint32_t mut_threshold; /* a gene mutates when its 32-bit draw is below this
                                (floor(rate * 2^32)) */
     float sigma;            /* standard deviation of the Gaussian mutation */
-    int32_t pad_;
+    uint32_t keep_threshold;/* crossover rate below 1 (Table I: 0.4): a child whose draw
+                               (c, crossover) is below floor((1 - rate) 2^32) copies parent A;
+                               0 = every child is a crossover */
     uint64_t seed;          /* seed of the counter-based generator */
 } evo_params;
 
@@ -174,7 +180,8 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
  * (when draw (c, j, mutate) < mut_threshold add sigma * sqrt(-2 ln u1) cos(2 pi u2),
  * u1 = (draw(c, j, u1) + 1) / 2^32, u2 = draw(c, j, u2) / 2^32).  A draw is the high 32 bits of
  * SplitMix64 output number ((((generation << 16 | c) << 26 | j) << 3) | purpose) of the stream
- * seeded with e->seed; purposes: parent A 0, parent B 1, mask 2, mutate 3, u1 4, u2 5.
+ * seeded with e->seed; purposes: parent A 0, parent B 1, mask 2, mutate 3, u1 4, u2 5,
+ * crossover 6 (drawn at gene 0; only with a keep_threshold).
  * fitness: double [P]; genomes_in / genomes_out: float [P][G] (may alias: the input is copied
  * first); parents_out: int32 [P][2] or NULL (elites name themselves twice); mask_out: uint8
  * [P][G] or NULL (1 = gene from parent A, 0 for elites).  All device memory of the context's

@@ -40,7 +40,8 @@ class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("dt", "gravity", "mass", "edge", "damping", "k_ground",
                                            "mu_s", "mu_k", "freq", "dead_bound")] + [
         ("k_mat", C.c_double * 5), ("amp_mat", C.c_double * 5), ("phase_mat", C.c_double * 5),
-        ("ground_on", C.c_int32), ("pad_", C.c_int32)]
+        ("ground_on", C.c_int32), ("pad_", C.c_int32), ("spring_zeta", C.c_double),
+        ("ground_zeta", C.c_double)]
 
     @classmethod
     def of(cls, phys) -> "OrcParams":
@@ -52,6 +53,8 @@ class OrcParams(C.Structure):
         p.amp_mat = (C.c_double * 5)(*[float(v) for v in phys.amp_mat])
         p.phase_mat = (C.c_double * 5)(*[float(v) for v in phys.phase_mat])
         p.ground_on = 1 if phys.ground_on else 0
+        p.spring_zeta = float(getattr(phys, "spring_zeta", 0.0))
+        p.ground_zeta = float(getattr(phys, "ground_zeta", 0.0))
         return p
 
 
@@ -82,7 +85,7 @@ def lib():
             L.orc_run_population.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
             L.orc_run_population.restype = i32
             L.orc_rng_draw.argtypes = [u64, u64, u64, u64, u64]; L.orc_rng_draw.restype = u32
-            L.orc_evo_generation.argtypes = [i32, i32, vp, vp, vp, i32, u64, u64, u32, d, vp, vp, vp, vp]
+            L.orc_evo_generation.argtypes = [i32, i32, vp, vp, vp, i32, u64, u64, u32, d, u32, vp, vp, vp, vp]
             L.orc_evo_generation.restype = i32
             L.orc_fitness_after.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, i32, vp]
             L.orc_fitness_after.restype = d
@@ -230,7 +233,8 @@ def rng_draw(seed: int, gen: int, child: int, gene: int, purpose: int) -> int:
     return int(lib().orc_rng_draw(seed, gen, child, gene, purpose))
 
 
-def evo_generation(fitness, genomes, E: int, seed: int, gen: int, mut_threshold: int, sigma: float):
+def evo_generation(fitness, genomes, E: int, seed: int, gen: int, mut_threshold: int, sigma: float,
+                   keep_threshold: int = 0):
     """Returns dict(genomes f64 [P, G], order i32 [P], parents i32 [P, 2], mask u8 [P, G],
     mutate u8 [P, G])."""
     f = _f64(fitness)
@@ -239,7 +243,8 @@ def evo_generation(fitness, genomes, E: int, seed: int, gen: int, mut_threshold:
     out = np.empty((P, G)); order = np.empty(P, np.int32); par = np.empty((P, 2), np.int32)
     mask = np.empty((P, G), np.uint8); mut = np.empty((P, G), np.uint8)
     rc = lib().orc_evo_generation(P, G, _p(f), _p(g), _p(out), int(E), int(seed), int(gen),
-                                  int(mut_threshold), float(sigma), _p(order), _p(par), _p(mask), _p(mut))
+                                  int(mut_threshold), float(sigma), int(keep_threshold), _p(order),
+                                  _p(par), _p(mask), _p(mut))
     if rc != 0:
         raise ValueError("bad evolution sizes")
     return dict(genomes=out, order=order, parents=par, mask=mask, mutate=mut)

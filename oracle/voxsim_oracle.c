@@ -47,6 +47,8 @@ typedef struct {
     double phase_mat[ORC_NMAT]; /* actuation phase per material [rad] */
     int32_t ground_on;  /* 0 disables the ground (conservation pins) */
     int32_t pad_;
+    double spring_zeta; /* spring dashpot damping ratio (Table II; 0 in the configurations) */
+    double ground_zeta; /* ground damping ratio (Table II; 0 in the configurations) */
 } orc_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -491,8 +493,12 @@ enum { ORC_FREE = 0, ORC_STICK = 1, ORC_SLIP = 2 };
  *  2. every spring s = (a, b): d = x_b - x_a, l = |d|, actuated rest length
  *     L = L0 (1 + alpha_s sin(w t) + beta_s cos(w t)) with w = 2 pi freq; Hooke force
  *     f = k_s (l - L) d / l is added to mass a and subtracted from mass b;
+ *     With a spring damping ratio zeta_s > 0 (Table II; the paper's own preset), a dashpot
+ *     c_s ((v_b - v_a) . u) u with c_s = 2 zeta_s sqrt(k_s m / 2) (the critical damping of two
+ *     equal masses) is added to the spring force;
  *  3. every mass below the ground plane (z < 0) gets the penalty normal force
- *     F_n = k_ground (-z) added to F_z; with F_h = (F_x, F_y): if |F_h| <= mu_s F_n the mass
+ *     F_n = k_ground (-z) added to F_z (and, with a ground damping ratio zeta_g > 0, the dashpot
+ *     -2 zeta_g sqrt(k_ground m) v_z); with F_h = (F_x, F_y): if |F_h| <= mu_s F_n the mass
  *     sticks (F_h = 0 and horizontal velocity = 0), otherwise it slips and kinetic friction
  *     mu_k F_n is removed along F_h;
  *  4. semi-implicit Euler with velocity damping: v <- c (v + dt F / m), x <- x + dt v.
@@ -515,6 +521,13 @@ static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes
         if (l < 1e-12) { ++skipped; continue; }
         double L = R->L0[s] * (1.0 + R->alpha[s] * sn + R->beta[s] * cs);
         double fm = R->ks[s] * (l - L) / l;
+        if (p->spring_zeta > 0.0) {
+            /* dashpot along the spring: c_s ((v_b - v_a) . u) u, c_s = 2 zeta sqrt(k_s m / 2) */
+            double cs_ = 2.0 * p->spring_zeta * sqrt(R->ks[s] * p->mass / 2.0);
+            double rv = 0.0;
+            for (int q = 0; q < 3; ++q) rv += (R->v[3 * b + q] - R->v[3 * a + q]) * d[q] / l;
+            fm += cs_ * rv / l;
+        }
         for (int q = 0; q < 3; ++q) { F[3 * a + q] += fm * d[q]; F[3 * b + q] -= fm * d[q]; }
     }
     if (Fpre) memcpy(Fpre, F, sizeof(double) * 3 * (size_t)M);
@@ -524,6 +537,8 @@ static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes
         if (p->ground_on && x[2] < 0.0) {
             double fn = p->k_ground * (-x[2]);
             f[2] += fn;
+            /* ground dashpot on the normal velocity: c_g = 2 zeta sqrt(k_g m) */
+            if (p->ground_zeta > 0.0) f[2] -= 2.0 * p->ground_zeta * sqrt(p->k_ground * p->mass) * v[2];
             double fh = sqrt(f[0] * f[0] + f[1] * f[1]);
             if (fh <= p->mu_s * fn) {
                 mode = ORC_STICK;
@@ -628,7 +643,7 @@ static uint64_t orc_splitmix64(uint64_t seed, uint64_t ctr)
 
 /* Purposes of the random numbers of one generation. */
 enum { ORC_RNG_PARENT_A = 0, ORC_RNG_PARENT_B = 1, ORC_RNG_MASK = 2, ORC_RNG_MUTATE = 3,
-       ORC_RNG_GAUSS_U1 = 4, ORC_RNG_GAUSS_U2 = 5 };
+       ORC_RNG_GAUSS_U1 = 4, ORC_RNG_GAUSS_U2 = 5, ORC_RNG_CROSS = 6 };
 
 /* Counter of the draw for (generation, child, gene, purpose): the fields are packed as
  * generation | child (16 bits) | gene (26 bits) | purpose (3 bits). */
@@ -661,7 +676,9 @@ static int cmp_rank(const void* p, const void* q)
  * The E best genomes are copied unchanged into slots 0..E-1 in rank order.  Every slot c >= E
  * is a child of two elites: parent ranks floor(u * E / 2^32) for the draws (c, PARENT_A) and
  * (c, PARENT_B).  Uniform crossover: gene j comes from parent A when the top bit of draw
- * (c, j, MASK) is set, else from parent B.  Mutation: when draw (c, j, MUTATE) < mut_threshold
+ * (c, j, MASK) is set, else from parent B; with a crossover rate below 1 (Table I: 0.4), a child
+ * whose draw (c, CROSS) is below keep_threshold = floor((1 - rate) 2^32) takes every gene from
+ * parent A instead (0 = always cross).  Mutation: when draw (c, j, MUTATE) < mut_threshold
  * the gene gets sigma * z added, z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller) with
  * u1 = (draw(c, j, U1) + 1) / 2^32 and u2 = draw(c, j, U2) / 2^32.
  * order_out[P] receives the rank order, parents_out[2P] the parent genome indices (elites name
@@ -669,8 +686,9 @@ static int cmp_rank(const void* p, const void* q)
  * (0 for elites).  All outputs but genomes_out are optional.  Returns 0, or -1 on bad sizes. */
 int orc_evo_generation(int P, int G, const double* fitness, const float* genomes_in,
                        double* genomes_out, int E, uint64_t seed, uint64_t gen,
-                       uint32_t mut_threshold, double sigma, int32_t* order_out,
-                       int32_t* parents_out, uint8_t* mask_out, uint8_t* mutate_out)
+                       uint32_t mut_threshold, double sigma, uint32_t keep_threshold,
+                       int32_t* order_out, int32_t* parents_out, uint8_t* mask_out,
+                       uint8_t* mutate_out)
 {
     if (P <= 0 || G <= 0 || E <= 0 || E > P || P > 65536 || G > (1 << 26)) return -1;
     double* key = (double*)malloc(sizeof(double) * (size_t)P);
@@ -690,8 +708,9 @@ int orc_evo_generation(int P, int G, const double* fitness, const float* genomes
         int pa = order[(int)(((uint64_t)ua * (uint64_t)E) >> 32)];
         int pb = order[(int)(((uint64_t)ub * (uint64_t)E) >> 32)];
         if (parents_out) { parents_out[2 * c] = pa; parents_out[2 * c + 1] = pb; }
+        int copy_a = orc_draw(seed, gen, (uint64_t)c, 0, ORC_RNG_CROSS) < keep_threshold;
         for (int j = 0; j < G; ++j) {
-            int from_a = (int)(orc_draw(seed, gen, (uint64_t)c, (uint64_t)j, ORC_RNG_MASK) >> 31);
+            int from_a = copy_a ? 1 : (int)(orc_draw(seed, gen, (uint64_t)c, (uint64_t)j, ORC_RNG_MASK) >> 31);
             double g = from_a ? genomes_in[(size_t)pa * G + j] : genomes_in[(size_t)pb * G + j];
             int mut = orc_draw(seed, gen, (uint64_t)c, (uint64_t)j, ORC_RNG_MUTATE) < mut_threshold;
             if (mut) {

@@ -177,7 +177,7 @@ struct voxsim_ctx {
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
     DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
     DevBuf<int2> d_sab;
-    DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v, d_x_alt;
+    DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v, d_x_alt, d_v_alt;
     DevBuf<float> d_plain_f;       // force accumulators of the plain path (3 per corner)
     DevBuf<double> d_x0c, d_keys, d_fit;
     DevBuf<float2> d_sc;
@@ -236,6 +236,9 @@ struct voxsim_ctx {
         c.edge_sqrt2 = (float)(p.edge * 1.4142135623730951);
         c.edge_sqrt3 = (float)(p.edge * 1.7320508075688772);
         c.ground_on = p.ground_on ? 1 : 0;
+        c.spring_c = (float)(2.0 * p.spring_zeta * std::sqrt(p.mass / 2.0));
+        c.ground_c = (float)(2.0 * p.ground_zeta * std::sqrt(p.k_ground * p.mass));
+        c.damped = p.spring_zeta > 0.0 ? 1 : 0;
         return c;
     }
 };
@@ -594,9 +597,11 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         VX_CK(ctx->d_stream.ensure(streamed.size()));
         VX_CK(cudaMemcpyAsync(ctx->d_stream.p, streamed.data(), sizeof(int) * streamed.size(),
                               cudaMemcpyHostToDevice, s));
-        // both position buffers start equal (corners without a mass are never rewritten)
+        // both state buffers start equal (corners without a mass are never rewritten)
         VX_CK(ctx->d_x_alt.ensure(ctx->M_cap));
+        VX_CK(ctx->d_v_alt.ensure(ctx->M_cap));
         VX_CK(cudaMemcpyAsync(ctx->d_x_alt.p, ctx->d_x.p, sizeof(float4) * ctx->M_cap, cudaMemcpyDeviceToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_v_alt.p, ctx->d_v.p, sizeof(float4) * ctx->M_cap, cudaMemcpyDeviceToDevice, s));
     }
     VX_CK(ctx->d_items.ensure(items.size()));
     VX_CK(ctx->d_item_robots.ensure(robots.size()));
@@ -729,7 +734,6 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
     a.pv = ctx->view();
     a.cflags = ctx->d_cflags.p;
     a.prm = ctx->d_prm.p;
-    a.v = ctx->d_v.p;
     a.sc = ctx->d_sc.p;
     a.c = ctx->stepconst();
     a.robots = ctx->d_stream.p;
@@ -737,12 +741,16 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
     for (int i = 0; i < n; ++i) {
         a.u_in = (i & 1) ? ctx->d_x_alt.p : ctx->d_x.p;
         a.u_out = (i & 1) ? ctx->d_x.p : ctx->d_x_alt.p;
+        a.v_in = (i & 1) ? ctx->d_v_alt.p : ctx->d_v.p;
+        a.v_out = (i & 1) ? ctx->d_v.p : ctx->d_v_alt.p;
         VX_CK(launch_step_streamed(a, i, ctx->max_stream_corner, s));
     }
     if (n & 1)
         for (int r : ctx->stream_robots) {
             const size_t o = (size_t)ctx->moff[r], len = (size_t)(ctx->moff[r + 1] - ctx->moff[r]);
             VX_CK(cudaMemcpyAsync(ctx->d_x.p + o, ctx->d_x_alt.p + o, sizeof(float4) * len,
+                                  cudaMemcpyDeviceToDevice, s));
+            VX_CK(cudaMemcpyAsync(ctx->d_v.p + o, ctx->d_v_alt.p + o, sizeof(float4) * len,
                                   cudaMemcpyDeviceToDevice, s));
         }
     return SIM_OK;
@@ -851,7 +859,7 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
     }
     VX_LAUNCH(ctx, launch_evo_rank(fitness, P, ctx->d_order.p, s));
     VX_LAUNCH(ctx, launch_evo_children(src, genomes_out, ctx->d_order.p, P, G, e->elites, e->seed, generation,
-                              e->mut_threshold, e->sigma, parents_out, mask_out, s));
+                              e->mut_threshold, e->sigma, e->keep_threshold, parents_out, mask_out, s));
     return SIM_OK;
 }
 
@@ -861,6 +869,8 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
     if (k_steps < 0) return fail(SIM_EINVAL, "k_steps must be >= 0");
     if (k_steps > 0 && ctx->p.accumulate == SIM_ACC_ATOMIC)
         return fail(SIM_EINVAL, "checkpointing needs the bit-reproducible stepping (not SIM_ACC_ATOMIC)");
+    if (k_steps > 0 && (ctx->p.spring_zeta != 0.0 || ctx->p.ground_zeta != 0.0))
+        return fail(SIM_EINVAL, "the adjoint is built for undamped springs and ground (zeta = 0)");
     ctx->ckpt_every = k_steps;
     ctx->rec_valid = false;
     return SIM_OK;
@@ -997,8 +1007,10 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
             for (int rep = 0; rep < 2 && result == SIM_OK; ++rep) {    // warm-up run, timed run
                 VX_CK(cudaMemcpyAsync(ctx->d_x.p, snap_u.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
                 VX_CK(cudaMemcpyAsync(ctx->d_v.p, snap_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
-                if (ctx->n_stream > 0)
+                if (ctx->n_stream > 0) {
                     VX_CK(cudaMemcpyAsync(ctx->d_x_alt.p, snap_u.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+                    VX_CK(cudaMemcpyAsync(ctx->d_v_alt.p, snap_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
+                }
                 VX_CK(cudaEventRecord(e0, s));
                 if ((result = step_lattice(ctx, n_steps)) != SIM_OK) break;
                 if ((result = step_resident(ctx, n_steps)) != SIM_OK) break;

@@ -55,6 +55,9 @@ struct StepConst {
     float edge_sqrt2;
     float edge_sqrt3;
     int ground_on;
+    int damped;         // spring dashpots present (spring_c > 0)
+    float spring_c;     // 2 zeta_s sqrt(mass / 2): dashpot coefficient = spring_c sqrt(k)
+    float ground_c;     // 2 zeta_g sqrt(k_ground mass)
 };
 
 // Device view of a population's layout.
@@ -150,7 +153,8 @@ struct StreamArgs {
     const float* prm;
     const float4* u_in;      // positions at the start of the step (per corner)
     float4* u_out;           // positions at its end
-    float4* v;               // velocities (updated in place)
+    const float4* v_in;      // velocities at the start of the step
+    float4* v_out;           // velocities at its end
     const float2* sc;        // sin / cos of w t per step of this call (indexed by the step)
     StepConst c;
     const int* robots;       // streamed robots (grid.y)
@@ -196,7 +200,7 @@ cudaError_t launch_adjoint_voxels(const uint8_t* mat, const float* w, const floa
                                   const float* g_b, int64_t n, float* g_w, float* g_kappa,
                                   float* g_phi, cudaStream_t s);
 int lattice_max_threads();
-constexpr int kLatticeSlotVec4 = 14;     // shared float4 per corner slot: u + 13 force planes
+constexpr int kLatticeSlotVec4 = 15;     // shared float4 per corner slot: u, v, 13 force planes
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s);
 size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);
@@ -207,7 +211,7 @@ cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, 
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s);
 cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
                                 int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
-                                int* parents, uint8_t* mask, cudaStream_t s);
+                                uint32_t keep, int* parents, uint8_t* mask, cudaStream_t s);
 
 cudaError_t launch_compact_state(PopView pv, const int* mass_corner, const float4* src,
                                  const float4* add, float* dst, const int64_t* dst_off, cudaStream_t s);

@@ -75,7 +75,7 @@ extern "C" sim_status evo_generation_static(const double* fitness, const float* 
     err = launch_evo_rank(fitness, P, order, s);
     if (err != cudaSuccess) return vx_fail(SIM_ECUDA, "rank kernel: %s", cudaGetErrorString(err));
     err = launch_evo_children(genomes_in, genomes_out, order, P, G, e->elites, e->seed, generation,
-                              e->mut_threshold, e->sigma, parents_out, mask_out, s);
+                              e->mut_threshold, e->sigma, e->keep_threshold, parents_out, mask_out, s);
     if (err != cudaSuccess) return vx_fail(SIM_ECUDA, "crossover kernel: %s", cudaGetErrorString(err));
     return SIM_OK;
 }

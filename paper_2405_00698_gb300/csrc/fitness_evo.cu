@@ -63,7 +63,7 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr)
     return z ^ (z >> 31);
 }
 
-enum { kParentA = 0, kParentB = 1, kMask = 2, kMutate = 3, kU1 = 4, kU2 = 5 };
+enum { kParentA = 0, kParentB = 1, kMask = 2, kMutate = 3, kU1 = 4, kU2 = 5, kCross = 6 };
 
 // High 32 bits of the draw for (generation, child, gene, purpose), fields packed as
 // generation | child (16 bits) | gene (26 bits) | purpose (3 bits).
@@ -105,8 +105,8 @@ __global__ void k_rank(const double* __restrict__ f, int P, int* __restrict__ or
 // crossover mask and mutation from the counter-based generator.
 __global__ void k_children(const float* __restrict__ gin, float* __restrict__ gout,
                            const int* __restrict__ order, int P, int G, int E, uint64_t seed,
-                           uint64_t gen, uint32_t thresh, float sigma, int* __restrict__ parents,
-                           uint8_t* __restrict__ mask)
+                           uint64_t gen, uint32_t thresh, float sigma, uint32_t keep,
+                           int* __restrict__ parents, uint8_t* __restrict__ mask)
 {
     const int c = blockIdx.y;
     const size_t row = (size_t)c * G;
@@ -132,8 +132,10 @@ __global__ void k_children(const float* __restrict__ gin, float* __restrict__ go
     }
     const float* A = gin + (size_t)pa * G;
     const float* Bp = gin + (size_t)pb * G;
+    // crossover rate below 1: some children copy parent A (a draw per child)
+    const bool copy_a = keep != 0u && draw32(seed, gen, c, 0, kCross) < keep;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G; j += gridDim.x * blockDim.x) {
-        const uint32_t m = draw32(seed, gen, c, j, kMask) >> 31;
+        const uint32_t m = copy_a ? 1u : draw32(seed, gen, c, j, kMask) >> 31;
         float g = m ? A[j] : Bp[j];
         if (draw32(seed, gen, c, j, kMutate) < thresh) {
             const float u1 = ((float)draw32(seed, gen, c, j, kU1) + 1.0f) * 2.3283064365386963e-10f;
@@ -200,13 +202,13 @@ cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream
 
 cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
                                 int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
-                                int* parents, uint8_t* mask, cudaStream_t s)
+                                uint32_t keep, int* parents, uint8_t* mask, cudaStream_t s)
 {
     const int T = 256;
     int bx = (G + T - 1) / T;
     if (bx > 64) bx = 64;
     dim3 grid(bx, P);
-    k_children<<<grid, T, 0, s>>>(gin, gout, order, P, G, E, seed, gen, thresh, sigma, parents,
+    k_children<<<grid, T, 0, s>>>(gin, gout, order, P, G, E, seed, gen, thresh, sigma, keep, parents,
                                   mask);
     return cudaGetLastError();
 }

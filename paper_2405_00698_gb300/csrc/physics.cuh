@@ -109,12 +109,26 @@ __device__ __forceinline__ void for_each_dir(F&& f)
     }
 }
 
+// Spring dashpot of the paper's preset (Table II spring damping ratio): adds
+// c_s ((v_b - v_a) . u) u to the force on a, c_s = spring_c sqrt(k) (spring_c = 2 zeta sqrt(m / 2)).
+__device__ __forceinline__ void spring_dashpot(SpringEval& e, float dvx, float dvy, float dvz, float k,
+                                               const StepConst& c)
+{
+    const float cs = __fmul_rn(c.spring_c, __fsqrt_rn(k));
+    const float rv = __fmul_rn(__fmaf_rn(e.dz, dvz, __fmaf_rn(e.dy, dvy, __fmul_rn(e.dx, dvx))), e.inv);
+    const float fd = __fmul_rn(__fmul_rn(cs, rv), e.inv);      // per unit of d
+    e.gx = __fmaf_rn(fd, e.dx, e.gx);
+    e.gy = __fmaf_rn(fd, e.dy, e.gy);
+    e.gz = __fmaf_rn(fd, e.dz, e.gz);
+}
+
 // Contact modes of a mass in one step.
 enum : unsigned { kFree = 0u, kStick = 1u, kSlip = 2u };
 
 // Gravity, ground contact with static / kinetic friction, and the semi-implicit Euler update of
 // one mass, given the summed spring force F.  Returns the contact mode.
-//   below the ground (z = z0 + uz < 0): normal force F_n = k_g (-z) added to F_z; with
+//   below the ground (z = z0 + uz < 0): normal force F_n = k_g (-z) added to F_z (and the ground
+//   dashpot -c_g v_z of the paper's preset); with
 //   F_h = (F_x, F_y): stick (|F_h| <= mu_s F_n) zeroes F_h and the horizontal velocity, slip
 //   removes mu_k F_n along F_h;
 //   v <- c (v + dt F / m), u <- u + dt v.
@@ -127,6 +141,7 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
     if (c.ground_on && z < 0.f) {
         const float fn = __fmul_rn(c.k_ground, -z);
         Fz = __fadd_rn(Fz, fn);
+        if (c.ground_c > 0.f) Fz = __fsub_rn(Fz, __fmul_rn(c.ground_c, v.z));   // ground dashpot
         const float fh = __fsqrt_rn(__fmaf_rn(Fy, Fy, __fmul_rn(Fx, Fx)));
         if (fh <= __fmul_rn(c.mu_s, fn)) {
             mode = kStick;

@@ -13,7 +13,7 @@
 //            registers and publishes its new u.
 // Two block barriers per step, no atomics, and a fixed summation order (own forward springs by
 // direction, then backward springs by direction): bit-reproducible.
-// Shared memory per robot slot: u (float4 per corner) + 13 float4 force planes.
+// Shared memory per robot slot: u and v (float4 per corner) + 13 float4 force planes.
 // The state is the displacement from the rest lattice (rest height z0 in u.w), so a spring
 // vector is d0 + (u_b - u_a) with d0 the exact lattice offset and the extension is formed without
 // cancellation: l - L0 = (2 d0.du + du.du) / (l + L0).
@@ -30,6 +30,9 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// DAMPED: spring dashpots of the paper's preset (a separate instantiation, so the undamped path
+// keeps its registers).
+template <bool DAMPED>
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -60,7 +63,8 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             // shared-memory slot of this group (S = gthreads corners): u, then 13 force planes
             const int S = gthreads;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
-            float4* fb = su + S;               // plane d at fb + d * S: force on a of spring (a, d)
+            float4* sv = su + S;               // velocities (read by spring dashpots)
+            float4* fb = sv + S;               // plane d at fb + d * S: force on a of spring (a, d)
             // thread lt owns the lt-th mass (ascending corner order: neighbouring threads touch
             // neighbouring shared-memory rows); threads past the mass count only take part in the
             // barriers
@@ -80,7 +84,10 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             const bool mass = (fl >> 31) & 1u;
-            if (in) su[cidx] = u;
+            if (in) {
+                su[cidx] = u;
+                if (DAMPED) sv[cidx] = v;
+            }
             group_sync(bar, gthreads);
             for (int n = 0; n < a.nsteps; ++n) {
                 if (a.ckpt_u && in && n % a.ckpt_every == 0) {   // state at the start of segment n / K
@@ -95,9 +102,13 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> d) & 1u)) return;
                     const float4 ub = su[cidx + lattice_offset<d>(X, XY)];
-                    const SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
-                                                            __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c),
-                                                            pk[d], pa[d], pb[d], sc.x, sc.y);
+                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
+                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c),
+                                                      pk[d], pa[d], pb[d], sc.x, sc.y);
+                    if constexpr (DAMPED) {
+                        const float4 vb = sv[cidx + lattice_offset<d>(X, XY)];
+                        spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[d], c);
+                    }
                     Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
                     fb[d * S + cidx] = make_float4(e.gx, e.gy, e.gz, 0.f);
                 });
@@ -112,6 +123,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                 if (mass) {
                     mass_update(u, v, Fx, Fy, Fz, c);
                     su[cidx] = u;
+                    if (DAMPED) sv[cidx] = v;
                 }
                 group_sync(bar, gthreads);
             }
@@ -131,9 +143,10 @@ int lattice_max_threads() { return kMaxLatticeThreads; }
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_step_lattice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kernel = a.c.damped ? k_step_lattice<true> : k_step_lattice<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_step_lattice<<<grid, threads, smem, s>>>(a);
+    kernel<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

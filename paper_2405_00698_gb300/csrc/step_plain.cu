@@ -14,8 +14,8 @@ constexpr int kPlainThreads = 256;
 
 __global__ void __launch_bounds__(kPlainThreads)
 k_plain_springs(const int2* __restrict__ ab, const float4* __restrict__ prm, const int* __restrict__ mass_corner,
-                const float4* __restrict__ u, float* __restrict__ F, int S, int X, int XY, const float2* sc_tab,
-                int n, StepConst c)
+                const float4* __restrict__ u, const float4* __restrict__ v, float* __restrict__ F, int S, int X,
+                int XY, const float2* sc_tab, int n, StepConst c)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -26,8 +26,12 @@ k_plain_springs(const int2* __restrict__ ab, const float4* __restrict__ prm, con
     const int ox = cb % X - ca % X, oy = (cb / X) % (XY / X) - (ca / X) % (XY / X), oz = cb / XY - ca / XY;
     const float4 ua = u[ca], ub = u[cb];
     const float2 sc = sc_tab[n];
-    const SpringEval ev = spring_eval_rt(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y), __fsub_rn(ub.z, ua.z),
-                                         ox, oy, oz, c.edge, p.x, p.y, p.z * p.x, p.w * p.x, sc.x, sc.y);
+    SpringEval ev = spring_eval_rt(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y), __fsub_rn(ub.z, ua.z),
+                                   ox, oy, oz, c.edge, p.x, p.y, p.z * p.x, p.w * p.x, sc.x, sc.y);
+    if (c.damped) {
+        const float4 va = v[ca], vb = v[cb];
+        spring_dashpot(ev, __fsub_rn(vb.x, va.x), __fsub_rn(vb.y, va.y), __fsub_rn(vb.z, va.z), p.y, c);
+    }
     atomicAdd(&F[3 * ca + 0], ev.gx); atomicAdd(&F[3 * ca + 1], ev.gy); atomicAdd(&F[3 * ca + 2], ev.gz);
     atomicAdd(&F[3 * cb + 0], -ev.gx); atomicAdd(&F[3 * cb + 1], -ev.gy); atomicAdd(&F[3 * cb + 2], -ev.gz);
 }
@@ -55,7 +59,7 @@ cudaError_t launch_step_plain_robot(const int2* ab, const float4* prm, const int
 {
     const int X = nx + 1, XY = (nx + 1) * (ny + 1);
     if (S > 0) k_plain_springs<<<(S + kPlainThreads - 1) / kPlainThreads, kPlainThreads, 0, s>>>(
-        ab, prm, mass_corner, u, F, S, X, XY, sc, n, c);
+        ab, prm, mass_corner, u, v, F, S, X, XY, sc, n, c);
     if (M > 0) k_plain_masses<<<(M + kPlainThreads - 1) / kPlainThreads, kPlainThreads, 0, s>>>(mass_corner, u, v, F, M, c);
     return cudaGetLastError();
 }

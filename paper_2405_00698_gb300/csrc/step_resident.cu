@@ -14,6 +14,7 @@
 // Blocks are persistent: each pops the next robot from a work counter over a longest-first
 // order, so an uneven population runs in one launch.
 #include "common.cuh"
+#include "physics.cuh"
 
 namespace vx {
 namespace {
@@ -93,7 +94,12 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
                 const float num = 2.0f * (d0.x * dux + d0.y * duy + d0.z * duz) +
                                   (dux * dux + duy * duy + duz * duz);
                 const float ext = __fdividef(num, l + d0.w) - (q.y * sc.x + q.z * sc.y);
-                const float f = l2 > 1e-30f ? q.x * ext * inv : 0.0f;
+                float f = l2 > 1e-30f ? q.x * ext * inv : 0.0f;
+                if (c.damped) {     // spring dashpot of the paper's preset
+                    const float4 va = L.vel[ia], vb = L.vel[ib];
+                    const float rv = ((vb.x - va.x) * dx + (vb.y - va.y) * dy + (vb.z - va.z) * dz) * inv;
+                    f += c.spring_c * sqrtf(q.x) * rv * inv;
+                }
                 const float gx = f * dx, gy = f * dy, gz = f * dz;
                 atomicAdd(&L.fx[ia], gx); atomicAdd(&L.fy[ia], gy); atomicAdd(&L.fz[ia], gz);
                 atomicAdd(&L.fx[ib], -gx); atomicAdd(&L.fy[ib], -gy); atomicAdd(&L.fz[ib], -gz);
@@ -108,6 +114,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
                 if (c.ground_on && z < 0.f) {
                     const float fn = c.k_ground * (-z);
                     fz += fn;
+                    fz -= c.ground_c * v.z;
                     const float fh = sqrtf(fx * fx + fy * fy);
                     if (fh <= c.mu_s * fn) {
                         fx = 0.f; fy = 0.f; v.x = 0.f; v.y = 0.f;

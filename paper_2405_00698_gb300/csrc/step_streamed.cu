@@ -7,8 +7,8 @@
 //   endpoint's parameters, read from the same coalesced planes at corner c - offset(d)), each
 //   with the shared arithmetic of physics.cuh and in the same order as the lattice kernel, so a
 //   robot stepped here follows the resident path's trajectory bit for bit;
-//   positions are double-buffered (read u_in, write u_out), so one launch needs no grid-wide
-//   barrier.
+//   positions and velocities are double-buffered (read *_in, write *_out), so one launch needs
+//   no grid-wide barrier.
 // Per spring update it moves the spring's parameters twice (once per endpoint, 24 B) and the
 // endpoint states through L2; per corner 16 B in + 32 B out (u, v) + 16 B v in + 4 B flags.
 #include "common.cuh"
@@ -32,7 +32,8 @@ k_step_streamed(StreamArgs a, int n)
     if (!(fl >> 31)) return;                    // no mass here: nothing moves
     const float4* __restrict__ uin = a.u_in + mo;
     float4 u = uin[cidx];
-    float4 v = a.v[mo + cidx];
+    const float4* __restrict__ vin = a.v_in + mo;
+    float4 v = vin[cidx];
     const float* __restrict__ prm = a.prm + 39 * mo;
     const float2 sc = a.sc[n];
     const StepConst c = a.c;
@@ -41,9 +42,13 @@ k_step_streamed(StreamArgs a, int n)
         constexpr int d = decltype(t)::value;
         if (!((fl >> d) & 1u)) return;
         const float4 ub = uin[cidx + lattice_offset<d>(X, XY)];
-        const SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z),
-                                                c.edge, lattice_rest<d>(c), prm[d * C + cidx],
-                                                prm[(13 + d) * C + cidx], prm[(26 + d) * C + cidx], sc.x, sc.y);
+        SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z),
+                                          c.edge, lattice_rest<d>(c), prm[d * C + cidx],
+                                          prm[(13 + d) * C + cidx], prm[(26 + d) * C + cidx], sc.x, sc.y);
+        if (c.damped) {
+            const float4 vb = vin[cidx + lattice_offset<d>(X, XY)];
+            spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), prm[d * C + cidx], c);
+        }
         Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
     });
     for_each_dir([&](auto t) {                 // backward springs (c - offset(d), c)
@@ -51,14 +56,18 @@ k_step_streamed(StreamArgs a, int n)
         if (!((fl >> (16 + d)) & 1u)) return;
         const int na = cidx - lattice_offset<d>(X, XY);
         const float4 ua = uin[na];
-        const SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z),
-                                                c.edge, lattice_rest<d>(c), prm[d * C + na],
-                                                prm[(13 + d) * C + na], prm[(26 + d) * C + na], sc.x, sc.y);
+        SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z),
+                                          c.edge, lattice_rest<d>(c), prm[d * C + na],
+                                          prm[(13 + d) * C + na], prm[(26 + d) * C + na], sc.x, sc.y);
+        if (c.damped) {
+            const float4 va = vin[na];
+            spring_dashpot(e, __fsub_rn(v.x, va.x), __fsub_rn(v.y, va.y), __fsub_rn(v.z, va.z), prm[d * C + na], c);
+        }
         Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
     });
     mass_update(u, v, Fx, Fy, Fz, c);
     a.u_out[mo + cidx] = u;
-    a.v[mo + cidx] = v;
+    a.v_out[mo + cidx] = v;
 }
 
 }  // namespace

@@ -39,7 +39,8 @@ class SimParams(C.Structure):
                                            "mu_s", "mu_k", "freq", "dead_bound")] + [
         ("k_mat", C.c_double * 5), ("amp_mat", C.c_double * 5), ("phase_mat", C.c_double * 5),
         ("ground_on", C.c_int32), ("accumulate", C.c_int32), ("path", C.c_int32),
-        ("threads", C.c_int32), ("mlp_kernel", C.c_int32), ("pad_", C.c_int32)]
+        ("threads", C.c_int32), ("mlp_kernel", C.c_int32), ("pad_", C.c_int32),
+        ("spring_zeta", C.c_double), ("ground_zeta", C.c_double)]
 
     @classmethod
     def of(cls, phys, accumulate: int = ACC_AUTO, path: int = PATH_AUTO, threads: int = 0,
@@ -54,6 +55,8 @@ class SimParams(C.Structure):
         p.ground_on = 1 if phys.ground_on else 0
         p.accumulate, p.path, p.threads = int(accumulate), int(path), int(threads)
         p.mlp_kernel = int(mlp_kernel)
+        p.spring_zeta = float(getattr(phys, "spring_zeta", 0.0))
+        p.ground_zeta = float(getattr(phys, "ground_zeta", 0.0))
         return p
 
 
@@ -63,7 +66,7 @@ class VoxelParams(C.Structure):
 
 class EvoParams(C.Structure):
     _fields_ = [("elites", C.c_int32), ("mut_threshold", C.c_uint32), ("sigma", C.c_float),
-                ("pad_", C.c_int32), ("seed", C.c_uint64)]
+                ("keep_threshold", C.c_uint32), ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -275,7 +278,8 @@ class Simulator:
         """All tensors on the device: fitness f64 [P], genomes f32 [P, G] (in and out may be the
         same tensor), parents i32 [P, 2] or None, mask u8 [P, G] or None."""
         P, G = genomes_in.shape
-        e = EvoParams(int(evo.elites(P)), int(evo.mut_threshold()), float(evo.sigma), 0, int(evo.seed))
+        e = EvoParams(int(evo.elites(P)), int(evo.mut_threshold()), float(evo.sigma),
+                      int(evo.keep_threshold()), int(evo.seed))
         self._sync_inputs(MEM_DEVICE)
         _check(lib().evo_generation(self._h, _ptr(fitness)[0], _ptr(genomes_in)[0],
                                     _ptr(genomes_out)[0], int(P), int(G), C.byref(e),

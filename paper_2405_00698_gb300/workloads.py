@@ -42,9 +42,17 @@ class Physics:
     amp_mat: Tuple[float, ...] = (0.0, 0.2, 0.2, 0.0, 0.0)
     phase_mat: Tuple[float, ...] = (0.0, 0.0, math.pi, 0.0, 0.0)
     ground_on: bool = True
+    spring_zeta: float = 0.0    # spring dashpot damping ratio
+    ground_zeta: float = 0.0    # ground damping ratio
 
 
 CONFIG = Physics()
+
+# The paper's own constants (Table II): time step 1e-5 s, muscle 2e3, soft tissue 1e3, bone 1e4
+# N/m, spring and ground damping ratios 0.1, muscle amplitude 0.25 with phase pi for the
+# contracting muscle, ground 1e5 N/m, static / kinetic friction 0.6 / 1.0; no velocity damping.
+PAPER = Physics(dt=1e-5, damping=1.0, mu_s=0.6, mu_k=1.0, k_mat=(0.0, 2e3, 2e3, 1e3, 1e4),
+                amp_mat=(0.0, 0.25, 0.25, 0.0, 0.0), spring_zeta=0.1, ground_zeta=0.1)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -55,6 +63,7 @@ class Evolution:
     mut_rate: float = 0.1
     sigma: float = 0.05
     seed: int = 12345
+    cross_rate: float = 1.0
 
     def elites(self, P: int) -> int:
         return max(1, min(P, math.ceil(self.elite_frac * P - 1e-9)))
@@ -62,6 +71,15 @@ class Evolution:
     def mut_threshold(self) -> int:
         """Mutation threshold on a 32-bit uniform draw: floor(rate * 2^32), clamped."""
         return int(min(max(self.mut_rate, 0.0) * 4294967296.0, 4294967295.0))
+
+    def keep_threshold(self) -> int:
+        """A child skips crossover when its 32-bit draw is below floor((1 - rate) * 2^32)."""
+        return int(min(max(1.0 - self.cross_rate, 0.0) * 4294967296.0, 4294967295.0))
+
+
+# Table I: 100 generations of 30 robots on a 5x5x5 grid; mutation rate 0.1 and scale 0.1,
+# crossover rate 0.4, elite fraction 0.3.
+PAPER_EVOLUTION = Evolution(elite_frac=0.3, mut_rate=0.1, sigma=0.1, cross_rate=0.4)
 
 
 @dataclasses.dataclass

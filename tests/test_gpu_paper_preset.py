@@ -1,0 +1,77 @@
+"""The paper's own constants (Table I / Table II): time step 1e-5 s, muscle / soft / bone
+stiffness 2e3 / 1e3 / 1e4 N/m, spring and ground damping ratios 0.1, amplitude 0.25, friction
+0.6 / 1.0; 30 robots on a 5x5x5 grid; crossover rate 0.4, elite fraction 0.3, mutation 0.1 / 0.1.
+Every stepping path against the oracle, and the evolution step with its crossover rate."""
+import numpy as np
+import pytest
+
+from paper_2405_00698_gb300 import workloads as W
+from tests.parity import check_population
+
+pytestmark = pytest.mark.gpu
+PHYS = W.PAPER
+
+
+@pytest.fixture(scope="module")
+def vs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00698_gb300 import build, voxsim
+    build.build()
+    return voxsim
+
+
+@pytest.mark.parametrize("kw", [{}, {"accumulate": 1}, {"path": 2}, {"path": 3}],
+                         ids=["lattice", "atomic", "streamed", "plain"])
+def test_paper_preset_population(vs, orc, kw):
+    pop = W.population_uniform(30, (5, 5, 5), seed=97)
+    sim = vs.Simulator(PHYS, **kw)
+    sim.set_population_from(pop)
+    sim.step(2000)
+    x, v, off = sim.state()
+    f = sim.fitness()
+    sim.close()
+    ref = orc.run_population(pop, PHYS, 2000, want_x=True)
+    check_population(orc, pop, PHYS, 2000, f, x, off, ref)
+
+
+def test_streamed_equals_lattice_with_dashpots(vs):
+    pop = W.population_uniform(6, (5, 5, 5), seed=98)
+    out = []
+    for kw in ({}, {"path": 2}):
+        sim = vs.Simulator(PHYS, **kw)
+        sim.set_population_from(pop)
+        sim.step(333)
+        out.append(sim.state()[:2])
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_paper_evolution_crossover_rate(vs, orc):
+    import torch
+    rng = np.random.default_rng(99)
+    P, G = 30, 5 * 5 * 5 * 5
+    evo = W.PAPER_EVOLUTION
+    f = rng.standard_normal(P)
+    g = rng.standard_normal((P, G)).astype(np.float32)
+    sim = vs.Simulator(PHYS)
+    out = torch.empty((P, G), device="cuda")
+    par = torch.empty((P, 2), dtype=torch.int32, device="cuda")
+    mask = torch.empty((P, G), dtype=torch.uint8, device="cuda")
+    sim.evo_generation(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), out, evo, 7, par, mask)
+    torch.cuda.synchronize()
+    ref = orc.evo_generation(f, g, evo.elites(P), evo.seed, 7, evo.mut_threshold(), evo.sigma, evo.keep_threshold())
+    assert np.array_equal(par.cpu().numpy(), ref["parents"]) and np.array_equal(mask.cpu().numpy(), ref["mask"])
+    mut = ref["mutate"] == 1
+    o = out.cpu().numpy()
+    assert np.array_equal(o[~mut], ref["genomes"][~mut].astype(np.float32))
+    assert np.abs(o[mut] - ref["genomes"][mut]).max(initial=0.0) < 4e-6
+    sim.close()
+
+
+def test_adjoint_refuses_damped_physics(vs):
+    sim = vs.Simulator(PHYS)
+    with pytest.raises(vs.VoxsimError):
+        sim.set_checkpointing(100)
+    sim.close()

@@ -497,3 +497,57 @@ def test_diversity_matches_pdist(orc):
     assert abs(orc.morphology_diversity(m) - np.mean(pdist(m, metric="hamming"))) < 1e-12
     same = np.tile(m[:1], (5, 1))
     assert orc.morphology_diversity(same) == 0.0 and orc.genome_diversity(np.tile(g[:1], (4, 1))) == 0.0
+
+
+# ------------------------------------------------------------------------------------------
+# The paper's preset: spring and ground dashpots, crossover rate (Table I / Table II)
+# ------------------------------------------------------------------------------------------
+
+def test_damped_breathing_cube_linear_recurrence(orc):
+    """With a spring dashpot of ratio zeta, the uniform scaling of a one-voxel cube stays exact:
+    every spring carries k (lambda - 1)(q0 - p0) + c_s lambda' (q0 - p0), so the corner obeys
+    lambda'' = -(8k/m)(lambda - 1) - (8 c_s / m) lambda', c_s = 2 zeta sqrt(k m / 2).  Semi-implicit
+    Euler is the linear map [y, v] -> A [y, v] with A = [[1 - h w2, h (1 - h g)], [-h w2, 1 - h g]]
+    (w2 = 8k/m, g = 8 c_s / m); numpy's matrix power gives y_n."""
+    phys = dataclasses.replace(FREE, spring_zeta=0.3)
+    r = orc.Robot(full_grid(1, 1, 1, 3), (1, 1, 1), phys)
+    x0, _ = r.state()
+    c = x0.mean(axis=0)
+    eps = 0.01
+    r.set_state(c + (1 + eps) * (x0 - c), np.zeros_like(x0), 0)
+    k, m, h = phys.k_mat[3], phys.mass, phys.dt
+    w2, g = 8 * k / m, 8 * 2 * 0.3 * math.sqrt(k * m / 2) / m
+    A = np.array([[1 - h * h * w2, h * (1 - h * g)], [-h * w2, 1 - h * g]])
+    r.simulate(600)
+    x, v = r.state()
+    y, vy = np.linalg.matrix_power(A, 600) @ np.array([eps, 0.0])
+    assert np.allclose(x, c + (1 + y) * (x0 - c), rtol=0, atol=1e-13)
+    assert abs(y) < eps * 0.5            # damped
+
+
+def test_ground_damping_keeps_the_resting_load(orc):
+    phys = dataclasses.replace(PHYS, ground_zeta=0.1, spring_zeta=0.1)
+    r = orc.Robot(full_grid(1, 1, 1, 4), (1, 1, 1), phys)
+    r.simulate(20000)
+    x, v = r.state()
+    bottom = x[:, 2] < phys.edge / 2
+    load = (phys.k_ground * -x[bottom, 2]).sum()
+    assert abs(load - 8 * phys.mass * phys.gravity) / (8 * phys.mass * phys.gravity) < 1e-3
+    assert np.abs(v).max() < 1e-5
+
+
+def test_crossover_rate(orc):
+    rng = np.random.default_rng(19)
+    P, G = 400, 64
+    f = rng.standard_normal(P)
+    g = rng.standard_normal((P, G)).astype(np.float32)
+    evo = W.Evolution(cross_rate=0.4, mut_rate=0.0)
+    E = evo.elites(P)
+    out = orc.evo_generation(f, g, E, 5, 0, evo.mut_threshold(), evo.sigma, evo.keep_threshold())
+    copied = np.all(out["mask"][E:] == 1, axis=1)
+    n = P - E
+    assert abs(copied.mean() - 0.6) < 5 * math.sqrt(0.24 / n)
+    rows = np.flatnonzero(copied) + E
+    assert np.array_equal(out["genomes"][rows].astype(np.float32), g[out["parents"][rows, 0]])
+    none = orc.evo_generation(f, g, E, 5, 0, 0, 0.1, W.Evolution(cross_rate=0.0).keep_threshold())
+    assert np.all(none["mask"][E:] == 1)
