@@ -330,7 +330,7 @@ def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_step
                         f"{N} steps", "unit": "spring-updates/s", "batched": batched,
             "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
             "autotune": {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
-                         "kind (0 lattice, 1 atomic, 2 streamed)": kinds.tolist(),
+                         "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted)": kinds.tolist(),
                          "atomic_threads": threads.tolist(), "seconds": tune_s},
             "plain": res["plain"], "batched_on_plain_sample": res["batched_same_sample"],
             "plain_sample": f"{plain_robots} robots stratified by spring count, {plain_steps} steps",

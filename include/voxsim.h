@@ -81,6 +81,16 @@ enum {
     SIM_MLP_SIMT = 1    /* CUDA-core kernel with the same bfloat16 rounding points */
 };
 
+/* Variant of the lattice-gather kernel (robots of at most 768 corners on the resident path).
+ * Both give identical bits; they differ in how threads share the work. */
+enum {
+    SIM_LATTICE_AUTO = 0,   /* library choice per size class (measured default, autotuned) */
+    SIM_LATTICE_CORNER = 1, /* a thread per corner evaluates its 13 forward lattice directions */
+    SIM_LATTICE_COMPACT = 2 /* along each direction the existing springs are packed onto the
+                               first threads, so warps skip absent springs; each mass then sums
+                               its springs' forces from shared memory */
+};
+
 /* Physics constants (Table II; the workload configurations override some of them) and
  * execution choices. */
 typedef struct {
@@ -102,7 +112,7 @@ typedef struct {
     int32_t path;       /* SIM_PATH_* */
     int32_t threads;    /* threads per robot on the resident path; 0 = autotuned */
     int32_t mlp_kernel; /* SIM_MLP_TENSOR (tcgen05, default) or SIM_MLP_SIMT (CUDA cores) */
-    int32_t pad_;
+    int32_t lattice;    /* SIM_LATTICE_* */
     double spring_zeta; /* spring dashpot damping ratio (Table II: 0.1; 0 in the configurations):
                            c_s ((v_b - v_a) . u) u with c_s = 2 zeta sqrt(k_s mass / 2) */
     double ground_zeta; /* ground damping ratio (Table II: 0.1): -2 zeta sqrt(k_ground mass) v_z
@@ -241,13 +251,14 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
 /* Per-size autotuner of the stepping kernels (project-written; the paper has no counterpart).
  * Robots are grouped by grid-corner count into 10 classes (up to 64, 128, 192, 256, 384, 768,
  * 1536, 2560, 5120 corners, and more).  For every class present in the population, each
- * admissible kernel (the lattice-gather kernel, the atomic resident kernel at three block sizes,
- * the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
+ * admissible kernel (the lattice-gather kernel in its two variants, the atomic resident kernel
+ * at three block sizes, the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
  * the current state (CUDA events), and the fastest is kept for that class.  The state is
  * restored afterwards; the choices persist for later populations of this context.  Modes that
  * require bit-reproducibility (SIM_ACC_GATHER, checkpointing) only consider deterministic
  * kernels.  kind_out / threads_out: int32 [10] host arrays (either may be NULL) receiving per
- * class 0 = lattice, 1 = atomic resident, 2 = streamed, and the atomic kernel's block size.
+ * class 0 = lattice (per corner), 1 = atomic resident, 2 = streamed, 3 = lattice
+ * (direction-compacted), and the atomic kernel's block size.
  * Synchronises the stream.  Errors: SIM_ESTATE without a population, SIM_EINVAL. */
 sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out);
 

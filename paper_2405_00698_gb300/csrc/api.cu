@@ -114,7 +114,7 @@ int64_t full_springs(int nx, int ny, int nz)
 // Size classes by grid-corner count: the six lattice slot sizes, then larger bands.
 constexpr int kNumClasses = 10;
 constexpr int kClassCorners[kNumClasses] = {64, 128, 192, 256, 384, 768, 1536, 2560, 5120, 1 << 30};
-enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2 };
+enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2, kKindLatticeCompact = 3 };
 
 static int class_of(int corners)
 {
@@ -140,9 +140,13 @@ struct voxsim_ctx {
     int64_t step = 0;
     // lattice work items (robots up to lattice_max_threads() corners), robots on the atomic
     // resident kernel (larger, state still fits one SM) and streamed robots (the rest)
-    int n_items = 0, n_big = 0, max_big_corner = 0;
+    // (lattice items: the per-corner variant's first, n_items_corner of them, then the
+    // direction-compacted variant's)
+    int n_items = 0, n_items_corner = 0, n_big = 0, max_big_corner = 0;
+    bool have_pack = false;   // the packed spring list exists for the current population
     int64_t max_big_spring_cap = 0;
-    // per size class (by corner count): kind (0 lattice, 1 atomic, 2 streamed) and threads per
+    // per size class (by corner count): kind (0 lattice per corner, 1 atomic, 2 streamed,
+    // 3 lattice direction-compacted) and threads per
     // robot of the atomic kernel (0 = from the robot size); set by sim_autotune
     int class_kind[kNumClasses];
     int class_threads[kNumClasses];
@@ -291,6 +295,8 @@ sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, vo
     *out = nullptr;
     if (!(p->dt > 0) || !(p->mass > 0) || !(p->edge > 0))
         return fail(SIM_EINVAL, "dt, mass and edge must be positive");
+    if (p->lattice < SIM_LATTICE_AUTO || p->lattice > SIM_LATTICE_COMPACT)
+        return fail(SIM_EINVAL, "unknown lattice variant %d", p->lattice);
     int ndev = 0;
     VX_CK(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(SIM_EINVAL, "device %d out of range", device);
@@ -390,6 +396,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     VX_CK(ctx->d_corner_mass.ensure(Mc)); VX_CK(ctx->d_mass_corner.ensure(Mc));
     VX_CK(ctx->d_sab.ensure(Sc)); VX_CK(ctx->d_sp.ensure(Sc));
     if (packed) VX_CK(ctx->d_spack.ensure(Sc));
+    ctx->have_pack = packed;
     VX_CK(ctx->d_x0.ensure(Mc)); VX_CK(ctx->d_x.ensure(Mc)); VX_CK(ctx->d_v.ensure(Mc));
     VX_CK(ctx->d_cflags.ensure(Mc)); VX_CK(ctx->d_prm.ensure(39 * (size_t)Mc));
     VX_CK(ctx->d_x0c.ensure(P)); VX_CK(ctx->d_keys.ensure(P)); VX_CK(ctx->d_fit.ensure(P));
@@ -484,15 +491,24 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
 
 // Default kind of a size class: the lattice kernel up to its block size, then the atomic
 // resident kernel while the robot's state fits one SM, then the streamed path.
+static bool is_lattice(int kind) { return kind == kKindLattice || kind == kKindLatticeCompact; }
+
+// The lattice variant a size class takes before any tuning: the requested one, else the
+// direction-compacted kernel (measured faster on partly filled grids).
+static int lattice_default(const voxsim_ctx* ctx)
+{
+    return ctx->p.lattice == SIM_LATTICE_CORNER ? kKindLattice : kKindLatticeCompact;
+}
+
 static void default_choices(voxsim_ctx* ctx)
 {
     const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
     for (int k = 0; k < kNumClasses; ++k) {
         const int C = std::min(kClassCorners[k], kResidentMaxCorner);
         const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
-        int kind = k < 6 ? kKindLattice : (fits ? kKindAtomic : kKindStreamed);
+        int kind = k < 6 ? lattice_default(ctx) : (fits ? kKindAtomic : kKindStreamed);
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindStreamed;
-        if (kind == kKindLattice && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
+        if (is_lattice(kind) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
         ctx->class_kind[k] = kind;
         ctx->class_threads[k] = 0;
     }
@@ -514,13 +530,13 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     ctx->max_big_spring_cap = 0;
     ctx->atomic_groups.clear();
     if (ctx->p.path == SIM_PATH_PLAIN) {       // every robot on the baseline kernels
-        ctx->n_items = ctx->n_big = ctx->n_stream = 0;
+        ctx->n_items = ctx->n_items_corner = ctx->n_big = ctx->n_stream = 0;
         VX_CK(ctx->d_plain_f.ensure(3 * (size_t)ctx->M_cap));
         VX_CK(cudaMemsetAsync(ctx->d_plain_f.p, 0, sizeof(float) * 3 * (size_t)ctx->M_cap, ctx->stream));
         return SIM_OK;
     }
     const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
-    std::vector<std::vector<std::pair<int, int>>> lattice(6);
+    std::vector<std::vector<std::pair<int, int>>> lattice(6), lattice_sp(6);
     std::vector<std::pair<int, std::pair<int, int>>> atomic;   // (threads, (-corners, robot))
     std::vector<int> streamed;
     ctx->max_stream_corner = 0;
@@ -533,20 +549,23 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         const bool fits_sm = C <= kResidentMaxCorner && resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget;
         int kind = ctx->class_kind[k];
         if (ctx->p.path == SIM_PATH_STREAMED) kind = kKindStreamed;
-        else if (ctx->p.accumulate == SIM_ACC_ATOMIC && kind == kKindLattice) kind = kKindAtomic;
-        else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? kKindLattice : kKindStreamed;
-        if (kind == kKindLattice && C > block) kind = fits_sm ? kKindAtomic : kKindStreamed;
+        else if (ctx->p.accumulate == SIM_ACC_ATOMIC && is_lattice(kind)) kind = kKindAtomic;
+        else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? lattice_default(ctx) : kKindStreamed;
+        if (is_lattice(kind) && C > block) kind = fits_sm ? kKindAtomic : kKindStreamed;
         if (kind == kKindAtomic && !fits_sm) kind = kKindStreamed;
         if (kind == kKindStreamed && ctx->p.path == SIM_PATH_RESIDENT) {
             if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
-            kind = C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC ? kKindLattice : kKindAtomic;
+            kind = C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC ? lattice_default(ctx) : kKindAtomic;
         }
+        // a requested variant wins over the class choice; the direction-compacted one needs the list
+        if (kind == kKindLattice && ctx->p.lattice == SIM_LATTICE_COMPACT) kind = kKindLatticeCompact;
+        if (kind == kKindLatticeCompact && (ctx->p.lattice == SIM_LATTICE_CORNER || !ctx->have_pack)) kind = kKindLattice;
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER)
             return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners on the resident path", block);
-        if (kind == kKindLattice) {
+        if (is_lattice(kind)) {
             int slot = 0;
             while (kSlot[slot] < C) ++slot;
-            lattice[slot].push_back({-C, r});
+            (kind == kKindLattice ? lattice : lattice_sp)[slot].push_back({-C, r});
         } else if (kind == kKindAtomic) {
             int threads = ctx->class_threads[k] > 0 ? ctx->class_threads[k] : ctx->p.threads;
             if (threads <= 0) {
@@ -562,14 +581,17 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     }
     std::vector<int4> items;
     std::vector<int> robots;
-    for (int k = 5; k >= 0; --k) {
-        auto& v = lattice[k];
-        std::sort(v.begin(), v.end());
-        const int per = block / kSlot[k];
-        for (size_t i = 0; i < v.size(); i += per) {
-            const int n = (int)std::min<size_t>(per, v.size() - i);
-            items.push_back(make_int4((int)robots.size(), n, kSlot[k], 0));
-            for (int j = 0; j < n; ++j) robots.push_back(v[i + j].second);
+    for (int variant = 0; variant < 2; ++variant) {
+        if (variant == 1) ctx->n_items_corner = (int)items.size();
+        for (int k = 5; k >= 0; --k) {
+            auto& v = variant == 0 ? lattice[k] : lattice_sp[k];
+            std::sort(v.begin(), v.end());
+            const int per = block / kSlot[k];
+            for (size_t i = 0; i < v.size(); i += per) {
+                const int n = (int)std::min<size_t>(per, v.size() - i);
+                items.push_back(make_int4((int)robots.size(), n, kSlot[k], variant));
+                for (int j = 0; j < n; ++j) robots.push_back(v[i + j].second);
+            }
         }
     }
     std::sort(atomic.begin(), atomic.end());
@@ -660,9 +682,20 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     }
     const int threads = lattice_max_threads();
     const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
-    const int grid = std::min(ctx->n_items, ctx->num_sms);
-    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), ctx->stream));
-    VX_LAUNCH(ctx, launch_step_lattice(a, grid, threads, smem, ctx->stream));
+    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, 2 * sizeof(int), ctx->stream));
+    // per-corner variant: items [0, n_items_corner); direction-compacted variant: the rest
+    const int n_corner = ctx->n_items_corner, n_spring = ctx->n_items - ctx->n_items_corner;
+    if (n_corner > 0) {
+        a.n_items = n_corner;
+        VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_corner, ctx->num_sms), threads, smem, ctx->stream));
+    }
+    if (n_spring > 0) {
+        a.items = ctx->d_items.p + n_corner;
+        a.n_items = n_spring;
+        a.queue = ctx->d_queue.p + 1;
+        a.spack = ctx->d_spack.p;
+        VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_spring, ctx->num_sms), threads, smem, ctx->stream));
+    }
     return SIM_OK;
 }
 
@@ -990,7 +1023,10 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
         const int Cmax = -members[k].front().first;
         const bool fits = Cmax <= kResidentMaxCorner && resident_smem_bytes(Cmax, 0, SIM_ACC_ATOMIC) <= budget;
         std::vector<std::pair<int, int>> cands;
-        if (k < 6 && ctx->p.accumulate != SIM_ACC_ATOMIC) cands.push_back({kKindLattice, 0});
+        if (k < 6 && ctx->p.accumulate != SIM_ACC_ATOMIC) {
+            if (ctx->p.lattice != SIM_LATTICE_COMPACT) cands.push_back({kKindLattice, 0});
+            if (ctx->p.lattice != SIM_LATTICE_CORNER && ctx->have_pack) cands.push_back({kKindLatticeCompact, 0});
+        }
         if (fits && ctx->p.accumulate != SIM_ACC_GATHER) {
             const int t3[3] = {k < 6 ? 128 : 256, k < 6 ? 256 : 512, k < 6 ? 512 : 1024};
             for (int t : t3) cands.push_back({kKindAtomic, t});

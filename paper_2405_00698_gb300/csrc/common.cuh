@@ -130,6 +130,9 @@ struct LatticeArgs {
     const int* corner_order; // per robot at moff: the mass corners (ascending), one per thread
     const uint32_t* cflags;  // per corner: forward mask bits 0..12, backward 16..28, mass bit 31
     const float* prm;        // per robot at 39 * moff: [3][13][C] (k, alpha L0, beta L0)
+    // spring-parallel variant (NULL: per-corner variant): the direction-major packed springs
+    // per robot at soff, (k, alpha L0, beta L0, a | b << 14 | direction << 28)
+    const float4* spack;
     float4* u;               // per corner displacement (rest height in .w)
     float4* v;               // per corner velocity
     const float2* sc;        // sin / cos of w t per step of this call

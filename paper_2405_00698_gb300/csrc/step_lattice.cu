@@ -136,6 +136,156 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
     }
 }
 
+
+// ----------------------------------------------------------------------------------------------
+// Direction-compacted variant of the same step.  In the per-corner kernel above a warp spends an
+// evaluation on direction d whenever any of its 32 corners has a spring along d, so partly
+// filled grids pay for absent springs.  Here thread t's slot d holds the t-th existing spring of
+// direction d (the direction-major packed list), so along every direction the busy threads are
+// 0 .. n_d - 1 and whole warps past n_d skip it: the cost of phase A follows the spring count.
+// Per step:
+//   phase A: slot d of every thread below n_d evaluates its spring (a, a + off(d)) from the shared
+//            positions and writes the force on a to plane d at index a;
+//   phase B: each mass thread adds its forward planes (index c) and subtracts its backward planes
+//            (index c - off(d)) in direction order, then the mass update.
+// Same arithmetic (compile-time directions), same per-mass summation order (forward by direction,
+// then backward by direction) and same initial zero as the per-corner kernel: the two give
+// identical bits.  It trades instructions for shared-memory traffic (phase A also reads u_a and
+// phase B also reads the forward planes).
+// ----------------------------------------------------------------------------------------------
+template <bool DAMPED>
+__global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_compact(LatticeArgs a)
+{
+    extern __shared__ __align__(16) float4 sm4[];
+    __shared__ int sh_item[4];
+    __shared__ int sh_nd[kMaxLatticeThreads / 64][16];   // per group: springs per direction
+    const int tid = threadIdx.x;
+    const StepConst c = a.c;
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(a.queue, 1);
+            if (it < a.n_items) {
+                const int4 item = a.items[it];
+                sh_item[0] = item.x; sh_item[1] = item.y; sh_item[2] = item.z; sh_item[3] = 1;
+            } else {
+                sh_item[3] = 0;
+            }
+        }
+        __syncthreads();
+        if (!sh_item[3]) break;
+        const int first = sh_item[0], count = sh_item[1], gthreads = sh_item[2];
+        const int group = tid / gthreads, lt = tid % gthreads;
+        __syncthreads();
+        if (group < count) {
+            const int r = a.item_robots[first + group];
+            const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1];
+            const int X = nx + 1, XY = (nx + 1) * (ny + 1);
+            const int64_t mo = a.pv.moff[r];
+            const int bar = 1 + group;
+            const int S = gthreads;
+            float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
+            float4* sv = su + S;
+            float4* fb = sv + S;
+            int* nd = sh_nd[group];
+            const int M = a.pv.n_mass[r];
+            const bool in = lt < M;
+            const int cidx = in ? a.corner_order[mo + lt] : 0;
+            const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
+            // springs per direction = corners with that forward bit
+            if (lt < 13) nd[lt] = 0;
+            group_sync(bar, gthreads);
+            for_each_dir([&](auto t) {
+                constexpr int d = decltype(t)::value;
+                const unsigned w = __ballot_sync(0xffffffffu, (fl >> d) & 1u);
+                if ((lt & 31) == 0 && w) atomicAdd(&nd[d], __popc(w));
+            });
+            group_sync(bar, gthreads);
+            // slot d: the lt-th spring of direction d, at list offset (springs of directions < d) + lt
+            const float4* __restrict__ list = a.spack + a.pv.soff[r];
+            float pk[13], pa[13], pb[13];
+            uint32_t cpack[5];                                     // the slots' corners a, 10 bits each
+            uint32_t has = 0u;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) cpack[i] = 0u;
+            int base = 0;
+            for_each_dir([&](auto t) {
+                constexpr int d = decltype(t)::value;
+                const int n_d = nd[d];
+                const bool h = lt < n_d;
+                const float4 p = h ? list[base + lt] : make_float4(0.f, 0.f, 0.f, 0.f);
+                pk[d] = p.x; pa[d] = p.y; pb[d] = p.z;
+                cpack[d / 3] |= (__float_as_uint(p.w) & 0x3ffu) << (10 * (d % 3));
+                has |= (h ? 1u : 0u) << d;
+                base += n_d;
+            });
+            float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) {
+                su[cidx] = u;
+                if (DAMPED) sv[cidx] = v;
+            }
+            group_sync(bar, gthreads);
+            for (int n = 0; n < a.nsteps; ++n) {
+                if (a.ckpt_u && in && n % a.ckpt_every == 0) {
+                    const int64_t o = (int64_t)(n / a.ckpt_every) * a.ckpt_stride + mo + cidx;
+                    a.ckpt_u[o] = u;
+                    a.ckpt_v[o] = v;
+                }
+                const float2 sc = a.sc[n];
+                // phase A: this thread's slot of every direction.  The corner words are re-read
+                // as opaque values every step so the compiler decodes them where used instead of
+                // keeping 13 decoded corners (and their neighbours) live across the loop.
+#pragma unroll
+                for (int i = 0; i < 5; ++i) asm volatile("" : "+r"(cpack[i]));
+                asm volatile("" : "+r"(has));
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((has >> d) & 1u)) return;
+                    const int ca = (int)((cpack[d / 3] >> (10 * (d % 3))) & 0x3ffu);
+                    const int cb = ca + lattice_offset<d>(X, XY);
+                    const float4 ua = su[ca];
+                    const float4 ub = su[cb];
+                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y),
+                                                      __fsub_rn(ub.z, ua.z), c.edge, lattice_rest<d>(c),
+                                                      pk[d], pa[d], pb[d], sc.x, sc.y);
+                    if constexpr (DAMPED) {
+                        const float4 va = sv[ca];
+                        const float4 vb = sv[cb];
+                        spring_dashpot(e, __fsub_rn(vb.x, va.x), __fsub_rn(vb.y, va.y), __fsub_rn(vb.z, va.z), pk[d], c);
+                    }
+                    fb[d * S + ca] = make_float4(e.gx, e.gy, e.gz, 0.f);
+                });
+                group_sync(bar, gthreads);
+                // phase B: the forces of this mass's springs in direction order, then the update
+                if (in) {
+                    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+                    for_each_dir([&](auto t) {
+                        constexpr int d = decltype(t)::value;
+                        if (!((fl >> d) & 1u)) return;
+                        const float4 g = fb[d * S + cidx];
+                        Fx = __fadd_rn(Fx, g.x); Fy = __fadd_rn(Fy, g.y); Fz = __fadd_rn(Fz, g.z);
+                    });
+                    for_each_dir([&](auto t) {
+                        constexpr int d = decltype(t)::value;
+                        if (!((fl >> (16 + d)) & 1u)) return;
+                        const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];
+                        Fx = __fsub_rn(Fx, g.x); Fy = __fsub_rn(Fy, g.y); Fz = __fsub_rn(Fz, g.z);
+                    });
+                    mass_update(u, v, Fx, Fy, Fz, c);
+                    su[cidx] = u;
+                    if (DAMPED) sv[cidx] = v;
+                }
+                group_sync(bar, gthreads);
+            }
+            if (in) {
+                a.u[mo + cidx] = u;
+                a.v[mo + cidx] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int lattice_max_threads() { return kMaxLatticeThreads; }
@@ -143,7 +293,8 @@ int lattice_max_threads() { return kMaxLatticeThreads; }
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
-    auto kernel = a.c.damped ? k_step_lattice<true> : k_step_lattice<false>;
+    auto kernel = a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
+                          : (a.c.damped ? k_step_lattice<true> : k_step_lattice<false>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<grid, threads, smem, s>>>(a);

@@ -20,6 +20,7 @@ MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS = 0, 1, 2, 3
 ACC_AUTO, ACC_ATOMIC, ACC_GATHER = 0, 1, 2
 MLP_TENSOR, MLP_SIMT = 0, 1
 PATH_AUTO, PATH_RESIDENT, PATH_STREAMED, PATH_PLAIN = 0, 1, 2, 3
+LATTICE_AUTO, LATTICE_CORNER, LATTICE_COMPACT = 0, 1, 2
 GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
@@ -39,12 +40,12 @@ class SimParams(C.Structure):
                                            "mu_s", "mu_k", "freq", "dead_bound")] + [
         ("k_mat", C.c_double * 5), ("amp_mat", C.c_double * 5), ("phase_mat", C.c_double * 5),
         ("ground_on", C.c_int32), ("accumulate", C.c_int32), ("path", C.c_int32),
-        ("threads", C.c_int32), ("mlp_kernel", C.c_int32), ("pad_", C.c_int32),
+        ("threads", C.c_int32), ("mlp_kernel", C.c_int32), ("lattice", C.c_int32),
         ("spring_zeta", C.c_double), ("ground_zeta", C.c_double)]
 
     @classmethod
     def of(cls, phys, accumulate: int = ACC_AUTO, path: int = PATH_AUTO, threads: int = 0,
-           mlp_kernel: int = 0):
+           mlp_kernel: int = 0, lattice: int = 0):
         p = cls()
         for n in ("dt", "gravity", "mass", "edge", "damping", "k_ground", "mu_s", "mu_k", "freq",
                   "dead_bound"):
@@ -55,6 +56,7 @@ class SimParams(C.Structure):
         p.ground_on = 1 if phys.ground_on else 0
         p.accumulate, p.path, p.threads = int(accumulate), int(path), int(threads)
         p.mlp_kernel = int(mlp_kernel)
+        p.lattice = int(lattice)
         p.spring_zeta = float(getattr(phys, "spring_zeta", 0.0))
         p.ground_zeta = float(getattr(phys, "ground_zeta", 0.0))
         return p
@@ -131,11 +133,12 @@ class Simulator:
     """One library context on one GPU, enqueueing on a torch CUDA stream."""
 
     def __init__(self, phys, device: int = 0, stream=None, accumulate: int = ACC_AUTO,
-                 path: int = PATH_AUTO, threads: int = 0, mlp_kernel: int = MLP_TENSOR):
+                 path: int = PATH_AUTO, threads: int = 0, mlp_kernel: int = MLP_TENSOR,
+                 lattice: int = 0):
         import torch
         self.device = int(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.params = SimParams.of(phys, accumulate, path, threads, mlp_kernel)
+        self.params = SimParams.of(phys, accumulate, path, threads, mlp_kernel, lattice)
         h = C.c_void_p()
         _check(lib().sim_create(C.byref(self.params), self.device, C.c_void_p(self.stream.cuda_stream),
                                 C.byref(h)))
@@ -213,7 +216,8 @@ class Simulator:
 
     def autotune(self, n_steps: int = 50):
         """Time the admissible stepping kernels per size class and keep the fastest; returns
-        (kind [10], threads [10]) with kind 0 lattice, 1 atomic resident, 2 streamed."""
+        (kind [10], threads [10]) with kind 0 lattice per corner, 1 atomic resident, 2 streamed,
+        3 lattice direction-compacted."""
         kind = np.zeros(10, np.int32); threads = np.zeros(10, np.int32)
         _check(lib().sim_autotune(self._h, int(n_steps), kind.ctypes.data, threads.ctypes.data))
         return kind, threads

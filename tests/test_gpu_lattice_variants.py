@@ -1,0 +1,112 @@
+"""The two variants of the lattice-gather kernel (per-corner threads; springs compacted per
+direction onto the first threads) evaluate the same springs with the same arithmetic and sum
+every mass's forces in the same order, so they must agree bit for bit: on uniform, uneven and
+MLP-decoded populations, with the spring and ground dashpots of the paper's preset, and as the
+forward run the checkpointed adjoint replays.  The compacted variant is also held against the
+FP64 oracle directly."""
+import numpy as np
+import pytest
+
+from paper_2405_00698_gb300 import workloads as W
+from tests.parity import check_population
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00698_gb300 import build, voxsim
+    build.build()
+    return voxsim
+
+
+def run(vs, pop, phys, nsteps, lattice, **kw):
+    sim = vs.Simulator(phys, lattice=lattice, **kw)
+    sim.set_population_from(pop)
+    sim.step(nsteps)
+    x, v, off = sim.state()
+    f = sim.fitness()
+    sim.close()
+    return x, v, f, off
+
+
+CASES = {
+    "uniform-4cube": lambda: W.population_uniform(40, (4, 4, 4), seed=70),
+    "uneven": lambda: W.population_uneven(60, seed=71, sizes=(2, 3, 4, 6, 8)),
+    "sparse-8cube": lambda: W.population_bernoulli(20, (8, 8, 8), 0.45, seed=72),
+    "full-8cube": lambda: W.population_bernoulli(4, (8, 8, 8), 1.0, seed=73),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("phys_name", ["CONFIG", "PAPER"])
+def test_variants_agree_bitwise(vs, case, phys_name):
+    pop = CASES[case]()
+    phys = getattr(W, phys_name)
+    n = 600 if phys_name == "CONFIG" else 1500
+    a = run(vs, pop, phys, n, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
+    b = run(vs, pop, phys, n, vs.LATTICE_COMPACT, path=vs.PATH_RESIDENT)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+
+
+def test_variants_agree_on_mlp_population(vs):
+    import torch
+    G, B = W.workload_mlp(P=48, seed=74)
+    dims = np.tile(np.array([8, 8, 8], np.int32), (48, 1))
+    out = []
+    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT):
+        sim = vs.Simulator(W.CONFIG, lattice=lattice)
+        sim.set_population(dims, torch.from_numpy(G).cuda(), vs.MODE_MLP, B=torch.from_numpy(B).cuda())
+        sim.step(400)
+        out.append(sim.state()[:2])
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_compact_variant_matches_oracle(vs, orc):
+    pop = W.population_uneven(24, seed=75, sizes=(3, 4, 6, 8), occ=(0.3, 0.7))
+    x, v, f, off = run(vs, pop, W.CONFIG, 1000, vs.LATTICE_COMPACT)
+    ref = orc.run_population(pop, W.CONFIG, 1000, want_x=True)
+    check_population(orc, pop, W.CONFIG, 1000, f, x, off, ref)
+
+
+def test_adjoint_after_either_variant(vs):
+    """The adjoint replays its segments with its own kernel: its gradient is the same whichever
+    variant ran the recorded forward pass."""
+    import torch
+    rng = np.random.default_rng(76)
+    pop = W.population_uniform(8, (4, 4, 4), seed=76)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    grads = []
+    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT):
+        sim = vs.Simulator(W.CONFIG, lattice=lattice)
+        sim.set_checkpointing(50)
+        sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+        sim.step(300)
+        n = pop.mats.size
+        g = [torch.empty(n, device="cuda") for _ in range(3)]
+        sim.backward(t(np.ones(pop.P)), *g)
+        torch.cuda.synchronize()
+        grads.append([a.cpu().numpy() for a in g])
+        sim.close()
+    for a, b in zip(*grads):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_reports_the_variant(vs):
+    pop = W.population_uneven(200, seed=77, sizes=(4, 6, 8))
+    sim = vs.Simulator(W.CONFIG, accumulate=vs.ACC_GATHER)
+    sim.set_population_from(pop)
+    kinds, _ = sim.autotune(20)
+    sim.close()
+    assert set(int(k) for k in kinds[:6]) <= {0, 3}
+    sim = vs.Simulator(W.CONFIG, accumulate=vs.ACC_GATHER, lattice=vs.LATTICE_CORNER)
+    sim.set_population_from(pop)
+    kinds, _ = sim.autotune(20)
+    sim.close()
+    assert set(int(k) for k in kinds[:6]) <= {0}
