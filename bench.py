@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--robots", type=int, default=P_ROBOTS, help=argparse.SUPPRESS)
     ap.add_argument("--sim-steps", type=int, default=SIM_STEPS, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", choices=["auto", "corner", "compact"], default="auto",
+                    help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
     return ap.parse_args()
@@ -169,7 +171,8 @@ def run_ours(args):
     genomes_h, Bmat_h = W.workload_mlp(P, seed=shards.shard_seed(1, rank))
     dims = np.tile(np.asarray(GRID, np.int32), (P, 1))
     stream = torch.cuda.current_stream()
-    sim = vs.Simulator(phys, device=local, stream=stream)
+    lattice = {"auto": vs.LATTICE_AUTO, "corner": vs.LATTICE_CORNER, "compact": vs.LATTICE_COMPACT}[args.lattice]
+    sim = vs.Simulator(phys, device=local, stream=stream, lattice=lattice)
     g_a = torch.from_numpy(genomes_h).cuda()
     g_b = torch.empty_like(g_a)
     Bmat = torch.from_numpy(Bmat_h).cuda()

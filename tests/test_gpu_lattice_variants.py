@@ -76,7 +76,8 @@ def test_compact_variant_matches_oracle(vs, orc):
 
 def test_adjoint_after_either_variant(vs):
     """The adjoint replays its segments with its own kernel: its gradient is the same whichever
-    variant ran the recorded forward pass."""
+    variant ran the recorded forward pass (up to the order of the per-voxel float atomics that
+    gather the spring sensitivities)."""
     import torch
     rng = np.random.default_rng(76)
     pop = W.population_uniform(8, (4, 4, 4), seed=76)
@@ -95,7 +96,7 @@ def test_adjoint_after_either_variant(vs):
         grads.append([a.cpu().numpy() for a in g])
         sim.close()
     for a, b in zip(*grads):
-        assert np.array_equal(a, b)
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
 
 
 def test_autotune_reports_the_variant(vs):
