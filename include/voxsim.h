@@ -51,8 +51,10 @@ enum {
     SIM_MODE_LOGITS = 1,    /* float32 [voxels][5] material scores; material = argmax (lowest id
                                on ties), material weight 1 */
     SIM_MODE_MLP = 2,       /* float32 [P][20998] MLP genomes, queried at every voxel centre */
-    SIM_MODE_PARAMS = 3     /* const sim_voxel_params*: materials plus per-voxel weight,
+    SIM_MODE_PARAMS = 3,    /* const sim_voxel_params*: materials plus per-voxel weight,
                                stiffness and phase (the differentiable parametrisation) */
+    SIM_MODE_PARAM_ROWS = 4 /* const sim_param_rows*: the same parametrisation as one genome row
+                               per robot, [w | kappa | phi], for the genetic operators */
 };
 
 /* Force accumulation of the time stepping kernels. */
@@ -127,6 +129,14 @@ typedef struct {
     const float* kappa;
     const float* phi;
 } sim_voxel_params;
+
+/* SIM_MODE_PARAM_ROWS: every robot on one grid shape of V voxels; row r of `rows` (float32
+ * [P][3 V]) holds robot r's per-voxel w (entries 0 .. V-1), kappa (V .. 2V-1) and phi (2V ..
+ * 3V-1), voxel order as in sim_set_population; `mat` is uint8 [P][V]. */
+typedef struct {
+    const uint8_t* mat;
+    const float* rows;
+} sim_param_rows;
 
 /* Evolution rates (Table I; configuration values: elites 25 %, sigma 0.05, rate 0.1). */
 typedef struct {
@@ -221,6 +231,23 @@ sim_status evo_generation_static(const double* fitness, const float* genomes_in,
                                  float* genomes_out, int32_t P, int32_t G, const evo_params* e,
                                  uint64_t generation, int32_t* parents_out, uint8_t* mask_out,
                                  void* cuda_stream);
+
+/* Lamarckian gradient step of the gradient-assisted co-design variant (project extension: the
+ * paper evolves with genetic operators only; this keeps them unchanged and moves chosen genomes
+ * uphill along the adjoint's gradient before they breed).  Genomes are SIM_MODE_PARAM_ROWS rows
+ * (float32 device [P][G], G = 3 V) of the context's current population (P robots on one grid of
+ * V voxels); g_w, g_kappa, g_phi are sim_backward's outputs for that population (device, one
+ * entry per voxel).  For every robot r in rows (host int32 [n_rows], each in 0 .. P-1; NULL =
+ * every robot) and gene j with gradient d_rj (g_w, g_kappa or g_phi of voxel j mod V) and step
+ * eta_j (eta_w, eta_kappa or eta_phi, one per segment since the three scale differently):
+ *     genome_rj <- min(max(fmaf(eta_j, d_rj, genome_rj), lo_j), hi_j)
+ * lo, hi: device float32 [G] bounds, or NULL for none.  Enqueued on the context's stream.
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL (sizes, null pointers, a row out of range,
+ * a population that is not on one grid shape). */
+sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t G, const float* g_w,
+                             const float* g_kappa, const float* g_phi, const int32_t* rows,
+                             int32_t n_rows, float eta_w, float eta_kappa, float eta_phi,
+                             const float* lo, const float* hi);
 
 /* Turn state checkpointing on (every k_steps steps, k_steps >= 1) or off (0).  While on, each
  * sim_step_n call records the state at its start and every k_steps steps after, which

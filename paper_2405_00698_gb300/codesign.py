@@ -1,5 +1,5 @@
-"""The co-design loop around the library (Section II-C, Section II-D, Fig. 2) and headless
-trajectory export.
+"""The co-design loop around the library (Section II-C, Section II-D, Fig. 2), its
+gradient-assisted variant, and headless trajectory export.
 
 Every generation runs on the GPU through the C ABI: MLP decode of all genomes, simulation,
 fitness, then elite selection / crossover / mutation into the next genome matrix.  Between
@@ -80,6 +80,71 @@ def run(sim: "vs.Simulator", genomes, B, dims: Sequence[int], generations: int, 
             spring_updates=int(S.astype(np.int64).sum()) * steps, evolution=evo))
         if hook is not None:
             evo = hook(records[-3:], evo)
+        sim.evo_generation(fit, cur, other, evo, gen)
+        cur, other = other, cur
+    return records, cur
+
+
+def param_bounds(V: int, device="cuda"):
+    """Default box of a [w | kappa | phi] genome row: 0 <= w <= 1, kappa >= 0, phi free."""
+    import torch
+    inf = float("inf")
+    lo = torch.tensor([0.0] * V + [0.0] * V + [-inf] * V, dtype=torch.float32, device=device)
+    hi = torch.tensor([1.0] * V + [inf] * V + [inf] * V, dtype=torch.float32, device=device)
+    return lo, hi
+
+
+def rank_order(f: np.ndarray) -> np.ndarray:
+    """The genetic operators' ranking: fitness descending, index ascending on ties, NaN last."""
+    key = np.where(np.isnan(f), -np.inf, f)
+    return np.argsort(-key, kind="stable")
+
+
+def run_lamarckian(sim: "vs.Simulator", mats, genomes, dims: Sequence[int], generations: int,
+                   steps: int, evo: W.Evolution = W.Evolution(), eta=(0.0, 0.0, 0.0),
+                   checkpoint: int = 100, bounds=None, first_generation: int = 0) -> tuple:
+    """Gradient-assisted co-design on per-voxel parameter genomes (a project extension beside the
+    paper's purely genetic loop): the morphology `mats` (CUDA uint8 [P * V]) stays fixed and each
+    genome row is [w | kappa | phi] (CUDA float32 [P, 3V], updated in place).  Every generation:
+    simulate with checkpoints, take the fitness, run the adjoint of the elites' summed fitness,
+    move the elites one gradient step uphill (evo_gradient_step, per-segment steps `eta`, box
+    `bounds` = (lo, hi) or the default of param_bounds), then breed the next generation with the
+    unchanged genetic operators from the improved elites.  Returns (records, final genomes)."""
+    import torch
+    P, G = genomes.shape
+    V = G // 3
+    d = np.tile(np.asarray(dims, np.int32), (P, 1))
+    lo, hi = bounds if bounds is not None else param_bounds(V, genomes.device)
+    fit = torch.empty(P, dtype=torch.float64, device=genomes.device)
+    dl = torch.zeros(P, dtype=torch.float64, device=genomes.device)
+    gw, gk, gp = (torch.empty(P * V, dtype=torch.float32, device=genomes.device) for _ in range(3))
+    other = torch.empty_like(genomes)
+    cur = genomes
+    sim.set_checkpointing(checkpoint)
+    records: List[GenerationRecord] = []
+    for k in range(generations):
+        gen = first_generation + k
+        sim.set_population(d, (mats, cur), vs.MODE_PARAM_ROWS)
+        sim.step(steps)
+        sim.fitness(fit)
+        f = fit.cpu().numpy()
+        alive = f[np.isfinite(f)]
+        E = evo.elites(P)
+        elite = [int(r) for r in rank_order(f)[:E] if np.isfinite(f[r])]
+        dl_h = np.zeros(P)
+        dl_h[elite] = 1.0
+        dl.copy_(torch.from_numpy(dl_h))
+        if elite:
+            sim.backward(dl, gw, gk, gp)
+            sim.evo_gradient_step(cur, gw, gk, gp, eta, rows=elite, lo=lo, hi=hi)
+        _, S = sim.counts()
+        records.append(GenerationRecord(
+            generation=gen, best=float(alive.max()) if alive.size else float("-inf"),
+            mean=float(alive.mean()) if alive.size else float("nan"),
+            median=float(np.median(alive)) if alive.size else float("nan"),
+            dead=int(P - alive.size), genome_diversity=sim.diversity(cur)[0],
+            morphology_diversity=float("nan"), spring_updates=int(S.astype(np.int64).sum()) * steps,
+            evolution=evo))
         sim.evo_generation(fit, cur, other, evo, gen)
         cur, other = other, cur
     return records, cur

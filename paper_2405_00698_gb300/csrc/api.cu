@@ -173,7 +173,7 @@ struct voxsim_ctx {
     // device buffers
     DevBuf<int> d_dims;
     DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
-    DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big;
+    DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big, d_grad_rows;
     DevBuf<int4> d_items;
     DevBuf<uint32_t> d_cflags;
     DevBuf<float> d_prm;
@@ -335,7 +335,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     if (P < 0) return fail(SIM_EINVAL, "P must be >= 0");
     if (P > 0 && !dims) return fail(SIM_EINVAL, "null dims");
     if (mem != SIM_MEM_HOST && mem != SIM_MEM_DEVICE) return fail(SIM_EINVAL, "bad mem %d", mem);
-    if (mode < SIM_MODE_MATERIALS || mode > SIM_MODE_PARAMS) return fail(SIM_EINVAL, "bad mode %d", mode);
+    if (mode < SIM_MODE_MATERIALS || mode > SIM_MODE_PARAM_ROWS) return fail(SIM_EINVAL, "bad mode %d", mode);
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     // layout
@@ -358,11 +358,11 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         max_corner = std::max(max_corner, corners);
         max_sc = std::max(max_sc, sc);
     }
-    if (mode == SIM_MODE_MLP && P > 0) {
+    if ((mode == SIM_MODE_MLP || mode == SIM_MODE_PARAM_ROWS) && P > 0) {
         for (int r = 1; r < P; ++r)
             if (d[3 * r] != d[0] || d[3 * r + 1] != d[1] || d[3 * r + 2] != d[2])
-                return fail(SIM_EINVAL, "MLP mode needs one grid shape for all robots");
-        if (!B) return fail(SIM_EINVAL, "MLP mode needs the encoding matrix B");
+                return fail(SIM_EINVAL, "this mode needs one grid shape for all robots");
+        if (mode == SIM_MODE_MLP && !B) return fail(SIM_EINVAL, "MLP mode needs the encoding matrix B");
     }
     if (P > 0 && !genomes) return fail(SIM_EINVAL, "null genomes");
     const int64_t V = voff[P], Mc = moff[P], Sc = soff[P];
@@ -372,9 +372,10 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     if (mode == SIM_MODE_MLP && !packed)
         return fail(SIM_EINVAL, "MLP decoding supports grids of at most %d corners", kResidentMaxCorner);
     // host-side validation of host materials
-    if (mem == SIM_MEM_HOST && (mode == SIM_MODE_MATERIALS || mode == SIM_MODE_PARAMS)) {
+    if (mem == SIM_MEM_HOST && (mode == SIM_MODE_MATERIALS || mode == SIM_MODE_PARAMS || mode == SIM_MODE_PARAM_ROWS)) {
         const uint8_t* m = mode == SIM_MODE_MATERIALS ? (const uint8_t*)genomes
-                                                      : ((const sim_voxel_params*)genomes)->mat;
+                           : mode == SIM_MODE_PARAMS  ? ((const sim_voxel_params*)genomes)->mat
+                                                      : ((const sim_param_rows*)genomes)->mat;
         if (V > 0 && !m) return fail(SIM_EINVAL, "null materials");
         for (int64_t i = 0; i < V; ++i)
             if (m[i] >= kNumMat) return fail(SIM_EINVAL, "material id %d at voxel %lld", (int)m[i], (long long)i);
@@ -447,6 +448,20 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
             }
             VX_LAUNCH(ctx, launch_decode_params(m, w, k, ph, V, ctx->d_mat_raw.p, ctx->d_w.p, ctx->d_kappa.p,
                                        ctx->d_phi.p, ctx->d_status.p, s));
+        } else if (mode == SIM_MODE_PARAM_ROWS) {
+            const sim_param_rows* pr = (const sim_param_rows*)genomes;
+            const uint8_t* m = pr->mat;
+            const float* rows = pr->rows;
+            if (V > 0 && (!m || !rows)) return fail(SIM_EINVAL, "null materials or rows");
+            if (mem == SIM_MEM_HOST) {
+                VX_CK(ctx->d_in_u8.ensure(V));
+                VX_CK(ctx->d_in_f32.ensure(3 * (size_t)V));
+                if (sim_status st = copy_in(m, V, mem, ctx->d_in_u8.p, s)) return st;
+                if (sim_status st = copy_in(rows, 12 * V, mem, ctx->d_in_f32.p, s)) return st;
+                m = ctx->d_in_u8.p; rows = ctx->d_in_f32.p;
+            }
+            VX_LAUNCH(ctx, launch_decode_param_rows(m, rows, V / P, V, ctx->d_mat_raw.p, ctx->d_w.p,
+                                                    ctx->d_kappa.p, ctx->d_phi.p, ctx->d_status.p, s));
         } else {
             const int Q = d[0] * d[1] * d[2];
             const float* gsrc = (const float*)genomes;
@@ -894,6 +909,45 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
     VX_LAUNCH(ctx, launch_evo_rank(fitness, P, ctx->d_order.p, s));
     VX_LAUNCH(ctx, launch_evo_children(src, genomes_out, ctx->d_order.p, P, G, e->elites, e->seed, generation,
                               e->mut_threshold, e->sigma, e->keep_threshold, parents_out, mask_out, s));
+    return SIM_OK;
+}
+
+// Lamarckian gradient step on genome rows [w | kappa | phi] of the current population.
+sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t G, const float* g_w,
+                             const float* g_kappa, const float* g_phi, const int32_t* rows,
+                             int32_t n_rows, float eta_w, float eta_kappa, float eta_phi,
+                             const float* lo, const float* hi)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    if (P != ctx->P || P < 1) return fail(SIM_EINVAL, "P must equal the population size %d", ctx->P);
+    for (int r = 1; r < P; ++r)
+        if (ctx->dims[3 * r] != ctx->dims[0] || ctx->dims[3 * r + 1] != ctx->dims[1] || ctx->dims[3 * r + 2] != ctx->dims[2])
+            return fail(SIM_EINVAL, "the gradient step needs one grid shape for all robots");
+    const int64_t V = (int64_t)ctx->dims[0] * ctx->dims[1] * ctx->dims[2];
+    if ((int64_t)G != 3 * V) return fail(SIM_EINVAL, "G must be 3 x voxels per robot = %lld", (long long)(3 * V));
+    if (!genomes || !g_w || !g_kappa || !g_phi) return fail(SIM_EINVAL, "null genomes or gradients");
+    if (!std::isfinite(eta_w) || !std::isfinite(eta_kappa) || !std::isfinite(eta_phi))
+        return fail(SIM_EINVAL, "step sizes must be finite");
+    std::vector<int> list;
+    if (rows) {
+        if (n_rows < 0 || n_rows > P) return fail(SIM_EINVAL, "n_rows must be in 0..P");
+        for (int i = 0; i < n_rows; ++i) {
+            if (rows[i] < 0 || rows[i] >= P) return fail(SIM_EINVAL, "row %d out of range", rows[i]);
+            list.push_back(rows[i]);
+        }
+    } else {
+        for (int r = 0; r < P; ++r) list.push_back(r);
+    }
+    if (list.empty()) return SIM_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_grad_rows.ensure(list.size()));
+    VX_CK(cudaMemcpyAsync(ctx->d_grad_rows.p, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, s));
+    VX_LAUNCH(ctx, launch_grad_step(genomes, G, V, ctx->d_voff.p, g_w, g_kappa, g_phi, ctx->d_grad_rows.p,
+                                    (int)list.size(), eta_w, eta_kappa, eta_phi, lo, hi, s));
+    // the row list is copied from pageable memory
+    VX_CK(cudaStreamSynchronize(s));
     return SIM_OK;
 }
 

@@ -81,8 +81,15 @@ cudaError_t launch_decode_logits(const float* logits, int64_t n, MatConst mc, ui
 cudaError_t launch_decode_params(const uint8_t* mats, const float* w_in, const float* k_in,
                                  const float* p_in, int64_t n, uint8_t* mat, float* w,
                                  float* kappa, float* phi, int* bad, cudaStream_t s);
+cudaError_t launch_decode_param_rows(const uint8_t* mats, const float* rows, int64_t V, int64_t n,
+                                     uint8_t* mat, float* w, float* kappa, float* phi, int* bad,
+                                     cudaStream_t s);
 cudaError_t launch_pe_table(int nx, int ny, int nz, const float* B, void* pe_bf16,
                             cudaStream_t s);
+cudaError_t launch_grad_step(float* genomes, int G, int64_t V, const int64_t* voff, const float* g_w,
+                             const float* g_kappa, const float* g_phi, const int* rows, int n_rows,
+                             float eta_w, float eta_kappa, float eta_phi, const float* lo,
+                             const float* hi, cudaStream_t s);
 cudaError_t launch_mlp_query(int P, int Q, const void* pe_bf16, const float* genomes, MatConst mc,
                              uint8_t* mat, float* w, float* kappa, float* phi, int* status,
                              int num_sms, cudaStream_t s);

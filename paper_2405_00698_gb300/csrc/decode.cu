@@ -59,6 +59,24 @@ __global__ void k_decode_params(const uint8_t* __restrict__ mats, const float* _
     }
 }
 
+// The same parametrisation read from genome rows [w (V) | kappa (V) | phi (V)] per robot.
+__global__ void k_decode_param_rows(const uint8_t* __restrict__ mats, const float* __restrict__ rows,
+                                    int64_t V, int64_t n, uint8_t* mat, float* w, float* kappa,
+                                    float* phi, int* bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / V, v = i - r * V;
+        const float* row = rows + 3 * V * r;
+        int m = mats[i];
+        if (m >= kNumMat) { m = 0; atomicOr(bad, 2); }
+        mat[i] = (uint8_t)m;
+        w[i] = row[v];
+        kappa[i] = row[V + v];
+        phi[i] = row[2 * V + v];
+    }
+}
+
 // Eq. (1): gamma(v) = [cos(2 pi B v), sin(2 pi B v)], v the voxel centre normalised to [0,1]^3.
 // FP64 with explicit round-to-nearest operations (no contraction), then rounded once to
 // bfloat16.  One thread per (query, row of B).
@@ -185,6 +203,15 @@ cudaError_t launch_decode_params(const uint8_t* mats, const float* w_in, const f
     if (n == 0) return cudaSuccess;
     k_decode_params<<<grid_for(n, 256), 256, 0, s>>>(mats, w_in, k_in, p_in, n, mat, w, kappa,
                                                      phi, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_param_rows(const uint8_t* mats, const float* rows, int64_t V, int64_t n,
+                                     uint8_t* mat, float* w, float* kappa, float* phi, int* bad,
+                                     cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_decode_param_rows<<<grid_for(n, 256), 256, 0, s>>>(mats, rows, V, n, mat, w, kappa, phi, bad);
     return cudaGetLastError();
 }
 

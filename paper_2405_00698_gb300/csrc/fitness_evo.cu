@@ -285,3 +285,51 @@ cudaError_t launch_diversity(const float* genomes, int P, int G, const uint8_t* 
 }
 
 }  // namespace vx
+
+// ----------------------------------------------------------------------------------------------
+// Lamarckian gradient step on genome rows [w | kappa | phi] (gradient-assisted co-design): for
+// listed row r and gene j, genome <- clamp(fmaf(eta_seg, d, genome), lo_j, hi_j) with d the
+// adjoint's gradient of voxel j mod V of robot r (robot r's voxels start at voff[r]) and eta_seg
+// the step of the gene's segment.
+// ----------------------------------------------------------------------------------------------
+namespace vx {
+namespace {
+
+__global__ void k_grad_step(float* __restrict__ genomes, int G, int64_t V, const int64_t* __restrict__ voff,
+                            const float* __restrict__ g_w, const float* __restrict__ g_kappa,
+                            const float* __restrict__ g_phi, const int* __restrict__ rows, float eta_w,
+                            float eta_kappa, float eta_phi, const float* __restrict__ lo,
+                            const float* __restrict__ hi)
+{
+    const int r = rows[blockIdx.y];
+    float* row = genomes + (size_t)r * G;
+    const int64_t base = voff[r];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G; j += gridDim.x * blockDim.x) {
+        const int seg = (int)(j / V);
+        const int64_t v = j - seg * V;
+        const float* grad = seg == 0 ? g_w : (seg == 1 ? g_kappa : g_phi);
+        const float eta = seg == 0 ? eta_w : (seg == 1 ? eta_kappa : eta_phi);
+        float x = __fmaf_rn(eta, grad[base + v], row[j]);
+        if (lo) x = fmaxf(x, lo[j]);
+        if (hi) x = fminf(x, hi[j]);
+        row[j] = x;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_grad_step(float* genomes, int G, int64_t V, const int64_t* voff, const float* g_w,
+                             const float* g_kappa, const float* g_phi, const int* rows, int n_rows,
+                             float eta_w, float eta_kappa, float eta_phi, const float* lo,
+                             const float* hi, cudaStream_t s)
+{
+    if (n_rows == 0 || G == 0) return cudaSuccess;
+    const int T = 256;
+    int bx = (G + T - 1) / T;
+    if (bx > 64) bx = 64;
+    k_grad_step<<<dim3(bx, n_rows), T, 0, s>>>(genomes, G, V, voff, g_w, g_kappa, g_phi, rows, eta_w,
+                                               eta_kappa, eta_phi, lo, hi);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libvoxsim.so")
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ESTATE, SIM_ETIMEOUT, SIM_ENUMERIC = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
-MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS = 0, 1, 2, 3
+MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS, MODE_PARAM_ROWS = 0, 1, 2, 3, 4
 ACC_AUTO, ACC_ATOMIC, ACC_GATHER = 0, 1, 2
 MLP_TENSOR, MLP_SIMT = 0, 1
 PATH_AUTO, PATH_RESIDENT, PATH_STREAMED, PATH_PLAIN = 0, 1, 2, 3
@@ -24,7 +24,7 @@ LATTICE_AUTO, LATTICE_CORNER, LATTICE_COMPACT = 0, 1, 2
 GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
-           "sim_fitness", "evo_generation", "evo_generation_static", "sim_set_checkpointing",
+           "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
            "sim_backward", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
@@ -66,6 +66,10 @@ class VoxelParams(C.Structure):
     _fields_ = [("mat", C.c_void_p), ("w", C.c_void_p), ("kappa", C.c_void_p), ("phi", C.c_void_p)]
 
 
+class ParamRows(C.Structure):
+    _fields_ = [("mat", C.c_void_p), ("rows", C.c_void_p)]
+
+
 class EvoParams(C.Structure):
     _fields_ = [("elites", C.c_int32), ("mut_threshold", C.c_uint32), ("sigma", C.c_float),
                 ("keep_threshold", C.c_uint32), ("seed", C.c_uint64)]
@@ -90,6 +94,8 @@ def lib():
             "sim_fitness": [vp, vp, i32],
             "evo_generation": [vp, vp, vp, vp, i32, i32, vp, u64, vp, vp],
             "evo_generation_static": [vp, vp, vp, i32, i32, vp, u64, vp, vp, vp],
+            "evo_gradient_step": [vp, vp, i32, i32, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float,
+                                  vp, vp],
             "sim_set_checkpointing": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
             "sim_autotune": [vp, i32, vp, vp],
@@ -164,7 +170,15 @@ class Simulator:
         d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
         P = d.shape[0]
         keep = [d]
-        if mode == MODE_PARAMS:
+        if mode == MODE_PARAM_ROWS:
+            mat, rows = genomes
+            ptrs = [_ptr(mat), _ptr(rows)]
+            mems = {m for _, m in ptrs}
+            assert len(mems) == 1, "materials and rows must both be host or both device"
+            pr = ParamRows(*[p for p, _ in ptrs])
+            keep += [pr, mat, rows]
+            gptr, mem = C.addressof(pr), mems.pop()
+        elif mode == MODE_PARAMS:
             mat, w, kappa, phi = genomes
             ptrs = [_ptr(mat), _ptr(w), _ptr(kappa), _ptr(phi)]
             mems = {m for _, m in ptrs}
@@ -288,6 +302,22 @@ class Simulator:
         _check(lib().evo_generation(self._h, _ptr(fitness)[0], _ptr(genomes_in)[0],
                                     _ptr(genomes_out)[0], int(P), int(G), C.byref(e),
                                     int(generation), _ptr(parents)[0], _ptr(mask)[0]))
+
+
+    def evo_gradient_step(self, genomes, g_w, g_kappa, g_phi, eta, rows=None, lo=None, hi=None):
+        """Lamarckian step on MODE_PARAM_ROWS genome rows (device f32 [P, 3V]) along sim_backward's
+        per-voxel gradients: genome <- clamp(eta_seg * grad + genome, lo, hi) for the listed robots
+        (host int sequence, None = all); eta = (eta_w, eta_kappa, eta_phi); lo / hi device f32
+        [3V] or None."""
+        ew, ek, ep = (float(e) for e in eta)
+        P, G = genomes.shape
+        rl = None if rows is None else np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+        self._sync_inputs(MEM_DEVICE)
+        _check(lib().evo_gradient_step(self._h, _ptr(genomes)[0], int(P), int(G), _ptr(g_w)[0],
+                                       _ptr(g_kappa)[0], _ptr(g_phi)[0],
+                                       None if rl is None else rl.ctypes.data,
+                                       0 if rl is None else int(rl.size), ew, ek, ep,
+                                       _ptr(lo)[0], _ptr(hi)[0]))
 
 
 def fitness_function():
