@@ -41,7 +41,7 @@ SMEM_PEAK_GBS = 152 * 128 * 2.07
 # DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
 # 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
 # stays in shared memory, so traffic grows with the robots, not with the steps.
-LATTICE_DRAM_BYTES_PER_ROBOT = 18.93e6 / 152
+LATTICE_DRAM_BYTES_PER_ROBOT = 18.91e6 / 152
 LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of k_step_lattice (152 robots, 1000 steps) scaled by robots; "
                         "independent of the step count")
 

@@ -109,7 +109,8 @@ def run_lamarckian(sim: "vs.Simulator", mats, genomes, dims: Sequence[int], gene
     simulate with checkpoints, take the fitness, run the adjoint of the elites' summed fitness,
     move the elites one gradient step uphill (evo_gradient_step, per-segment steps `eta`, box
     `bounds` = (lo, hi) or the default of param_bounds), then breed the next generation with the
-    unchanged genetic operators from the improved elites.  Returns (records, final genomes)."""
+    unchanged genetic operators from the improved elites (their Gaussian mutation is not held to
+    the box).  Returns (records, final genomes)."""
     import torch
     P, G = genomes.shape
     V = G // 3
