@@ -59,6 +59,8 @@ def parse():
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
+    ap.add_argument("--case", choices=["streamed"], default=None,
+                    help="run one extra measurement alone (for profiling; --robots sets its robots)")
     return ap.parse_args()
 
 
@@ -193,6 +195,9 @@ def run_ours(args):
         generation()
     torch.cuda.synchronize()
     sim.timing()
+    # the population entering the timed loop, so the end-to-end pass can replay the same
+    # generations (the evolution is deterministic)
+    replay_from = (state["g_in"].clone(), state["gen"])
     # timed region: device-resident inputs, L2 flushed between steps (outside the events)
     clocks = ClockSampler(local)
     clocks.start()
@@ -222,8 +227,11 @@ def run_ours(args):
     value, updates_all, secs = shards.job_throughput(float(updates), total_ms * 1e-3, "cuda")
     total_ms = secs * 1e3
 
-    # end to end through the public API, continuing the evolution of the timed loop: every step
-    # copies that generation's genomes in from pinned host memory and reads the fitness back
+    # end to end through the public API over the same generations as the first timed steps: every
+    # step copies that generation's genomes in from pinned host memory and reads the fitness back
+    state["g_in"].copy_(replay_from[0])
+    state["gen"] = replay_from[1]
+    del replay_from
     pinned = torch.empty(genomes_h.shape, dtype=torch.float32).pin_memory()
     fit_h = torch.empty(P, dtype=torch.float64).pin_memory()
     e2e_ms, e2e_updates = 0.0, 0
@@ -505,8 +513,24 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+def run_case(args):
+    """One extra measurement alone, printed as its own JSON object (a profiling aid, not a bench
+    line)."""
+    import torch
+    from paper_2405_00698_gb300 import build as B
+    from paper_2405_00698_gb300 import voxsim as vs
+    B.build()
+    stream = torch.cuda.current_stream()
+    peaks, _ = measured_peaks()
+    P = args.robots if args.robots != P_ROBOTS else 64
+    print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
