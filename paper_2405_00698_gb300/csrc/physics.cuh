@@ -109,6 +109,26 @@ __device__ __forceinline__ void for_each_dir(F&& f)
     }
 }
 
+// Directions D0 .. D0 + N - 1.
+template <int D0, int N, class F>
+__device__ __forceinline__ void for_each_dir_in(F&& f)
+{
+    if constexpr (N > 0) {
+        f(DirTag<D0>{});
+        for_each_dir_in<D0 + 1, N - 1>(f);
+    }
+}
+
+// First directions of consecutive batches of B directions: 0, B, 2B, ... below 13.
+template <int B, int D0 = 0, class F>
+__device__ __forceinline__ void for_each_batch(F&& f)
+{
+    if constexpr (D0 < 13) {
+        f(DirTag<D0>{});
+        for_each_batch<B, D0 + B>(f);
+    }
+}
+
 // Spring dashpot of the paper's preset (Table II spring damping ratio): adds
 // c_s ((v_b - v_a) . u) u to the force on a, c_s = spring_c sqrt(k) (spring_c = 2 zeta sqrt(m / 2)).
 __device__ __forceinline__ void spring_dashpot(SpringEval& e, float dvx, float dvy, float dvz, float k,

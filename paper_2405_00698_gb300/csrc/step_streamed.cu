@@ -17,9 +17,15 @@
 namespace vx {
 namespace {
 
+// Loads of 4 directions in flight per batch and at least 4 blocks of 256 threads per SM (64
+// registers): measured 0.085 ms per step on 16 robots 40x40x40 against 0.101 ms for loads behind
+// each direction's mask test; batches of 1, 2 or 13 directions and 1, 3 or 5 blocks per SM were
+// slower.
 constexpr int kStreamThreads = 256;
+constexpr int kStreamBatch = 4;
+constexpr int kStreamMinBlocks = 4;
 
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
 k_step_streamed(StreamArgs a, int n)
 {
     const int r = a.robots[blockIdx.y];
@@ -38,32 +44,61 @@ k_step_streamed(StreamArgs a, int n)
     const float2 sc = a.sc[n];
     const StepConst c = a.c;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    for_each_dir([&](auto t) {                 // forward springs (c, c + offset(d))
-        constexpr int d = decltype(t)::value;
-        if (!((fl >> d) & 1u)) return;
-        const float4 ub = uin[cidx + lattice_offset<d>(X, XY)];
-        SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z),
-                                          c.edge, lattice_rest<d>(c), prm[d * C + cidx],
-                                          prm[(13 + d) * C + cidx], prm[(26 + d) * C + cidx], sc.x, sc.y);
-        if (c.damped) {
-            const float4 vb = vin[cidx + lattice_offset<d>(X, XY)];
-            spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), prm[d * C + cidx], c);
-        }
-        Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
+    // Loads are issued for a batch of directions before any of them is evaluated (absent springs
+    // read their own corner and zero parameters, so every address is valid and no load waits on
+    // a branch): the memory-level parallelism the per-step pass needs.  The sums keep the fixed
+    // order (forward by direction, then backward by direction).
+    constexpr int kBatch = kStreamBatch;
+    for_each_batch<kBatch>([&](auto t0) {      // forward springs (c, c + offset(d))
+        constexpr int d0 = decltype(t0)::value;
+        constexpr int nb = d0 + kBatch <= 13 ? kBatch : 13 - d0;
+        float4 ub[nb];
+        float pk[nb], pa[nb], pb[nb];
+        for_each_dir_in<d0, nb>([&](auto t) {
+            constexpr int d = decltype(t)::value, i = d - d0;
+            const bool has = (fl >> d) & 1u;
+            ub[i] = uin[has ? cidx + lattice_offset<d>(X, XY) : cidx];
+            pk[i] = prm[d * C + cidx];
+            pa[i] = prm[(13 + d) * C + cidx];
+            pb[i] = prm[(26 + d) * C + cidx];
+        });
+        for_each_dir_in<d0, nb>([&](auto t) {
+            constexpr int d = decltype(t)::value, i = d - d0;
+            if (!((fl >> d) & 1u)) return;
+            SpringEval e = spring_eval_dir<d>(__fsub_rn(ub[i].x, u.x), __fsub_rn(ub[i].y, u.y), __fsub_rn(ub[i].z, u.z),
+                                              c.edge, lattice_rest<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
+            if (c.damped) {
+                const float4 vb = vin[cidx + lattice_offset<d>(X, XY)];
+                spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[i], c);
+            }
+            Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
+        });
     });
-    for_each_dir([&](auto t) {                 // backward springs (c - offset(d), c)
-        constexpr int d = decltype(t)::value;
-        if (!((fl >> (16 + d)) & 1u)) return;
-        const int na = cidx - lattice_offset<d>(X, XY);
-        const float4 ua = uin[na];
-        SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z),
-                                          c.edge, lattice_rest<d>(c), prm[d * C + na],
-                                          prm[(13 + d) * C + na], prm[(26 + d) * C + na], sc.x, sc.y);
-        if (c.damped) {
-            const float4 va = vin[na];
-            spring_dashpot(e, __fsub_rn(v.x, va.x), __fsub_rn(v.y, va.y), __fsub_rn(v.z, va.z), prm[d * C + na], c);
-        }
-        Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
+    for_each_batch<kBatch>([&](auto t0) {      // backward springs (c - offset(d), c)
+        constexpr int d0 = decltype(t0)::value;
+        constexpr int nb = d0 + kBatch <= 13 ? kBatch : 13 - d0;
+        float4 ua[nb];
+        float pk[nb], pa[nb], pb[nb];
+        for_each_dir_in<d0, nb>([&](auto t) {
+            constexpr int d = decltype(t)::value, i = d - d0;
+            const bool has = (fl >> (16 + d)) & 1u;
+            const int na = has ? cidx - lattice_offset<d>(X, XY) : cidx;
+            ua[i] = uin[na];
+            pk[i] = prm[d * C + na];
+            pa[i] = prm[(13 + d) * C + na];
+            pb[i] = prm[(26 + d) * C + na];
+        });
+        for_each_dir_in<d0, nb>([&](auto t) {
+            constexpr int d = decltype(t)::value, i = d - d0;
+            if (!((fl >> (16 + d)) & 1u)) return;
+            SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua[i].x), __fsub_rn(u.y, ua[i].y), __fsub_rn(u.z, ua[i].z),
+                                              c.edge, lattice_rest<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
+            if (c.damped) {
+                const float4 va = vin[cidx - lattice_offset<d>(X, XY)];
+                spring_dashpot(e, __fsub_rn(v.x, va.x), __fsub_rn(v.y, va.y), __fsub_rn(v.z, va.z), pk[i], c);
+            }
+            Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
+        });
     });
     mass_update(u, v, Fx, Fy, Fz, c);
     a.u_out[mo + cidx] = u;
