@@ -225,6 +225,8 @@ def run_ours(args):
     dist_barrier(world)
     clk = clocks.stop()
     value, updates_all, secs = shards.job_throughput(float(updates), total_ms * 1e-3, "cuda")
+    # the paper's unit is ambiguous (springs, masses or both per step): springs + masses too
+    sm_value, _, _ = shards.job_throughput(float(updates + masses), total_ms * 1e-3, "cuda")
     total_ms = secs * 1e3
 
     # end to end through the public API over the same generations as the timed steps: every
@@ -274,6 +276,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(genomes_h.nbytes),
                 "d2h_bytes_per_step": int(P * 8)},
         "gpu_launches": launches,
+        "spring_plus_mass_updates_per_s": sm_value,
         "roofline": {"bound": "smem", "kernel": "k_step_lattice",
                      "achieved": achieved_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                      "frac": achieved_gbs / SMEM_PEAK_GBS, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
@@ -287,7 +290,7 @@ def run_ours(args):
         rec["cpu_baseline"] = cpu_baseline(genomes_h, Bmat_h, N, budget_s=12.0)
     if not args.no_extras and world == 1:
         sim.close()
-        rec["batched_vs_plain"] = measure_uneven(vs, stream, args)
+        rec["batched_vs_plain"] = measure_uneven(vs, stream, args, peaks)
         rec["adjoint"] = measure_adjoint(vs, stream, args)
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
@@ -311,7 +314,7 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_steps=100):
+def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, plain_steps=100):
     """4096 robots, axes from {4,...,12}, occupancy U[0.3, 0.9]: the persistent batched launch
     for 5000 steps, against the plain form (one launch per robot per pass) on a stratified
     sample of 64 robots for 100 steps (a rate: spring updates per second)."""
@@ -327,24 +330,38 @@ def measure_uneven(vs, stream, args, P=4096, N=5000, plain_robots=64, plain_step
     ms = _timed(stream, lambda: sim.step(N))
     kms, launches = sim.timing()
     batched = float(S.astype(np.int64).sum()) * N / (ms * 1e-3)
+    # algorithmic shared-memory bytes of the resident kernels (48 B per spring update, 36 B per
+    # mass update) against the shared-memory peak
+    batched_gbs = (48.0 * S.astype(np.int64).sum() + 36.0 * M.astype(np.int64).sum()) * N / (ms * 1e-3) / 1e9
     sim.close()
     sub = pop.subset(W.stratified_subset(S, plain_robots))
     res = {}
     for name, path in (("plain", vs.PATH_PLAIN), ("batched_same_sample", vs.PATH_AUTO)):
         s2 = vs.Simulator(W.CONFIG, stream=stream, path=path)
         s2.set_population_from(sub)
-        _, S2 = s2.counts()
+        M2, S2 = s2.counts()
         s2.step(5)
         ms2 = _timed(stream, lambda: s2.step(plain_steps))
         res[name] = float(S2.astype(np.int64).sum()) * plain_steps / (ms2 * 1e-3)
+        if path == vs.PATH_PLAIN:
+            # device-memory bytes of the plain passes: per spring its endpoints, parameters,
+            # corner ids and positions (64 B) and six float atomics (48 B); per mass its corner
+            # id, u, v and force read, force cleared, u and v written (92 B)
+            res["plain_gbs"] = (112.0 * S2.astype(np.int64).sum() + 92.0 * M2.astype(np.int64).sum()) \
+                * plain_steps / (ms2 * 1e-3) / 1e9
         s2.close()
     return {"workload": f"{P} robots, axes from {{4,6,8,10,12}}, occupancy U[0.3,0.9], connected, "
                         f"{N} steps", "unit": "spring-updates/s", "batched": batched,
             "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
+            "batched_roofline": {"bound": "smem", "achieved": batched_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
+                                 "frac": batched_gbs / SMEM_PEAK_GBS},
             "autotune": {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
                          "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted)": kinds.tolist(),
                          "atomic_threads": threads.tolist(), "seconds": tune_s},
             "plain": res["plain"], "batched_on_plain_sample": res["batched_same_sample"],
+            "plain_roofline": {"bound": "hbm", "achieved": res["plain_gbs"], "peak": peaks["hbm_gbs"],
+                               "unit": "GB/s", "frac": res["plain_gbs"] / peaks["hbm_gbs"],
+                               "note": "launch bound: two launches per robot and step"},
             "plain_sample": f"{plain_robots} robots stratified by spring count, {plain_steps} steps",
             "speedup_vs_plain": batched / res["plain"]}
 
