@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         const float4 ub = su[cidx + lattice_offset<d>(X, XY)];
                         const SpringEval e = spring_eval_dir<d>(
                             __fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z), c.edge,
-                            lattice_rest<d>(c), prm[d * S + cidx], prm[(13 + d) * S + cidx],
+                            lattice_rest<d>(c), lattice_rest_sq<d>(c), prm[d * S + cidx], prm[(13 + d) * S + cidx],
                             prm[(26 + d) * S + cidx], sc.x, sc.y);
                         Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
                     });
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         const float4 ua = su[na];
                         const SpringEval e = spring_eval_dir<d>(
                             __fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z), c.edge,
-                            lattice_rest<d>(c), prm[d * S + na], prm[(13 + d) * S + na],
+                            lattice_rest<d>(c), lattice_rest_sq<d>(c), prm[d * S + na], prm[(13 + d) * S + na],
                             prm[(26 + d) * S + na], sc.x, sc.y);
                         Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
                     });
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         const float k = prm[d * S + cidx];
                         const SpringEval e = spring_eval_dir<d>(
                             __fsub_rn(ub.x, un.x), __fsub_rn(ub.y, un.y), __fsub_rn(ub.z, un.z), c.edge,
-                            lattice_rest<d>(c), k, prm[(13 + d) * S + cidx], prm[(26 + d) * S + cidx],
+                            lattice_rest<d>(c), lattice_rest_sq<d>(c), k, prm[(13 + d) * S + cidx], prm[(26 + d) * S + cidx],
                             sc.x, sc.y);
                         float ldx, ldy, ldz, dk, da, db;
                         spring_adjoint(e, k, lFx - gb.x, lFy - gb.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz,
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         const float k = prm[d * S + na];
                         const SpringEval e = spring_eval_dir<d>(
                             __fsub_rn(un.x, ua.x), __fsub_rn(un.y, ua.y), __fsub_rn(un.z, ua.z), c.edge,
-                            lattice_rest<d>(c), k, prm[(13 + d) * S + na], prm[(26 + d) * S + na], sc.x,
+                            lattice_rest<d>(c), lattice_rest_sq<d>(c), k, prm[(13 + d) * S + na], prm[(26 + d) * S + na], sc.x,
                             sc.y);
                         float ldx, ldy, ldz, dk, da, db;
                         spring_adjoint(e, k, ga.x - lFx, ga.y - lFy, ga.z - lFz, sc.x, sc.y, ldx, ldy, ldz,

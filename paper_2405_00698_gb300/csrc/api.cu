@@ -239,6 +239,9 @@ struct voxsim_ctx {
         c.edge = (float)p.edge;
         c.edge_sqrt2 = (float)(p.edge * 1.4142135623730951);
         c.edge_sqrt3 = (float)(p.edge * 1.7320508075688772);
+        c.edge_sq = (float)(p.edge * p.edge);
+        c.edge_sq2 = (float)(2.0 * p.edge * p.edge);
+        c.edge_sq3 = (float)(3.0 * p.edge * p.edge);
         c.ground_on = p.ground_on ? 1 : 0;
         c.spring_c = (float)(2.0 * p.spring_zeta * std::sqrt(p.mass / 2.0));
         c.ground_c = (float)(2.0 * p.ground_zeta * std::sqrt(p.k_ground * p.mass));

@@ -54,6 +54,9 @@ struct StepConst {
     float edge;
     float edge_sqrt2;
     float edge_sqrt3;
+    float edge_sq;      // rest lengths squared: edge^2, 2 edge^2, 3 edge^2
+    float edge_sq2;
+    float edge_sq3;
     int ground_on;
     int damped;         // spring dashpots present (spring_c > 0)
     float spring_c;     // 2 zeta_s sqrt(mass / 2): dashpot coefficient = spring_c sqrt(k)

@@ -11,7 +11,8 @@ namespace vx {
 
 // Force on the first endpoint a of a spring (the second endpoint b receives its negative).
 //   du = u_b - u_a (displacements from the rest lattice), d = d0 + du with d0 the lattice
-//   offset, l = |d|; extension without cancellation e0 = l - L0 = (2 d0.du + du.du) / (l + L0);
+//   offset; from the cancellation-free numerator n = 2 d0.du + du.du, l^2 = L0^2 + n and the
+//   extension e0 = l - L0 = n / (l + L0);
 //   actuated rest length L = L0 + act with act = (alpha L0) sin(w t) + (beta L0) cos(w t);
 //   f = k (l - L) d / l.
 // Outputs the force g (on a), and for the adjoint the unit-free pieces ext = l - L and inv = 1/l.
@@ -26,17 +27,14 @@ struct SpringEval {
 // drop out of the arithmetic statically.
 template <int D>
 __device__ __forceinline__ SpringEval spring_eval_dir(float dux, float duy, float duz, float edge,
-                                                      float L0, float k, float pa, float pb, float sn,
-                                                      float cs)
+                                                      float L0, float L0sq, float k, float pa, float pb,
+                                                      float sn, float cs)
 {
     constexpr int ox = lattice_dir(D, 0), oy = lattice_dir(D, 1), oz = lattice_dir(D, 2);
     SpringEval e;
     e.dx = ox ? __fadd_rn(ox > 0 ? edge : -edge, dux) : dux;
     e.dy = oy ? __fadd_rn(oy > 0 ? edge : -edge, duy) : duy;
     e.dz = oz ? __fadd_rn(oz > 0 ? edge : -edge, duz) : duz;
-    const float l2 = __fmaf_rn(e.dz, e.dz, __fmaf_rn(e.dy, e.dy, __fmul_rn(e.dx, e.dx)));
-    e.inv = rsqrtf(l2);
-    const float l = __fmul_rn(l2, e.inv);
     // d0 . du over the non-zero components of d0 (each +-edge)
     float d0du = 0.0f;
     if (ox) d0du = __fmaf_rn(ox > 0 ? edge : -edge, dux, d0du);
@@ -44,33 +42,37 @@ __device__ __forceinline__ SpringEval spring_eval_dir(float dux, float duy, floa
     if (oz) d0du = __fmaf_rn(oz > 0 ? edge : -edge, duz, d0du);
     const float dudu = __fmaf_rn(duz, duz, __fmaf_rn(duy, duy, __fmul_rn(dux, dux)));
     const float num = __fmaf_rn(2.0f, d0du, dudu);
+    const float l2 = __fadd_rn(L0sq, num);      // |d0 + du|^2 = L0^2 + 2 d0.du + du.du
+    e.inv = rsqrtf(l2);
+    const float l = __fmul_rn(l2, e.inv);
     const float act = __fmaf_rn(pa, sn, __fmul_rn(pb, cs));
     e.ext = __fsub_rn(__fdividef(num, __fadd_rn(l, L0)), act);
     const float f = l2 > 1e-30f ? __fmul_rn(__fmul_rn(k, e.ext), e.inv) : 0.0f;
-    e.gx = __fmul_rn(f, e.dx);
-    e.gy = __fmul_rn(f, e.dy);
+    const float2 gxy = __fmul2_rn(make_float2(f, f), make_float2(e.dx, e.dy));
+    e.gx = gxy.x;
+    e.gy = gxy.y;
     e.gz = __fmul_rn(f, e.dz);
     return e;
 }
 
 // The same spring evaluation for a lattice offset (ox, oy, oz) known only at run time.
 __device__ __forceinline__ SpringEval spring_eval_rt(float dux, float duy, float duz, int ox, int oy, int oz,
-                                                     float edge, float L0, float k, float pa, float pb,
-                                                     float sn, float cs)
+                                                     float edge, float L0, float L0sq, float k, float pa,
+                                                     float pb, float sn, float cs)
 {
     SpringEval e;
     e.dx = ox ? __fadd_rn(ox > 0 ? edge : -edge, dux) : dux;
     e.dy = oy ? __fadd_rn(oy > 0 ? edge : -edge, duy) : duy;
     e.dz = oz ? __fadd_rn(oz > 0 ? edge : -edge, duz) : duz;
-    const float l2 = __fmaf_rn(e.dz, e.dz, __fmaf_rn(e.dy, e.dy, __fmul_rn(e.dx, e.dx)));
-    e.inv = rsqrtf(l2);
-    const float l = __fmul_rn(l2, e.inv);
     float d0du = 0.0f;
     if (ox) d0du = __fmaf_rn(ox > 0 ? edge : -edge, dux, d0du);
     if (oy) d0du = __fmaf_rn(oy > 0 ? edge : -edge, duy, d0du);
     if (oz) d0du = __fmaf_rn(oz > 0 ? edge : -edge, duz, d0du);
     const float dudu = __fmaf_rn(duz, duz, __fmaf_rn(duy, duy, __fmul_rn(dux, dux)));
     const float num = __fmaf_rn(2.0f, d0du, dudu);
+    const float l2 = __fadd_rn(L0sq, num);      // |d0 + du|^2 = L0^2 + 2 d0.du + du.du
+    e.inv = rsqrtf(l2);
+    const float l = __fmul_rn(l2, e.inv);
     const float act = __fmaf_rn(pa, sn, __fmul_rn(pb, cs));
     e.ext = __fsub_rn(__fdividef(num, __fadd_rn(l, L0)), act);
     const float f = l2 > 1e-30f ? __fmul_rn(__fmul_rn(k, e.ext), e.inv) : 0.0f;
@@ -86,6 +88,21 @@ __device__ __forceinline__ float lattice_rest(const StepConst& c)
 {
     constexpr int cls = (lattice_dir(D, 0) != 0) + (lattice_dir(D, 1) != 0) + (lattice_dir(D, 2) != 0);
     return cls == 1 ? c.edge : (cls == 2 ? c.edge_sqrt2 : c.edge_sqrt3);
+}
+
+// Its square (edge^2 times 1, 2 or 3, each rounded once from the exact value).
+template <int D>
+__device__ __forceinline__ float lattice_rest_sq(const StepConst& c)
+{
+    constexpr int cls = (lattice_dir(D, 0) != 0) + (lattice_dir(D, 1) != 0) + (lattice_dir(D, 2) != 0);
+    return cls == 1 ? c.edge_sq : (cls == 2 ? c.edge_sq2 : c.edge_sq3);
+}
+
+// The same for an offset known at run time.
+__device__ __forceinline__ float lattice_rest_sq_rt(int ox, int oy, int oz, const StepConst& c)
+{
+    const int cls = (ox != 0) + (oy != 0) + (oz != 0);
+    return cls == 1 ? c.edge_sq : (cls == 2 ? c.edge_sq2 : c.edge_sq3);
 }
 
 // Corner-index offset of lattice direction D on a grid with X corners per row and XY per layer.

@@ -96,20 +96,21 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     a.ckpt_v[o] = v;
                 }
                 const float2 sc = a.sc[n];
-                float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+                float2 Fxy = make_float2(0.f, 0.f);
+                float Fz = 0.f;
                 // phase A: forward springs (c, c + offset(d))
                 for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> d) & 1u)) return;
                     const float4 ub = su[cidx + lattice_offset<d>(X, XY)];
                     SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
-                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c),
+                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
                                                       pk[d], pa[d], pb[d], sc.x, sc.y);
                     if constexpr (DAMPED) {
                         const float4 vb = sv[cidx + lattice_offset<d>(X, XY)];
                         spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[d], c);
                     }
-                    Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
+                    Fxy = __fadd2_rn(Fxy, make_float2(e.gx, e.gy)); Fz = __fadd_rn(Fz, e.gz);
                     fb[d * S + cidx] = make_float4(e.gx, e.gy, e.gz, 0.f);
                 });
                 group_sync(bar, gthreads);
@@ -118,10 +119,10 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> (16 + d)) & 1u)) return;
                     const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];   // force on a
-                    Fx = __fsub_rn(Fx, g.x); Fy = __fsub_rn(Fy, g.y); Fz = __fsub_rn(Fz, g.z);
+                    Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
                 });
                 if (mass) {
-                    mass_update(u, v, Fx, Fy, Fz, c);
+                    mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
                     su[cidx] = u;
                     if (DAMPED) sv[cidx] = v;
                 }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_compact(
                     const float4 ua = su[ca];
                     const float4 ub = su[cb];
                     SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y),
-                                                      __fsub_rn(ub.z, ua.z), c.edge, lattice_rest<d>(c),
+                                                      __fsub_rn(ub.z, ua.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
                                                       pk[d], pa[d], pb[d], sc.x, sc.y);
                     if constexpr (DAMPED) {
                         const float4 va = sv[ca];

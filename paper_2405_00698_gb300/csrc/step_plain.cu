@@ -27,7 +27,8 @@ k_plain_springs(const int2* __restrict__ ab, const float4* __restrict__ prm, con
     const float4 ua = u[ca], ub = u[cb];
     const float2 sc = sc_tab[n];
     SpringEval ev = spring_eval_rt(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y), __fsub_rn(ub.z, ua.z),
-                                   ox, oy, oz, c.edge, p.x, p.y, p.z * p.x, p.w * p.x, sc.x, sc.y);
+                                   ox, oy, oz, c.edge, p.x, lattice_rest_sq_rt(ox, oy, oz, c), p.y, p.z * p.x,
+                                   p.w * p.x, sc.x, sc.y);
     if (c.damped) {
         const float4 va = v[ca], vb = v[cb];
         spring_dashpot(ev, __fsub_rn(vb.x, va.x), __fsub_rn(vb.y, va.y), __fsub_rn(vb.z, va.z), p.y, c);

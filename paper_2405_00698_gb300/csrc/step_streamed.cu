@@ -66,7 +66,7 @@ k_step_streamed(StreamArgs a, int n)
             constexpr int d = decltype(t)::value, i = d - d0;
             if (!((fl >> d) & 1u)) return;
             SpringEval e = spring_eval_dir<d>(__fsub_rn(ub[i].x, u.x), __fsub_rn(ub[i].y, u.y), __fsub_rn(ub[i].z, u.z),
-                                              c.edge, lattice_rest<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
+                                              c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
             if (c.damped) {
                 const float4 vb = vin[cidx + lattice_offset<d>(X, XY)];
                 spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[i], c);
@@ -92,7 +92,7 @@ k_step_streamed(StreamArgs a, int n)
             constexpr int d = decltype(t)::value, i = d - d0;
             if (!((fl >> (16 + d)) & 1u)) return;
             SpringEval e = spring_eval_dir<d>(__fsub_rn(u.x, ua[i].x), __fsub_rn(u.y, ua[i].y), __fsub_rn(u.z, ua[i].z),
-                                              c.edge, lattice_rest<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
+                                              c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c), pk[i], pa[i], pb[i], sc.x, sc.y);
             if (c.damped) {
                 const float4 va = vin[cidx - lattice_offset<d>(X, XY)];
                 spring_dashpot(e, __fsub_rn(v.x, va.x), __fsub_rn(v.y, va.y), __fsub_rn(v.z, va.z), pk[i], c);
