@@ -59,7 +59,7 @@ def parse():
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
-    ap.add_argument("--case", choices=["streamed"], default=None,
+    ap.add_argument("--case", choices=["streamed", "streamed_adjoint"], default=None,
                     help="run one extra measurement alone (for profiling; --robots sets its robots)")
     return ap.parse_args()
 
@@ -294,6 +294,7 @@ def run_ours(args):
         rec["adjoint"] = measure_adjoint(vs, stream, args)
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
+        rec["streamed_adjoint"] = measure_streamed_adjoint(vs, stream, args, peaks)
     if rank == 0:
         print(json.dumps(rec))
     sim.close()
@@ -445,6 +446,43 @@ def measure_lamarckian(vs, stream, args, P=512, N=2000, K=100):
             "forward_spring_updates_per_s": float(S.astype(np.int64).sum()) * N / (ms * 1e-3)}
 
 
+def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100):
+    """The adjoint on large robots (16 robots 40x40x40 at occupancy 0.7, state in HBM): forward
+    with checkpoints every 100 steps, then the backward pass (segment replays with recording and
+    the reverse sweep), as robot gradients per second and as algorithmic HBM bytes against the
+    measured peak.  A 500-step sample of the 5000-step workload."""
+    import torch
+    rng = np.random.default_rng(6)
+    pop = W.workload_large(P, seed=5, n=n)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(W.CONFIG, stream=stream)
+    sim.set_checkpointing(K)
+    args_pop = (t(pop.mats), t(w), t(kappa), t(phi))
+    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+    dl = torch.ones(P, dtype=torch.float64, device="cuda")
+    sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
+    sim.step(N)
+    sim.backward(dl, *g)                           # warm-up (buffers, graph)
+    sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
+    fwd = _timed(stream, lambda: sim.step(N))
+    bwd = _timed(stream, lambda: sim.backward(dl, *g))
+    M, S = sim.counts()
+    sim.close()
+    Ssum, Msum = float(S.astype(np.int64).sum()), float(M.astype(np.int64).sum())
+    # algorithmic device-memory bytes per step: forward 12 B per spring + 64 B per mass; backward
+    # (replay with records, then the reverse step) 48 B per spring + 224 B per mass
+    fwd_gbs = (12.0 * Ssum + 64.0 * Msum) * N / (fwd * 1e-3) / 1e9
+    bwd_gbs = (48.0 * Ssum + 224.0 * Msum) * N / (bwd * 1e-3) / 1e9
+    return {"workload": f"{P} robots {n}^3, occupancy 0.7, per-voxel parameters, {N} steps (sample of 5000), "
+                        f"checkpoints every {K}",
+            "grads_per_s": P / ((fwd + bwd) * 1e-3), "forward_ms": fwd, "backward_ms": bwd,
+            "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": fwd_gbs / peaks["hbm_gbs"]},
+            "backward_roofline": {"bound": "hbm", "achieved": bwd_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": bwd_gbs / peaks["hbm_gbs"]}}
+
+
 def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=1000):
     """64 robots 40x40x40 at occupancy 0.7 (Bernoulli, largest component), state in HBM, one
     launch per step; a 1000-step sample of the 5000-step workload."""
@@ -539,8 +577,12 @@ def run_case(args):
     B.build()
     stream = torch.cuda.current_stream()
     peaks, _ = measured_peaks()
-    P = args.robots if args.robots != P_ROBOTS else 64
-    print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
+    if args.case == "streamed":
+        P = args.robots if args.robots != P_ROBOTS else 64
+        print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
+    else:
+        P = args.robots if args.robots != P_ROBOTS else 16
+        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P)}))
 
 
 def main():

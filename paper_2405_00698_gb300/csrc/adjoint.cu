@@ -20,6 +20,7 @@
 // end (one add per spring and incident voxel).
 #include <cmath>
 
+#include "adjoint.cuh"
 #include "common.cuh"
 #include "physics.cuh"
 
@@ -31,29 +32,6 @@ constexpr int kBlock = 768;
 __device__ __forceinline__ void group_sync(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Adjoint of one spring evaluated as e (force g on endpoint a), given lambda_f = lambda_F_a -
-// lambda_F_b: returns lambda_d (the adjoint of d = x_b - x_a) in (ldx, ldy, ldz) and the
-// sensitivities dL/dk, dL/d(alpha L0), dL/d(beta L0) of this step.
-//   f = k (l - L) d / l:  df/dd = k [ (l - L)/l I + (L/l) u u^T ],  u = d / l;
-//   df/dk = (l - L) u;    df/dL = -k u;   L = L0 + (alpha L0) sin + (beta L0) cos.
-__device__ __forceinline__ void spring_adjoint(const SpringEval& e, float k, float lfx, float lfy,
-                                               float lfz, float sn, float cs, float& ldx,
-                                               float& ldy, float& ldz, float& dk, float& da,
-                                               float& db)
-{
-    const float ul = (e.dx * lfx + e.dy * lfy + e.dz * lfz) * e.inv;    // u . lambda_f
-    const float ei = e.ext * e.inv;                                      // (l - L) / l
-    const float a1 = k * ei;
-    const float a2 = k * (1.0f - ei) * ul * e.inv;                       // k (L/l) (u.lf) / l
-    ldx = a1 * lfx + a2 * e.dx;
-    ldy = a1 * lfy + a2 * e.dy;
-    ldz = a1 * lfz + a2 * e.dz;
-    dk = e.ext * ul;
-    const float lL = -k * ul;
-    da = lL * sn;
-    db = lL * cs;
 }
 
 __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
@@ -163,35 +141,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                     }
                     const unsigned mode = __float_as_uint(un.w);
                     float lFx = 0.f, lFy = 0.f, lFz = 0.f;
-                    if (mass) {
-                        // v' = c (v~ + dt F~ / m), u' = u + dt v'  (lambda_u, lambda_v hold step n+1)
-                        const float l1x = lvx + c.dt * lux, l1y = lvy + c.dt * luy, l1z = lvz + c.dt * luz;
-                        const float kf = c.damping * c.dt_over_m;
-                        const float fx = kf * l1x, fy = kf * l1y, fz = kf * l1z;
-                        const float tx = c.damping * l1x, ty = c.damping * l1y, tz = c.damping * l1z;
-                        if (mode == kFree) {
-                            lFx = fx; lFy = fy; lFz = fz;
-                            lvx = tx; lvy = ty; lvz = tz;
-                        } else if (mode == kStick) {
-                            // horizontal force and velocity were zeroed; F_n = k_g (-z) adds to F_z
-                            lFz = fz;
-                            lvx = 0.f; lvy = 0.f; lvz = tz;
-                            luz += -c.k_ground * fz;
-                        } else {
-                            // slip: F~_h = F_h (1 - mu_k F_n / |F_h|), F~_z = F_z + F_n
-                            const float fn = c.k_ground * -(z0 + un.z);
-                            const float fhm = sqrtf(fh.x * fh.x + fh.y * fh.y);
-                            const float hx = fh.x / fhm, hy = fh.y / fhm;
-                            const float rr = c.mu_k * fn / fhm;
-                            const float ul = hx * fx + hy * fy;
-                            lFx = fx - rr * (fx - hx * ul);
-                            lFy = fy - rr * (fy - hy * ul);
-                            lFz = fz;
-                            const float lfn = -c.mu_k * ul + fz;
-                            luz += -c.k_ground * lfn;
-                            lvx = tx; lvy = ty; lvz = tz;
-                        }
-                    }
+                    if (mass) mass_adjoint(mode, z0 + un.z, fh, lux, luy, luz, lvx, lvy, lvz, lFx, lFy, lFz, c);
                     if (in) {
                         su[cidx] = un;
                         sg[cidx] = make_float4(lFx, lFy, lFz, 0.f);
@@ -234,38 +184,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
             }
             // ---- per-spring sensitivities -> per-voxel sums (mean over the incident voxels) ----
             if (in) {
-                const int ci = cidx % X, cj = (cidx / X) % (ny + 1), ck = cidx / XY;
                 const int64_t vo = a.pv.voff[r];
-                const uint8_t* mat = a.mat + vo;
                 for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> d) & 1u)) return;
-                    const int dd[3] = {lattice_dir(d, 0), lattice_dir(d, 1), lattice_dir(d, 2)};
-                    const int c0[3] = {ci, cj, ck};
-                    const int nn[3] = {nx, ny, nz};
-                    int lo[3], hi[3];
-                    for (int q = 0; q < 3; ++q) {
-                        if (dd[q] != 0) { lo[q] = hi[q] = dd[q] > 0 ? c0[q] : c0[q] - 1; }
-                        else { lo[q] = c0[q] - 1; hi[q] = c0[q]; }
-                        lo[q] = max(lo[q], 0);
-                        hi[q] = min(hi[q], nn[q] - 1);
-                    }
-                    int cnt = 0;
-                    for (int zz = lo[2]; zz <= hi[2]; ++zz)
-                        for (int yy = lo[1]; yy <= hi[1]; ++yy)
-                            for (int xx = lo[0]; xx <= hi[0]; ++xx) cnt += mat[xx + nx * (yy + ny * zz)] != 0;
-                    const float L0 = lattice_rest<d>(c);
-                    const float inv = 1.0f / (float)cnt;
-                    const float gk = acck[d] * inv, ga = acca[d] * L0 * inv, gb = accb[d] * L0 * inv;
-                    for (int zz = lo[2]; zz <= hi[2]; ++zz)
-                        for (int yy = lo[1]; yy <= hi[1]; ++yy)
-                            for (int xx = lo[0]; xx <= hi[0]; ++xx) {
-                                const int vv = xx + nx * (yy + ny * zz);
-                                if (!mat[vv]) continue;
-                                atomicAdd(&a.g_k[vo + vv], gk);
-                                atomicAdd(&a.g_a[vo + vv], ga);
-                                atomicAdd(&a.g_b[vo + vv], gb);
-                            }
+                    spring_sens_to_voxels<d>(cidx, X, XY, nx, ny, nz, a.mat + vo, acck[d], acca[d], accb[d], c,
+                                             a.g_k + vo, a.g_a + vo, a.g_b + vo);
                 });
             }
         }

@@ -163,12 +163,16 @@ struct voxsim_ctx {
     cudaGraphExec_t stream_graph = nullptr;
     int stream_graph_n = -1;
     const void* stream_graph_key = nullptr;   // buffers the graph was captured with
+    const void* stream_graph_ckpt = nullptr;  // checkpoint buffer it writes (NULL: none)
+    int stream_graph_every = 0;
     void drop_graph()
     {
         if (stream_graph) cudaGraphExecDestroy(stream_graph);
         stream_graph = nullptr;
         stream_graph_n = -1;
         stream_graph_key = nullptr;
+        stream_graph_ckpt = nullptr;
+        stream_graph_every = 0;
     }
     // device buffers
     DevBuf<int> d_dims;
@@ -197,6 +201,10 @@ struct voxsim_ctx {
     int rec_n = 0;
     DevBuf<float4> d_ckpt_u, d_ckpt_v, d_rec_u;
     DevBuf<float2> d_rec_f, d_sc_rec;
+    // streamed adjoint: per-step records of a segment, adjoints, sensitivity sums, replay state
+    DevBuf<float4> d_srec_u, d_slu, d_slv, d_slF0, d_slF1, d_rep_u0, d_rep_u1, d_rep_v0, d_rep_v1;
+    DevBuf<float2> d_srec_f;
+    DevBuf<float> d_sacc;
     DevBuf<float> d_gk, d_ga, d_gb;
     // timing: one event pair per stepping call since the last sim_get_timing
     std::vector<cudaEvent_t> ev_pool;
@@ -572,6 +580,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? lattice_default(ctx) : kKindStreamed;
         if (is_lattice(kind) && C > block) kind = fits_sm ? kKindAtomic : kKindStreamed;
         if (kind == kKindAtomic && !fits_sm) kind = kKindStreamed;
+        if (kind == kKindAtomic && ctx->ckpt_every > 0) kind = kKindStreamed;   // deterministic for the adjoint
         if (kind == kKindStreamed && ctx->p.path == SIM_PATH_RESIDENT) {
             if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
             kind = C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC ? lattice_default(ctx) : kKindAtomic;
@@ -690,10 +699,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     a.item_robots = ctx->d_item_robots.p;
     a.n_items = ctx->n_items;
     a.queue = ctx->d_queue.p;
-    if (ctx->ckpt_every > 0) {
-        const int nseg = (n + ctx->ckpt_every - 1) / ctx->ckpt_every;
-        VX_CK(ctx->d_ckpt_u.ensure((size_t)nseg * ctx->M_cap));
-        VX_CK(ctx->d_ckpt_v.ensure((size_t)nseg * ctx->M_cap));
+    if (ctx->ckpt_every > 0) {                  // (buffers sized by sim_step_n)
         a.ckpt_u = ctx->d_ckpt_u.p;
         a.ckpt_v = ctx->d_ckpt_v.p;
         a.ckpt_stride = ctx->M_cap;
@@ -790,7 +796,11 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
     a.c = ctx->stepconst();
     a.robots = ctx->d_stream.p;
     a.n_robots = ctx->n_stream;
+    const int K = ctx->ckpt_every;
     for (int i = 0; i < n; ++i) {
+        // the state at the start of every K-th step goes to its segment's checkpoint
+        a.ckpt_u = K > 0 && i % K == 0 ? ctx->d_ckpt_u.p + (size_t)(i / K) * ctx->M_cap : nullptr;
+        a.ckpt_v = K > 0 && i % K == 0 ? ctx->d_ckpt_v.p + (size_t)(i / K) * ctx->M_cap : nullptr;
         a.u_in = (i & 1) ? ctx->d_x_alt.p : ctx->d_x.p;
         a.u_out = (i & 1) ? ctx->d_x.p : ctx->d_x_alt.p;
         a.v_in = (i & 1) ? ctx->d_v_alt.p : ctx->d_v.p;
@@ -816,7 +826,9 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n)
     if (ctx->n_stream == 0) return SIM_OK;
     cudaStream_t s = ctx->stream;
     const void* key = ctx->d_sc.p;   // the step table may move when it grows
-    if (!(ctx->stream_graph && ctx->stream_graph_n == n && ctx->stream_graph_key == key)) {
+    const void* ckpt = ctx->ckpt_every > 0 ? (const void*)ctx->d_ckpt_u.p : nullptr;
+    if (!(ctx->stream_graph && ctx->stream_graph_n == n && ctx->stream_graph_key == key &&
+          ctx->stream_graph_ckpt == ckpt && ctx->stream_graph_every == ctx->ckpt_every)) {
         ctx->drop_graph();
         if (!ctx->capture_stream) VX_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         VX_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -830,6 +842,8 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n)
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
         ctx->stream_graph_n = n;
         ctx->stream_graph_key = key;
+        ctx->stream_graph_ckpt = ckpt;
+        ctx->stream_graph_every = ctx->ckpt_every;
     }
     VX_CK(cudaGraphLaunch(ctx->stream_graph, s));
     ctx->launches += n;
@@ -847,9 +861,13 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
     VX_CK(ctx->d_sc.ensure(n_steps));
     VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->step, n_steps,
                               ctx->d_sc.p, s));
-    if (ctx->ckpt_every > 0 && (ctx->n_big > 0 || ctx->n_stream > 0))
-        return fail(SIM_EINVAL, "checkpointing for the adjoint needs robots of at most %d corners",
-                    lattice_max_threads());
+    if (ctx->ckpt_every > 0 && ctx->n_big > 0)
+        return fail(SIM_EINVAL, "checkpointing needs the deterministic kernels (robots on the atomic kernel)");
+    if (ctx->ckpt_every > 0) {
+        const int nseg = (n_steps + ctx->ckpt_every - 1) / ctx->ckpt_every;
+        VX_CK(ctx->d_ckpt_u.ensure((size_t)nseg * ctx->M_cap));
+        VX_CK(ctx->d_ckpt_v.ensure((size_t)nseg * ctx->M_cap));
+    }
     cudaEvent_t ev[2];
     if (sim_status st = timing_pair(ctx, ev)) return st;
     VX_CK(cudaEventRecord(ev[0], s));
@@ -962,8 +980,89 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
         return fail(SIM_EINVAL, "checkpointing needs the bit-reproducible stepping (not SIM_ACC_ATOMIC)");
     if (k_steps > 0 && (ctx->p.spring_zeta != 0.0 || ctx->p.ground_zeta != 0.0))
         return fail(SIM_EINVAL, "the adjoint is built for undamped springs and ground (zeta = 0)");
+    const bool changed = (ctx->ckpt_every > 0) != (k_steps > 0);
     ctx->ckpt_every = k_steps;
     ctx->rec_valid = false;
+    ctx->drop_graph();
+    if (changed && ctx->have_pop && ctx->P > 0) {   // robots on the atomic kernel move to (or back from) the streamed path
+        DeviceGuard g(ctx->device);
+        if (sim_status st = build_work_items(ctx)) return st;
+    }
+    return SIM_OK;
+}
+
+// The adjoint of the streamed robots: per checkpoint segment, last to first, a recording replay
+// (the streamed step kernel) and a reverse sweep of one launch per step; the per-voxel
+// sensitivity sums go to the same accumulators as the resident adjoint's.
+static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
+{
+    cudaStream_t s = ctx->stream;
+    const int K = ctx->ckpt_every, N = ctx->rec_n;
+    const size_t Mc = ctx->M_cap;
+    VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
+    VX_CK(ctx->d_slF0.ensure(Mc)); VX_CK(ctx->d_slF1.ensure(Mc));
+    VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_u1.ensure(Mc));
+    VX_CK(ctx->d_rep_v0.ensure(Mc)); VX_CK(ctx->d_rep_v1.ensure(Mc));
+    VX_CK(ctx->d_sacc.ensure(39 * Mc));
+    StreamAdjArgs b{};
+    b.pv = ctx->view();
+    b.cflags = ctx->d_cflags.p;
+    b.prm = ctx->d_prm.p;
+    b.mat = ctx->d_mat.p;
+    b.u0 = ctx->d_x.p;
+    b.lu = ctx->d_slu.p;
+    b.lv = ctx->d_slv.p;
+    b.acc = ctx->d_sacc.p;
+    b.sc = ctx->d_sc_rec.p;
+    b.dL_df = dL_df;
+    b.c = ctx->stepconst();
+    b.robots = ctx->d_stream.p;
+    b.n_robots = ctx->n_stream;
+    b.g_k = ctx->d_gk.p;
+    b.g_a = ctx->d_ga.p;
+    b.g_b = ctx->d_gb.p;
+    const int maxc = ctx->max_stream_corner;
+    VX_LAUNCH(ctx, launch_stream_adj_init(b, maxc, s));
+    float4* lF[2] = {ctx->d_slF0.p, ctx->d_slF1.p};
+    float4* ru[2] = {ctx->d_rep_u0.p, ctx->d_rep_u1.p};
+    float4* rv[2] = {ctx->d_rep_v0.p, ctx->d_rep_v1.p};
+    StreamArgs f{};
+    f.pv = ctx->view();
+    f.cflags = ctx->d_cflags.p;
+    f.prm = ctx->d_prm.p;
+    f.sc = ctx->d_sc_rec.p;
+    f.c = ctx->stepconst();
+    f.robots = ctx->d_stream.p;
+    f.n_robots = ctx->n_stream;
+    const int nseg = (N + K - 1) / K;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int n0 = seg * K, n1 = std::min(N, n0 + K);
+        // replay from the checkpoint, recording every step
+        for (int i = 0; i < n1 - n0; ++i) {
+            f.u_in = i == 0 ? ctx->d_ckpt_u.p + (size_t)seg * Mc : ru[(i - 1) & 1];
+            f.v_in = i == 0 ? ctx->d_ckpt_v.p + (size_t)seg * Mc : rv[(i - 1) & 1];
+            f.u_out = ru[i & 1];
+            f.v_out = rv[i & 1];
+            f.rec_u = ctx->d_srec_u.p + (size_t)i * Mc;
+            f.rec_f = ctx->d_srec_f.p + (size_t)i * Mc;
+            VX_LAUNCH(ctx, launch_step_streamed(f, n0 + i, maxc, s));
+        }
+        // the mass part of the segment's last step, then per step its spring part and the mass
+        // part of the step before it
+        for (int j = n1; j >= n0; --j) {
+            b.step = j < n1 ? j : -1;
+            b.rec_u = j < n1 ? ctx->d_srec_u.p + (size_t)(j - n0) * Mc : nullptr;
+            b.lF_in = j < n1 ? lF[j & 1] : nullptr;
+            const bool mass = j - 1 >= n0;
+            b.mrec_u = mass ? ctx->d_srec_u.p + (size_t)(j - 1 - n0) * Mc : nullptr;
+            b.mrec_f = mass ? ctx->d_srec_f.p + (size_t)(j - 1 - n0) * Mc : nullptr;
+            b.lF_out = mass ? lF[(j - 1) & 1] : nullptr;
+            VX_LAUNCH(ctx, launch_stream_adj_step(b, maxc, s));
+        }
+    }
+    VX_LAUNCH(ctx, launch_stream_adj_voxels(b, maxc, s));
     return SIM_OK;
 }
 
@@ -984,36 +1083,40 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     VX_CK(ctx->d_sc_rec.ensure(ctx->rec_n));
     VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->rec_step0,
                                        ctx->rec_n, ctx->d_sc_rec.p, s));
-    const int threads = lattice_max_threads();
-    const int grid = std::min(ctx->n_items, ctx->num_sms);
-    VX_CK(ctx->d_rec_u.ensure((size_t)grid * K * threads));
-    VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
-    AdjointArgs a{};
-    a.pv = ctx->view();
-    a.corner_order = ctx->d_mass_corner.p;
-    a.cflags = ctx->d_cflags.p;
-    a.prm = ctx->d_prm.p;
-    a.mat = ctx->d_mat.p;
-    a.ckpt_u = ctx->d_ckpt_u.p;
-    a.ckpt_v = ctx->d_ckpt_v.p;
-    a.ckpt_stride = ctx->M_cap;
-    a.K = K;
-    a.nsteps = ctx->rec_n;
-    a.sc = ctx->d_sc_rec.p;
-    a.c = ctx->stepconst();
-    a.dL_df = dL_df;
-    a.items = ctx->d_items.p;
-    a.item_robots = ctx->d_item_robots.p;
-    a.n_items = ctx->n_items;
-    a.queue = ctx->d_queue.p;
-    a.rec_u = ctx->d_rec_u.p;
-    a.rec_f = ctx->d_rec_f.p;
-    a.g_k = ctx->d_gk.p;
-    a.g_a = ctx->d_ga.p;
-    a.g_b = ctx->d_gb.p;
-    const size_t smem = sizeof(float) * kAdjointSlotFloats * (size_t)threads;
-    VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
-    VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
+    if (ctx->n_items > 0) {
+        const int threads = lattice_max_threads();
+        const int grid = std::min(ctx->n_items, ctx->num_sms);
+        VX_CK(ctx->d_rec_u.ensure((size_t)grid * K * threads));
+        VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
+        AdjointArgs a{};
+        a.pv = ctx->view();
+        a.corner_order = ctx->d_mass_corner.p;
+        a.cflags = ctx->d_cflags.p;
+        a.prm = ctx->d_prm.p;
+        a.mat = ctx->d_mat.p;
+        a.ckpt_u = ctx->d_ckpt_u.p;
+        a.ckpt_v = ctx->d_ckpt_v.p;
+        a.ckpt_stride = ctx->M_cap;
+        a.K = K;
+        a.nsteps = ctx->rec_n;
+        a.sc = ctx->d_sc_rec.p;
+        a.c = ctx->stepconst();
+        a.dL_df = dL_df;
+        a.items = ctx->d_items.p;
+        a.item_robots = ctx->d_item_robots.p;
+        a.n_items = ctx->n_items;
+        a.queue = ctx->d_queue.p;
+        a.rec_u = ctx->d_rec_u.p;
+        a.rec_f = ctx->d_rec_f.p;
+        a.g_k = ctx->d_gk.p;
+        a.g_a = ctx->d_ga.p;
+        a.g_b = ctx->d_gb.p;
+        const size_t smem = sizeof(float) * kAdjointSlotFloats * (size_t)threads;
+        VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+        VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
+    }
+    if (ctx->n_stream > 0)
+        if (sim_status st = backward_streamed(ctx, dL_df)) return st;
     VX_LAUNCH(ctx, launch_adjoint_voxels(ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p, ctx->d_phi.p, ctx->matconst(),
                                          ctx->d_gk.p, ctx->d_ga.p, ctx->d_gb.p, (int64_t)V, g_w, g_kappa, g_phi, s));
     return SIM_OK;

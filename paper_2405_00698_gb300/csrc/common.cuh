@@ -172,8 +172,46 @@ struct StreamArgs {
     StepConst c;
     const int* robots;       // streamed robots (grid.y)
     int n_robots;
+    // checkpoint of the state at the start of this step (NULL: none), per corner
+    float4* ckpt_u;
+    float4* ckpt_v;
+    // record of this step for the adjoint (NULL: none), per corner: u before the update with the
+    // contact mode in .w, and the horizontal spring force before contact
+    float4* rec_u;
+    float2* rec_f;
 };
 cudaError_t launch_step_streamed(const StreamArgs& a, int n, int max_corners, cudaStream_t s);
+
+// Streamed adjoint (robots too large for one SM): records, adjoints and the per-spring
+// sensitivity sums live in device memory; one launch per reverse step does the spring part of
+// step j and the mass part of step j - 1 (which needs only the corner's own adjoints).
+struct StreamAdjArgs {
+    PopView pv;
+    const uint32_t* cflags;
+    const float* prm;        // per robot at 39 * moff: [3][13][C]
+    const uint8_t* mat;      // kept material per voxel
+    const float4* u0;        // any state array: rest height z0 in .w
+    const float4* rec_u;     // spring part: record of step j (u before the update, mode in .w)
+    const float4* mrec_u;    // mass part: record of step j - 1 (NULL: no mass part)
+    const float2* mrec_f;    //            its horizontal spring force before contact
+    const float4* lF_in;     // adjoint of the summed spring force at step j (read, neighbours too)
+    float4* lF_out;          // the same at step j - 1 (written by the mass part)
+    float4* lu;              // adjoint of u (per corner)
+    float4* lv;              // adjoint of v
+    float* acc;              // per robot at 39 * moff: [3][13][C] sensitivity sums to k, alpha L0, beta L0
+    const float2* sc;        // sin / cos of w t of the recorded call
+    int step;                // j, index of the spring part's step in the recorded call (-1: none)
+    const double* dL_df;
+    StepConst c;
+    const int* robots;       // streamed robots (grid.y)
+    int n_robots;
+    float* g_k;              // per voxel accumulators
+    float* g_a;
+    float* g_b;
+};
+cudaError_t launch_stream_adj_init(const StreamAdjArgs& a, int max_corners, cudaStream_t s);
+cudaError_t launch_stream_adj_step(const StreamAdjArgs& a, int max_corners, cudaStream_t s);
+cudaError_t launch_stream_adj_voxels(const StreamAdjArgs& a, int max_corners, cudaStream_t s);
 
 // The paper's organisation (baseline): one launch per robot per pass, two passes per step.
 cudaError_t launch_step_plain_robot(const int2* ab, const float4* prm, const int* mass_corner, float4* u,

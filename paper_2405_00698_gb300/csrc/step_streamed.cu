@@ -40,6 +40,10 @@ k_step_streamed(StreamArgs a, int n)
     float4 u = uin[cidx];
     const float4* __restrict__ vin = a.v_in + mo;
     float4 v = vin[cidx];
+    if (a.ckpt_u) {                             // state at the start of a checkpointed segment
+        a.ckpt_u[mo + cidx] = u;
+        a.ckpt_v[mo + cidx] = v;
+    }
     const float* __restrict__ prm = a.prm + 39 * mo;
     const float2 sc = a.sc[n];
     const StepConst c = a.c;
@@ -100,7 +104,12 @@ k_step_streamed(StreamArgs a, int n)
             Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
         });
     });
-    mass_update(u, v, Fx, Fy, Fz, c);
+    const float4 u_before = u;
+    const unsigned mode = mass_update(u, v, Fx, Fy, Fz, c);
+    if (a.rec_u) {                              // record for the adjoint's reverse sweep
+        a.rec_u[mo + cidx] = make_float4(u_before.x, u_before.y, u_before.z, __uint_as_float(mode));
+        a.rec_f[mo + cidx] = make_float2(Fx, Fy);
+    }
     a.u_out[mo + cidx] = u;
     a.v_out[mo + cidx] = v;
 }
