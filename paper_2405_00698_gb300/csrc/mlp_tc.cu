@@ -178,19 +178,35 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 // Convert a float32 [rows][K] weight block (8-byte aligned) into the swizzled bf16 layout.
+// Each thread takes kUnroll chunks of 8 values per round and issues all their loads before
+// converting any, so several global loads per thread are in flight.
+constexpr int kUnroll = 4;
 __device__ __forceinline__ void load_weights(const float* __restrict__ src, int rows, int K,
                                              int valid_rows, unsigned char* dst)
 {
     const int chunks = rows * (K / 8);
-    for (int c = threadIdx.x; c < chunks; c += kThreads) {
-        const int row = c / (K / 8), k0 = (c % (K / 8)) * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (row < valid_rows) {
-            const float2* p = reinterpret_cast<const float2*>(src + (size_t)row * K + k0);
-            const float2 a = p[0], b = p[1], cc = p[2], d = p[3];
-            v = make_uint4(pack_bf16(a.x, a.y), pack_bf16(b.x, b.y), pack_bf16(cc.x, cc.y), pack_bf16(d.x, d.y));
+    for (int c0 = threadIdx.x; c0 < chunks; c0 += kThreads * kUnroll) {
+        float2 v[kUnroll][4];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int c = c0 + u * kThreads;
+            const int row = c / (K / 8), k0 = (c % (K / 8)) * 8;
+            if (c < chunks && row < valid_rows) {
+                const float2* p = reinterpret_cast<const float2*>(src + (size_t)row * K + k0);
+                v[u][0] = p[0]; v[u][1] = p[1]; v[u][2] = p[2]; v[u][3] = p[3];
+            } else {
+                v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float2(0.f, 0.f);
+            }
         }
-        *reinterpret_cast<uint4*>(dst + sw128_offset(row, k0, rows)) = v;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int c = c0 + u * kThreads;
+            const int row = c / (K / 8), k0 = (c % (K / 8)) * 8;
+            if (c < chunks)
+                *reinterpret_cast<uint4*>(dst + sw128_offset(row, k0, rows)) =
+                    make_uint4(pack_bf16(v[u][0].x, v[u][0].y), pack_bf16(v[u][1].x, v[u][1].y),
+                               pack_bf16(v[u][2].x, v[u][2].y), pack_bf16(v[u][3].x, v[u][3].y));
+        }
     }
 }
 
