@@ -1,0 +1,133 @@
+"""Parity at the full workload sizes, in the launch configurations bench.py times, on sampled
+robots the FP64 oracle recomputes one by one:
+
+* 1024 MLP genomes on 8x8x8 grids, decode + 10,000 steps in one call (one lattice launch);
+* 4096 uneven robots after the autotuner's choices, 5000 steps;
+* 64 robots of 40x40x40 on the streamed path (one graph-captured launch per step), a 300-step
+  sample of the 5000-step run;
+* the adjoint of 512 robots of 8x8x8 over 2000 steps with checkpoints every 100.
+
+Robots are sampled evenly over the spring-count order.  The simulation is compared from the
+GPU's own decoded grid and weights (the decode is checked separately on the same genomes).  Over
+5000 and 10,000 steps contact switches make more trajectories ill-conditioned than over 1000,
+so up to a quarter of a sample may pass through the oracle's perturbation envelope
+(tests/parity.py) instead of the direct bar."""
+import numpy as np
+import pytest
+
+from paper_2405_00698_gb300 import workloads as W
+from tests.parity import check_population
+
+pytestmark = pytest.mark.gpu
+PHYS = W.CONFIG
+
+
+@pytest.fixture(scope="module")
+def vs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_00698_gb300 import build, voxsim
+    build.build()
+    return voxsim
+
+
+def test_mlp_population_full_size(vs, orc):
+    import torch
+    G, B = W.workload_mlp()
+    P, N, dims = G.shape[0], 10000, (8, 8, 8)
+    sim = vs.Simulator(PHYS)
+    sim.set_population(np.tile(np.int32(dims), (P, 1)), torch.from_numpy(G).cuda(), vs.MODE_MLP,
+                       B=torch.from_numpy(B).cuda())
+    vox = sim.voxels()
+    M, S = sim.counts()
+    sim.step(N)
+    f = sim.fitness()
+    x, _, off = sim.state()
+    sim.close()
+    pick = W.stratified_subset(S, 12)
+    # decode: exact outside the guard band of the oracle's FP64 scores
+    for g in pick:
+        mat, w, logits, guard = orc.mlp_query(dims, B, G[g])
+        got = vox["decoded"][g * 512:(g + 1) * 512]
+        top = np.sort(logits[:, :5], axis=1)
+        sure = (top[:, -1] - top[:, -2]) > 2 * guard
+        assert np.array_equal(got[sure], mat[sure]), g
+    # simulation of the GPU's decoded robots
+    pop = W.make_population([dims] * len(pick), [vox["decoded"][g * 512:(g + 1) * 512].reshape(8, 8, 8)
+                                                  for g in pick])
+    w = np.concatenate([vox["w"][g * 512:(g + 1) * 512] for g in pick]).astype(np.float64)
+    kappa = np.asarray(PHYS.k_mat)[pop.mats]
+    phi = np.asarray(PHYS.phase_mat)[pop.mats]
+    ref = orc.run_population(pop, PHYS, N, w=w, kappa=kappa, phi=phi, want_x=True)
+    assert np.array_equal(ref["S"], S[pick]) and np.array_equal(ref["M"], M[pick])
+    xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
+    offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick])])
+    check_population(orc, pop, PHYS, N, f[pick], xs, offs, ref, w=w, kappa=kappa, phi=phi, K=4,
+                     max_sensitive_frac=0.25)
+
+
+def test_uneven_population_full_size(vs, orc):
+    pop = W.workload_uneven()
+    N = 5000
+    sim = vs.Simulator(PHYS)
+    sim.set_population_from(pop)
+    sim.autotune(20)
+    sim.step(N)
+    f = sim.fitness()
+    x, _, off = sim.state()
+    M, S = sim.counts()
+    sim.close()
+    pick = W.stratified_subset(S, 16)
+    sub = pop.subset(pick)
+    ref = orc.run_population(sub, PHYS, N, want_x=True)
+    assert np.array_equal(ref["S"], S[pick])
+    xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
+    offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick])])
+    check_population(orc, sub, PHYS, N, f[pick], xs, offs, ref, K=4, max_sensitive_frac=0.25)
+
+
+def test_large_robots_full_size_sample(vs, orc):
+    pop = W.workload_large()
+    N = 300
+    sim = vs.Simulator(PHYS)
+    sim.set_population_from(pop)
+    sim.step(N)
+    f = sim.fitness()
+    x, _, off = sim.state()
+    M, S = sim.counts()
+    sim.close()
+    pick = W.stratified_subset(S, 2)
+    sub = pop.subset(pick)
+    ref = orc.run_population(sub, PHYS, N, want_x=True)
+    assert np.array_equal(ref["S"], S[pick])
+    xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
+    offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick])])
+    check_population(orc, sub, PHYS, N, f[pick], xs, offs, ref, K=2)
+
+
+def test_adjoint_full_size_sample(vs, orc):
+    import torch
+    rng = np.random.default_rng(3)
+    P, N, K = 512, 2000, 100
+    pop = W.population_uniform(P, (8, 8, 8), seed=3)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(PHYS)
+    sim.set_checkpointing(K)
+    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+    sim.step(N)
+    _, S = sim.counts()
+    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+    sim.backward(t(np.ones(P)), *g)
+    torch.cuda.synchronize()
+    g = [a.cpu().numpy() for a in g]
+    sim.close()
+    bad = []
+    for r in W.stratified_subset(S, 3):
+        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+        _, rw, rk, rp = orc.adjoint(pop.grid(r), (8, 8, 8), PHYS, N, 1.0, w[a:b], kappa[a:b], phi[a:b])
+        errs = [float(np.abs(x[a:b] - y).max() / max(np.abs(y).max(), 1e-30)) for x, y in zip(g, (rw, rk, rp))]
+        if max(errs) > 1e-3:
+            bad.append((r, errs))
+    assert len(bad) <= 1, bad
