@@ -2,22 +2,23 @@
 // with respect to the per-voxel material weight w, stiffness kappa and actuation phase phi
 // (k_v = w_v kappa_v, actuation a_v sin(w t + phi_v) with a_v = w_v amp[material]).
 //
-// One thread group per robot, one thread per grid corner, as in the forward lattice kernel.
-// For each checkpoint segment, last to first:
-//   replay:  the forward steps of the segment from its checkpoint with the same shared
-//            arithmetic (physics.cuh) and summation order as the forward run, so every state and
-//            contact mode is reproduced bit for bit; each step records the state before the
-//            update, the contact mode and the horizontal force before contact;
-//   reverse: the transpose of each recorded step, last to first, with the contact modes held
-//            fixed (their switches are measure-zero events where the step is not differentiable):
-//            the mass part turns (lambda_u, lambda_v) of step n+1 into the adjoint force
-//            lambda_F and the velocity adjoint of step n; the spring part turns lambda_F into
-//            lambda_u contributions and accumulates each spring's sensitivity to k, alpha L0 and
-//            beta L0.
-// Shared memory per robot slot: the spring parameters (read by both endpoints), u and lambda_F
-// as planes over the slot's corners.  Each endpoint recomputes the springs it shares, so nothing
-// is added atomically inside a robot; per-voxel gradients are accumulated with atomics at the
-// end (one add per spring and incident voxel).
+// For each checkpoint segment, last to first, the host launches
+//   the replay: the forward lattice kernel in recording mode from the segment's checkpoint (the
+//     same code as the forward run, so every state and contact mode is reproduced bit for bit),
+//     writing each step's state before the update, contact mode and horizontal force before
+//     contact to device memory;
+//   the reverse sweep (this kernel): one thread group per robot, one thread per grid corner,
+//     the transpose of each recorded step, last to first, with the contact modes held fixed
+//     (their switches are measure-zero events where the step is not differentiable).  Per step:
+//       mass part: (lambda_u, lambda_v) of step n+1 -> the adjoint force lambda_F and the velocity
+//         adjoint of step n;
+//       spring part: each forward spring's owner forms its transpose from both endpoints'
+//         recorded positions and adjoint forces, keeps its own share, accumulates the spring's
+//         sensitivities to k, alpha L0 and beta L0 in registers and leaves the other endpoint's
+//         share in a shared-memory plane, which that endpoint adds in direction order.
+// The adjoints and sensitivity sums are carried from one segment's launch to the next in device
+// memory; the last launch scatters the sums onto the voxels with atomics (one add per spring
+// and incident voxel).
 #include <cmath>
 
 #include "adjoint.cuh"
@@ -62,128 +63,102 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
             const int S = gthreads;                       // plane stride of this slot
-            // slot of this group: u (float4), lambda_F (float4), 39 parameter floats per corner
-            float4* su = reinterpret_cast<float4*>(reinterpret_cast<char*>(sm4) +
-                                                   (size_t)group * sizeof(float) * kAdjointSlotFloats * S);
-            float4* sg = su + S;                                       // lambda_F at step n
-            float* prm = reinterpret_cast<float*>(sg + S);             // [3][13][S] parameters
+            // slot of this group: recorded u, adjoint force, 13 planes of spring adjoints
+            float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
+            float4* sg = su + S;
+            float4* sl = sg + S;                          // plane d: lambda_d of spring (c, d)
             const int cidx = lt;
             const bool in = cidx < C;
             const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
             const bool mass = (fl >> 31) & 1u;
-            if (in) {
-                const float* gp = a.prm + 39 * mo;
-                for (int q = 0; q < 39; ++q) prm[q * S + cidx] = gp[q * C + cidx];
-            }
-            const int M = a.pv.n_mass[r];
-            // adjoint of the final state: the fitness is the mean of u_x over the masses
-            float lux = mass ? (float)(a.dL_df[r] / (double)M) : 0.f, luy = 0.f, luz = 0.f;
-            float lvx = 0.f, lvy = 0.f, lvz = 0.f;
+            const int64_t o = mo + cidx;
+            const float* prm = a.prm + 39 * mo;
+            float* __restrict__ accg = a.acc + 39 * mo;
+            // adjoints and sensitivity sums carried over from the later segment (or their
+            // initial values: the fitness is the mean of u_x over the masses)
+            float lux = 0.f, luy = 0.f, luz = 0.f, lvx = 0.f, lvy = 0.f, lvz = 0.f;
             float acck[13], acca[13], accb[13];
+            if (a.first) {
+                if (mass) lux = (float)(a.dL_df[r] / (double)a.pv.n_mass[r]);
 #pragma unroll
-            for (int d = 0; d < 13; ++d) { acck[d] = 0.f; acca[d] = 0.f; accb[d] = 0.f; }
-            float4* rec_u = a.rec_u + (size_t)blockIdx.x * a.K * kBlock + (size_t)group * S;
-            float2* rec_f = a.rec_f + (size_t)blockIdx.x * a.K * kBlock + (size_t)group * S;
-            const float z0 = in ? a.ckpt_u[mo + cidx].w : 0.f;
-            const int nseg = (a.nsteps + a.K - 1) / a.K;
-            group_sync(bar, gthreads);
-            for (int seg = nseg - 1; seg >= 0; --seg) {
-                const int n0 = seg * a.K, n1 = min(a.nsteps, n0 + a.K);
-                // ---- replay the segment from its checkpoint, recording every step ----
-                float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+                for (int d = 0; d < 13; ++d) { acck[d] = 0.f; acca[d] = 0.f; accb[d] = 0.f; }
+            } else {
                 if (in) {
-                    const int64_t o = (int64_t)seg * a.ckpt_stride + mo + cidx;
-                    u = a.ckpt_u[o];
-                    v = a.ckpt_v[o];
+                    const float4 lu = a.lu[o], lv = a.lv[o];
+                    lux = lu.x; luy = lu.y; luz = lu.z; lvx = lv.x; lvy = lv.y; lvz = lv.z;
                 }
-                for (int n = n0; n < n1; ++n) {
-                    if (in) su[cidx] = u;
-                    group_sync(bar, gthreads);
-                    const float2 sc = a.sc[n];
-                    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-                    for_each_dir([&](auto t) {        // own forward springs
-                        constexpr int d = decltype(t)::value;
-                        if (!((fl >> d) & 1u)) return;
-                        const float4 ub = su[cidx + lattice_offset<d>(X, XY)];
-                        const SpringEval e = spring_eval_dir<d>(
-                            __fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z), c.edge,
-                            lattice_rest<d>(c), lattice_rest_sq<d>(c), prm[d * S + cidx], prm[(13 + d) * S + cidx],
-                            prm[(26 + d) * S + cidx], sc.x, sc.y);
-                        Fx = __fadd_rn(Fx, e.gx); Fy = __fadd_rn(Fy, e.gy); Fz = __fadd_rn(Fz, e.gz);
-                    });
-                    for_each_dir([&](auto t) {        // backward springs: the forward run's values
-                        constexpr int d = decltype(t)::value;
-                        if (!((fl >> (16 + d)) & 1u)) return;
-                        const int na = cidx - lattice_offset<d>(X, XY);
-                        const float4 ua = su[na];
-                        const SpringEval e = spring_eval_dir<d>(
-                            __fsub_rn(u.x, ua.x), __fsub_rn(u.y, ua.y), __fsub_rn(u.z, ua.z), c.edge,
-                            lattice_rest<d>(c), lattice_rest_sq<d>(c), prm[d * S + na], prm[(13 + d) * S + na],
-                            prm[(26 + d) * S + na], sc.x, sc.y);
-                        Fx = __fadd_rn(Fx, -e.gx); Fy = __fadd_rn(Fy, -e.gy); Fz = __fadd_rn(Fz, -e.gz);
-                    });
-                    unsigned mode = kFree;
-                    const float4 ub4 = u;
-                    if (mass) mode = mass_update(u, v, Fx, Fy, Fz, c);
-                    if (in) {
-                        rec_u[(size_t)(n - n0) * kBlock + cidx] = make_float4(ub4.x, ub4.y, ub4.z, __uint_as_float(mode));
-                        rec_f[(size_t)(n - n0) * kBlock + cidx] = make_float2(Fx, Fy);
-                    }
-                    group_sync(bar, gthreads);
-                }
-                // ---- reverse sweep of the segment ----
-                for (int n = n1 - 1; n >= n0; --n) {
-                    float4 un = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float2 fh = make_float2(0.f, 0.f);
-                    if (in) {
-                        un = rec_u[(size_t)(n - n0) * kBlock + cidx];
-                        fh = rec_f[(size_t)(n - n0) * kBlock + cidx];
-                    }
-                    const unsigned mode = __float_as_uint(un.w);
-                    float lFx = 0.f, lFy = 0.f, lFz = 0.f;
-                    if (mass) mass_adjoint(mode, z0 + un.z, fh, lux, luy, luz, lvx, lvy, lvz, lFx, lFy, lFz, c);
-                    if (in) {
-                        su[cidx] = un;
-                        sg[cidx] = make_float4(lFx, lFy, lFz, 0.f);
-                    }
-                    group_sync(bar, gthreads);
-                    const float2 sc = a.sc[n];
-                    for_each_dir([&](auto t) {        // own forward springs: a = c, b = c + offset
-                        constexpr int d = decltype(t)::value;
-                        if (!((fl >> d) & 1u)) return;
-                        const int nb = cidx + lattice_offset<d>(X, XY);
-                        const float4 ub = su[nb], gb = sg[nb];
-                        const float k = prm[d * S + cidx];
-                        const SpringEval e = spring_eval_dir<d>(
-                            __fsub_rn(ub.x, un.x), __fsub_rn(ub.y, un.y), __fsub_rn(ub.z, un.z), c.edge,
-                            lattice_rest<d>(c), lattice_rest_sq<d>(c), k, prm[(13 + d) * S + cidx], prm[(26 + d) * S + cidx],
-                            sc.x, sc.y);
-                        float ldx, ldy, ldz, dk, da, db;
-                        spring_adjoint(e, k, lFx - gb.x, lFy - gb.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz,
-                                       dk, da, db);
-                        lux -= ldx; luy -= ldy; luz -= ldz;
-                        acck[d] += dk; acca[d] += da; accb[d] += db;
-                    });
-                    for_each_dir([&](auto t) {        // backward springs: a = c - offset, b = c
-                        constexpr int d = decltype(t)::value;
-                        if (!((fl >> (16 + d)) & 1u)) return;
-                        const int na = cidx - lattice_offset<d>(X, XY);
-                        const float4 ua = su[na], ga = sg[na];
-                        const float k = prm[d * S + na];
-                        const SpringEval e = spring_eval_dir<d>(
-                            __fsub_rn(un.x, ua.x), __fsub_rn(un.y, ua.y), __fsub_rn(un.z, ua.z), c.edge,
-                            lattice_rest<d>(c), lattice_rest_sq<d>(c), k, prm[(13 + d) * S + na], prm[(26 + d) * S + na], sc.x,
-                            sc.y);
-                        float ldx, ldy, ldz, dk, da, db;
-                        spring_adjoint(e, k, ga.x - lFx, ga.y - lFy, ga.z - lFz, sc.x, sc.y, ldx, ldy, ldz,
-                                       dk, da, db);
-                        lux += ldx; luy += ldy; luz += ldz;
-                    });
-                    group_sync(bar, gthreads);
-                }
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    const bool has = (fl >> d) & 1u;
+                    acck[d] = has ? accg[d * C + cidx] : 0.f;
+                    acca[d] = has ? accg[(13 + d) * C + cidx] : 0.f;
+                    accb[d] = has ? accg[(26 + d) * C + cidx] : 0.f;
+                });
             }
-            // ---- per-spring sensitivities -> per-voxel sums (mean over the incident voxels) ----
-            if (in) {
+            const float z0 = in ? a.u0[o].w : 0.f;
+            for (int n = a.n1 - 1; n >= a.n0; --n) {
+                const int64_t ro = (int64_t)(n - a.n0) * a.rec_stride + o;
+                float4 un = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 fh = make_float2(0.f, 0.f);
+                if (in) {
+                    un = a.rec_u[ro];
+                    fh = a.rec_f[ro];
+                }
+                // mass part: (lambda_u, lambda_v) of step n+1 -> lambda_F and lambda_v of step n
+                float lFx = 0.f, lFy = 0.f, lFz = 0.f;
+                if (mass) mass_adjoint(__float_as_uint(un.w), z0 + un.z, fh, lux, luy, luz, lvx, lvy, lvz, lFx, lFy, lFz, c);
+                if (in) {
+                    su[cidx] = un;
+                    sg[cidx] = make_float4(lFx, lFy, lFz, 0.f);
+                }
+                group_sync(bar, gthreads);
+                const float2 sc = a.sc[n];
+                // the parameters are re-read every step (from L1/L2) rather than held in
+                // registers next to the 39 sensitivity sums: an opaque copy of the pointer keeps
+                // the compiler from hoisting the loads out of the step loop
+                const float* p = prm;
+                asm volatile("" : "+l"(p));
+                // own forward springs (a = c, b = c + offset): their transposes, the share of b
+                // left in plane d for b to collect
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> d) & 1u)) return;
+                    const int nb = cidx + lattice_offset<d>(X, XY);
+                    const float4 ub = su[nb], gb = sg[nb];
+                    const float k = p[d * C + cidx];
+                    const SpringEval e = spring_eval_dir<d>(
+                        __fsub_rn(ub.x, un.x), __fsub_rn(ub.y, un.y), __fsub_rn(ub.z, un.z), c.edge,
+                        lattice_rest<d>(c), lattice_rest_sq<d>(c), k, p[(13 + d) * C + cidx],
+                        p[(26 + d) * C + cidx], sc.x, sc.y);
+                    float ldx, ldy, ldz, dk, da, db;
+                    spring_adjoint(e, k, lFx - gb.x, lFy - gb.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz, dk, da, db);
+                    lux -= ldx; luy -= ldy; luz -= ldz;
+                    acck[d] += dk; acca[d] += da; accb[d] += db;
+                    sl[d * S + cidx] = make_float4(ldx, ldy, ldz, 0.f);
+                });
+                group_sync(bar, gthreads);
+                // backward springs (a = c - offset, b = c): their share, computed by a
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> (16 + d)) & 1u)) return;
+                    const float4 ld = sl[d * S + cidx - lattice_offset<d>(X, XY)];
+                    lux += ld.x; luy += ld.y; luz += ld.z;
+                });
+            }
+            if (!a.last) {                                // carry over to the earlier segment
+                if (in) {
+                    a.lu[o] = make_float4(lux, luy, luz, 0.f);
+                    a.lv[o] = make_float4(lvx, lvy, lvz, 0.f);
+                }
+                for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> d) & 1u)) return;
+                    accg[d * C + cidx] = acck[d];
+                    accg[(13 + d) * C + cidx] = acca[d];
+                    accg[(26 + d) * C + cidx] = accb[d];
+                });
+            } else if (in) {
+                // ---- per-spring sensitivities -> per-voxel sums (mean over the incident voxels) ----
                 const int64_t vo = a.pv.voff[r];
                 for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
@@ -192,6 +167,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                                              a.g_k + vo, a.g_a + vo, a.g_b + vo);
                 });
             }
+            group_sync(bar, gthreads);                    // the slot is free for the next item
         }
         __syncthreads();
     }

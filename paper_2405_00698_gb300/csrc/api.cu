@@ -199,8 +199,8 @@ struct voxsim_ctx {
     bool rec_valid = false;      // a recorded call is available
     int64_t rec_step0 = 0;
     int rec_n = 0;
-    DevBuf<float4> d_ckpt_u, d_ckpt_v, d_rec_u;
-    DevBuf<float2> d_rec_f, d_sc_rec;
+    DevBuf<float4> d_ckpt_u, d_ckpt_v;
+    DevBuf<float2> d_sc_rec;
     // streamed adjoint: per-step records of a segment, adjoints, sensitivity sums, replay state
     DevBuf<float4> d_srec_u, d_slu, d_slv, d_slF0, d_slF1, d_rep_u0, d_rep_u1, d_rep_v0, d_rep_v1;
     DevBuf<float2> d_srec_f;
@@ -991,6 +991,82 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
     return SIM_OK;
 }
 
+// The adjoint of the robots on the lattice kernels: per checkpoint segment, last to first, the
+// forward per-corner lattice kernel replays the segment from a copy of its checkpoint in
+// recording mode, then the reverse-sweep kernel runs over the records; adjoints and sensitivity
+// sums are carried between segments in device memory.  The checkpoints stay intact, so the
+// backward pass may be repeated (other dL_df) on the same recorded run.
+static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
+{
+    cudaStream_t s = ctx->stream;
+    const int K = ctx->ckpt_every, N = ctx->rec_n;
+    const size_t Mc = ctx->M_cap;
+    VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
+    VX_CK(ctx->d_sacc.ensure(39 * Mc));
+    VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_v0.ensure(Mc));
+    const int threads = lattice_max_threads();
+    const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
+    const int grid = std::min(ctx->n_items, ctx->num_sms);
+    LatticeArgs f{};
+    f.pv = ctx->view();
+    f.corner_order = ctx->d_mass_corner.p;
+    f.cflags = ctx->d_cflags.p;
+    f.prm = ctx->d_prm.p;
+    f.c = ctx->stepconst();
+    f.items = ctx->d_items.p;
+    f.item_robots = ctx->d_item_robots.p;
+    f.n_items = ctx->n_items;
+    f.queue = ctx->d_queue.p;
+    f.rec_u = ctx->d_srec_u.p;
+    f.rec_f = ctx->d_srec_f.p;
+    f.rec_stride = (int64_t)Mc;
+    AdjointArgs a{};
+    a.pv = ctx->view();
+    a.cflags = ctx->d_cflags.p;
+    a.prm = ctx->d_prm.p;
+    a.mat = ctx->d_mat.p;
+    a.u0 = ctx->d_x.p;
+    a.rec_u = ctx->d_srec_u.p;
+    a.rec_f = ctx->d_srec_f.p;
+    a.rec_stride = (int64_t)Mc;
+    a.lu = ctx->d_slu.p;
+    a.lv = ctx->d_slv.p;
+    a.acc = ctx->d_sacc.p;
+    a.sc = ctx->d_sc_rec.p;
+    a.c = ctx->stepconst();
+    a.dL_df = dL_df;
+    a.items = ctx->d_items.p;
+    a.item_robots = ctx->d_item_robots.p;
+    a.n_items = ctx->n_items;
+    a.queue = ctx->d_queue.p;
+    a.g_k = ctx->d_gk.p;
+    a.g_a = ctx->d_ga.p;
+    a.g_b = ctx->d_gb.p;
+    const int nseg = (N + K - 1) / K;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int n0 = seg * K, n1 = std::min(N, n0 + K);
+        VX_CK(cudaMemcpyAsync(ctx->d_rep_u0.p, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                              cudaMemcpyDeviceToDevice, s));
+        VX_CK(cudaMemcpyAsync(ctx->d_rep_v0.p, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                              cudaMemcpyDeviceToDevice, s));
+        f.u = ctx->d_rep_u0.p;
+        f.v = ctx->d_rep_v0.p;
+        f.sc = ctx->d_sc_rec.p + n0;
+        f.nsteps = n1 - n0;
+        VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+        VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, s));
+        a.n0 = n0;
+        a.n1 = n1;
+        a.first = seg == nseg - 1;
+        a.last = seg == 0;
+        VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+        VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
+    }
+    return SIM_OK;
+}
+
 // The adjoint of the streamed robots: per checkpoint segment, last to first, a recording replay
 // (the streamed step kernel) and a reverse sweep of one launch per step; the per-voxel
 // sensitivity sums go to the same accumulators as the resident adjoint's.
@@ -1074,7 +1150,6 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     if (ctx->P == 0 || ctx->rec_n == 0) return SIM_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
-    const int K = ctx->ckpt_every;
     const size_t V = ctx->V_tot;
     VX_CK(ctx->d_gk.ensure(V)); VX_CK(ctx->d_ga.ensure(V)); VX_CK(ctx->d_gb.ensure(V));
     VX_CK(cudaMemsetAsync(ctx->d_gk.p, 0, sizeof(float) * V, s));
@@ -1083,38 +1158,8 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
     VX_CK(ctx->d_sc_rec.ensure(ctx->rec_n));
     VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->rec_step0,
                                        ctx->rec_n, ctx->d_sc_rec.p, s));
-    if (ctx->n_items > 0) {
-        const int threads = lattice_max_threads();
-        const int grid = std::min(ctx->n_items, ctx->num_sms);
-        VX_CK(ctx->d_rec_u.ensure((size_t)grid * K * threads));
-        VX_CK(ctx->d_rec_f.ensure((size_t)grid * K * threads));
-        AdjointArgs a{};
-        a.pv = ctx->view();
-        a.corner_order = ctx->d_mass_corner.p;
-        a.cflags = ctx->d_cflags.p;
-        a.prm = ctx->d_prm.p;
-        a.mat = ctx->d_mat.p;
-        a.ckpt_u = ctx->d_ckpt_u.p;
-        a.ckpt_v = ctx->d_ckpt_v.p;
-        a.ckpt_stride = ctx->M_cap;
-        a.K = K;
-        a.nsteps = ctx->rec_n;
-        a.sc = ctx->d_sc_rec.p;
-        a.c = ctx->stepconst();
-        a.dL_df = dL_df;
-        a.items = ctx->d_items.p;
-        a.item_robots = ctx->d_item_robots.p;
-        a.n_items = ctx->n_items;
-        a.queue = ctx->d_queue.p;
-        a.rec_u = ctx->d_rec_u.p;
-        a.rec_f = ctx->d_rec_f.p;
-        a.g_k = ctx->d_gk.p;
-        a.g_a = ctx->d_ga.p;
-        a.g_b = ctx->d_gb.p;
-        const size_t smem = sizeof(float) * kAdjointSlotFloats * (size_t)threads;
-        VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
-        VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
-    }
+    if (ctx->n_items > 0)
+        if (sim_status st = backward_lattice(ctx, dL_df)) return st;
     if (ctx->n_stream > 0)
         if (sim_status st = backward_streamed(ctx, dL_df)) return st;
     VX_LAUNCH(ctx, launch_adjoint_voxels(ctx->d_mat.p, ctx->d_w.p, ctx->d_kappa.p, ctx->d_phi.p, ctx->matconst(),

@@ -157,6 +157,12 @@ struct LatticeArgs {
     float4* ckpt_v;
     int64_t ckpt_stride;     // corners per checkpoint (sum over robots)
     int ckpt_every;          // K
+    // replay records for the adjoint (NULL when off; undamped only): per step n of the call, at
+    // n * rec_stride + corner, the state before the update (contact mode in .w) and the
+    // horizontal spring force before contact
+    float4* rec_u;
+    float2* rec_f;
+    int64_t rec_stride;
 };
 
 // Streamed path (robots too large for one SM): one launch per step over all their corners.
@@ -221,15 +227,19 @@ cudaError_t launch_step_plain_robot(const int2* ab, const float4* prm, const int
 // Adjoint of the lattice stepping over one recorded call (see adjoint.cu).
 struct AdjointArgs {
     PopView pv;
-    const int* corner_order;
     const uint32_t* cflags;
     const float* prm;
     const uint8_t* mat;      // kept material per voxel
-    const float4* ckpt_u;
-    const float4* ckpt_v;
-    int64_t ckpt_stride;
-    int K;
-    int nsteps;              // steps of the recorded call
+    const float4* u0;        // any state array: rest height z0 in .w
+    const float4* rec_u;     // this segment's records, [n - n0][rec_stride]: state before the update, mode in .w
+    const float2* rec_f;     //   and the horizontal spring force before contact
+    int64_t rec_stride;
+    int n0, n1;              // steps of the segment within the recorded call
+    int first;               // the latest segment: start from the adjoint of the fitness
+    int last;                // the earliest segment: scatter the sensitivity sums onto voxels
+    float4* lu;              // adjoints of u and v carried between segments (per corner)
+    float4* lv;
+    float* acc;              // per robot at 39 * moff: [3][13][C] sensitivity sums carried between segments
     const float2* sc;        // sin / cos of w t per step of the recorded call
     StepConst c;
     const double* dL_df;     // [P]
@@ -237,13 +247,10 @@ struct AdjointArgs {
     const int* item_robots;
     int n_items;
     int* queue;
-    float4* rec_u;           // per block: [K][block threads] state and contact mode per step
-    float2* rec_f;           // per block: [K][block threads] horizontal force before contact
     float* g_k;              // per voxel: dL/dk_v, dL/d(alpha_v), dL/d(beta_v) accumulators
     float* g_a;
     float* g_b;
 };
-constexpr int kAdjointSlotFloats = 8 + 39;   // per corner: u, adjoint force (float4 each), 39 parameters
 cudaError_t launch_adjoint_lattice(const AdjointArgs& a, int grid, int threads, size_t smem,
                                    cudaStream_t s);
 cudaError_t launch_adjoint_voxels(const uint8_t* mat, const float* w, const float* kappa,

@@ -31,8 +31,10 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 }
 
 // DAMPED: spring dashpots of the paper's preset (a separate instantiation, so the undamped path
-// keeps its registers).
-template <bool DAMPED>
+// keeps its registers).  RECORD: the adjoint's replay of a checkpoint segment, which also writes
+// every step's state before the update with its contact mode, and the horizontal spring force
+// before contact.
+template <bool DAMPED, bool RECORD>
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -122,7 +124,15 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
                 });
                 if (mass) {
-                    mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                    if constexpr (RECORD) {            // replay for the adjoint: the step's inputs
+                        const float4 ub4 = u;
+                        const unsigned mode = mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                        const int64_t o = (int64_t)n * a.rec_stride + mo + cidx;
+                        a.rec_u[o] = make_float4(ub4.x, ub4.y, ub4.z, __uint_as_float(mode));
+                        a.rec_f[o] = Fxy;
+                    } else {
+                        mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                    }
                     su[cidx] = u;
                     if (DAMPED) sv[cidx] = v;
                 }
@@ -294,8 +304,9 @@ int lattice_max_threads() { return kMaxLatticeThreads; }
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
-    auto kernel = a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
-                          : (a.c.damped ? k_step_lattice<true> : k_step_lattice<false>);
+    auto kernel = a.rec_u ? k_step_lattice<false, true>
+                : a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
+                          : (a.c.damped ? k_step_lattice<true, false> : k_step_lattice<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<grid, threads, smem, s>>>(a);
