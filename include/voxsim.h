@@ -251,17 +251,24 @@ sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t
 
 /* Turn state checkpointing on (every k_steps steps, k_steps >= 1) or off (0).  While on, each
  * sim_step_n call records the state at its start and every k_steps steps after, which
- * sim_backward replays.  Errors: SIM_EINVAL, SIM_ENOMEM. */
+ * sim_backward replays (device memory: two float4 per grid corner per checkpoint, plus during
+ * sim_backward k_steps records of 24 bytes per corner).  Every robot must run on a deterministic
+ * kernel: while checkpointing is on, robots that would run on the atomic resident kernel run on
+ * the streamed path instead (the population's plan is rebuilt when the setting changes).
+ * The paper preset's dashpots (spring_zeta, ground_zeta != 0) are not differentiated.
+ * Errors: SIM_EINVAL (k_steps < 0, SIM_ACC_ATOMIC, damped parameters), SIM_ENOMEM. */
 sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 
 /* Reverse-mode gradient of L = sum_r dL_df[r] * fitness_r over the most recent recorded
  * sim_step_n call, with respect to the per-voxel material weight w, stiffness kappa and
  * actuation phase phi (k_v = w_v kappa_v, a_v = w_v amp_mat[material], phase phi_v).  The
  * forward steps are recomputed from the checkpoints segment by segment, bit-identically, and
- * each segment is swept backwards; contact modes of the forward run are held fixed.  Empty
- * voxels get 0.  dL_df: double [P]; g_w, g_kappa, g_phi: float, one entry per voxel of every
- * grid (concatenated as in sim_set_population); all device memory.
- * Errors: SIM_ESTATE without a recorded run, SIM_EINVAL, SIM_ENOMEM. */
+ * each segment is swept backwards; contact modes of the forward run are held fixed.  Robots on
+ * the resident lattice kernels and robots on the streamed path are both differentiated (each
+ * by its own sweep).  The checkpoints are left intact, so the call may be repeated with another
+ * dL_df on the same recorded run.  Empty voxels get 0.  dL_df: double [P]; g_w, g_kappa,
+ * g_phi: float, one entry per voxel of every grid (concatenated as in sim_set_population); all
+ * device memory.  Errors: SIM_ESTATE without a recorded run, SIM_EINVAL, SIM_ENOMEM. */
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
                         float* g_phi);
 
