@@ -150,3 +150,27 @@ def test_backward_needs_a_recorded_run(vs):
     sim.close()
     with pytest.raises(vs.VoxsimError):
         vs.Simulator(PHYS, accumulate=vs.ACC_ATOMIC).set_checkpointing(10)
+
+
+@pytest.mark.parametrize("path", [0, 2], ids=["lattice", "streamed"])
+def test_backward_can_be_repeated_on_one_recorded_run(vs, path):
+    """The checkpoints survive a backward pass: a second call on the same forward run with
+    another dL/df gives the scaled gradient."""
+    import torch
+    rng = np.random.default_rng(65)
+    pop = W.population_uniform(3, (4, 3, 3), seed=65)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(PHYS, path=path)
+    sim.set_checkpointing(40)
+    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+    sim.step(200)
+    out = []
+    for scale in (1.0, 3.0):
+        g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+        sim.backward(t(np.full(pop.P, scale)), *g)
+        torch.cuda.synchronize()
+        out.append([a.cpu().numpy() for a in g])
+    sim.close()
+    for g1, g3 in zip(*out):
+        assert np.allclose(g3, 3.0 * g1, rtol=1e-5, atol=1e-9 * max(np.abs(g1).max(), 1e-30))
