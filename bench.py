@@ -59,7 +59,7 @@ def parse():
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
-    ap.add_argument("--case", choices=["streamed", "streamed_adjoint"], default=None,
+    ap.add_argument("--case", choices=["streamed", "streamed_adjoint", "paper_preset", "adjoint"], default=None,
                     help="run one extra measurement alone (for profiling; --robots sets its robots)")
     return ap.parse_args()
 
@@ -295,6 +295,7 @@ def run_ours(args):
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
         rec["streamed_adjoint"] = measure_streamed_adjoint(vs, stream, args, peaks)
+        rec["paper_preset"] = measure_paper_preset(vs, stream, args)
     if rank == 0:
         print(json.dumps(rec))
     sim.close()
@@ -446,6 +447,36 @@ def measure_lamarckian(vs, stream, args, P=512, N=2000, K=100):
             "forward_spring_updates_per_s": float(S.astype(np.int64).sum()) * N / (ms * 1e-3)}
 
 
+def measure_paper_preset(vs, stream, args, N=20000):
+    """The paper's own workload (Table I / Table II): 30 robots on a 5x5x5 grid, time step 1e-5 s
+    with the spring and ground dashpots, then one generation with crossover rate 0.4.  20,000
+    steps (0.2 s of simulated time) per generation; reported as spring updates and as springs +
+    masses per second, next to the paper's 7.89e9 (RTX 3090, unit unstated)."""
+    import torch
+    pop = W.population_uniform(30, (5, 5, 5), seed=11)
+    sim = vs.Simulator(W.PAPER, stream=stream)
+    evo = W.PAPER_EVOLUTION
+    g = torch.from_numpy(W.one_hot_logits(pop.mats).reshape(pop.P, -1).copy()).cuda()
+    out = torch.empty_like(g)
+    fit = torch.empty(pop.P, dtype=torch.float64, device="cuda")
+
+    def generation():
+        sim.set_population(pop.dims, g, vs.MODE_LOGITS)
+        sim.step(N)
+        sim.fitness(fit)
+        sim.evo_generation(fit, g, out, evo, 0)
+    generation()                                      # warm-up
+    ms = _timed(stream, generation)
+    M, S = sim.counts()
+    sim.close()
+    Ssum, Msum = float(S.astype(np.int64).sum()), float(M.astype(np.int64).sum())
+    return {"workload": f"30 robots 5x5x5 (Table I), Table II physics with dashpots, {N} steps of 1e-5 s, "
+                        "one generation (crossover 0.4, elites 0.3, mutation 0.1 / 0.1)",
+            "ms_per_generation": ms, "spring_updates_per_s": Ssum * N / (ms * 1e-3),
+            "spring_plus_mass_updates_per_s": (Ssum + Msum) * N / (ms * 1e-3),
+            "paper_figure": 7892537853, "note": "the paper's figure is on an RTX 3090 with unstated unit and workload"}
+
+
 def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100):
     """The adjoint on large robots (16 robots 40x40x40 at occupancy 0.7, state in HBM): forward
     with checkpoints every 100 steps, then the backward pass (segment replays with recording and
@@ -580,6 +611,12 @@ def run_case(args):
     if args.case == "streamed":
         P = args.robots if args.robots != P_ROBOTS else 64
         print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
+    elif args.case == "paper_preset":
+        print(json.dumps({"case": args.case, **measure_paper_preset(vs, stream, args)}))
+    elif args.case == "adjoint":
+        P = args.robots if args.robots != P_ROBOTS else 512
+        N = args.sim_steps if args.sim_steps != SIM_STEPS else 2000
+        print(json.dumps({"case": args.case, **measure_adjoint(vs, stream, args, P=P, N=N)}))
     else:
         P = args.robots if args.robots != P_ROBOTS else 16
         print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P)}))
