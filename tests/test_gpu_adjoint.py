@@ -172,5 +172,5 @@ def test_backward_can_be_repeated_on_one_recorded_run(vs, path):
         torch.cuda.synchronize()
         out.append([a.cpu().numpy() for a in g])
     sim.close()
-    for g1, g3 in zip(*out):
-        assert np.allclose(g3, 3.0 * g1, rtol=1e-5, atol=1e-9 * max(np.abs(g1).max(), 1e-30))
+    for g1, g3 in zip(*out):       # float32 sums: linear up to rounding, relative to the largest entry
+        assert np.abs(g3 - 3.0 * g1).max() <= 1e-5 * np.abs(g3).max()
