@@ -609,12 +609,17 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     }
     std::vector<int4> items;
     std::vector<int> robots;
+    // robots per block: as many as the slots hold when the population is large, fewer when that
+    // would leave SMs idle (a population of 30 small robots runs on 30 SMs, not 10)
+    size_t n_lattice = 0;
+    for (int k = 0; k < 6; ++k) n_lattice += lattice[k].size() + lattice_sp[k].size();
+    const int spread = (int)std::max<size_t>(1, n_lattice / (size_t)std::max(1, ctx->num_sms));
     for (int variant = 0; variant < 2; ++variant) {
         if (variant == 1) ctx->n_items_corner = (int)items.size();
         for (int k = 5; k >= 0; --k) {
             auto& v = variant == 0 ? lattice[k] : lattice_sp[k];
             std::sort(v.begin(), v.end());
-            const int per = block / kSlot[k];
+            const int per = std::min(block / kSlot[k], spread);
             for (size_t i = 0; i < v.size(); i += per) {
                 const int n = (int)std::min<size_t>(per, v.size() - i);
                 items.push_back(make_int4((int)robots.size(), n, kSlot[k], variant));
