@@ -62,15 +62,15 @@ enum {
     SIM_ACC_AUTO = 0,   /* library choice (measured default) */
     SIM_ACC_ATOMIC = 1, /* per-spring threads add into per-mass accumulators atomically */
     SIM_ACC_GATHER = 2  /* every mass sums its springs' forces in a fixed order (lattice-gather
-                           kernel, or the streamed path for robots too large for it):
-                           bit-reproducible */
+                           kernel, a cluster of lattice blocks for robots of up to 8 x 768
+                           corners in whole layers, or the streamed path): bit-reproducible */
 };
 
 /* Execution path of the time stepping. */
 enum {
     SIM_PATH_AUTO = 0,      /* resident for robots whose masses fit on chip, streamed otherwise */
-    SIM_PATH_RESIDENT = 1,  /* one thread-block group per robot, state in shared memory for all
-                               steps of a call */
+    SIM_PATH_RESIDENT = 1,  /* state in shared memory for all steps of a call: one thread-block
+                               group per robot, or a cluster of blocks for a larger robot */
     SIM_PATH_STREAMED = 2,  /* structure-of-arrays state in device memory, one pass per step */
     SIM_PATH_PLAIN = 3      /* the paper's organisation, kept as a baseline: per robot and step one
                                launch with a thread per spring (atomic force sums in device
@@ -285,14 +285,15 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
 /* Per-size autotuner of the stepping kernels (project-written; the paper has no counterpart).
  * Robots are grouped by grid-corner count into 10 classes (up to 64, 128, 192, 256, 384, 768,
  * 1536, 2560, 5120 corners, and more).  For every class present in the population, each
- * admissible kernel (the lattice-gather kernel in its two variants, the atomic resident kernel
- * at three block sizes, the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
+ * admissible kernel (the lattice-gather kernel in its two variants, the cluster lattice kernel,
+ * the atomic resident kernel at three block sizes, the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
  * the current state (CUDA events), and the fastest is kept for that class.  The state is
  * restored afterwards; the choices persist for later populations of this context.  Modes that
  * require bit-reproducibility (SIM_ACC_GATHER, checkpointing) only consider deterministic
  * kernels.  kind_out / threads_out: int32 [10] host arrays (either may be NULL) receiving per
  * class 0 = lattice (per corner), 1 = atomic resident, 2 = streamed, 3 = lattice
- * (direction-compacted), and the atomic kernel's block size.
+ * (direction-compacted), 4 = cluster of lattice blocks (robots cut into slabs of whole corner
+ * layers, one block each), and the atomic kernel's block size.
  * Synchronises the stream.  Errors: SIM_ESTATE without a population, SIM_EINVAL. */
 sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out);
 

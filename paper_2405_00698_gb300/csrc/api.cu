@@ -114,7 +114,7 @@ int64_t full_springs(int nx, int ny, int nz)
 // Size classes by grid-corner count: the six lattice slot sizes, then larger bands.
 constexpr int kNumClasses = 10;
 constexpr int kClassCorners[kNumClasses] = {64, 128, 192, 256, 384, 768, 1536, 2560, 5120, 1 << 30};
-enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2, kKindLatticeCompact = 3 };
+enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2, kKindLatticeCompact = 3, kKindCluster = 4 };
 
 static int class_of(int corners)
 {
@@ -154,6 +154,11 @@ struct voxsim_ctx {
     // atomic-kernel groups (one persistent launch each): robots of one thread count
     struct AtomicGroup { int threads; int first; int count; int max_corner; int64_t max_spring_cap; };
     std::vector<AtomicGroup> atomic_groups;
+    // cluster lattice groups (one launch each): robots cut into q slabs
+    struct ClusterGroup { int q; int first; int count; };
+    std::vector<ClusterGroup> cluster_groups;
+    int n_cluster = 0;
+    DevBuf<int> d_cluster;
     int n_stream = 0, max_stream_corner = 0;
     std::vector<int> stream_robots;
     DevBuf<int> d_stream;
@@ -519,6 +524,18 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
 // resident kernel while the robot's state fits one SM, then the streamed path.
 static bool is_lattice(int kind) { return kind == kKindLattice || kind == kKindLatticeCompact; }
 
+// CTAs per cluster for a robot on the cluster lattice kernel: the fewest slabs of whole corner
+// layers with at most 768 corners each; 0 when a layer alone is too large or more than 8 slabs
+// would be needed, 1 when the robot fits one block.
+static int cluster_q(int nx, int ny, int nz)
+{
+    const int XY = (nx + 1) * (ny + 1), Z = nz + 1, T = cluster_max_threads();
+    if (XY > T) return 0;
+    const int Lmax = T / XY;
+    const int q = (Z + Lmax - 1) / Lmax;
+    return q <= 8 ? q : 0;
+}
+
 // The lattice variant a size class takes before any tuning: the requested one, else the
 // per-corner kernel (measured faster than the compacted one on every workload tried: uniform,
 // Bernoulli 0.3 to 1.0 and MLP-decoded 8x8x8 grids, uneven populations).
@@ -533,9 +550,11 @@ static void default_choices(voxsim_ctx* ctx)
     for (int k = 0; k < kNumClasses; ++k) {
         const int C = std::min(kClassCorners[k], kResidentMaxCorner);
         const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
-        int kind = k < 6 ? lattice_default(ctx) : (fits ? kKindAtomic : kKindStreamed);
+        // robots of up to 768 corners: one lattice block; up to 5120: a cluster of lattice blocks
+        // (measured faster than the atomic kernel); larger: atomic when it fits, else streamed
+        int kind = k < 6 ? lattice_default(ctx) : (k < 9 ? kKindCluster : (fits ? kKindAtomic : kKindStreamed));
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindStreamed;
-        if (is_lattice(kind) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
+        if ((is_lattice(kind) || kind == kKindCluster) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = fits ? kKindAtomic : kKindStreamed;
         ctx->class_kind[k] = kind;
         ctx->class_threads[k] = 0;
     }
@@ -557,7 +576,8 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     ctx->max_big_spring_cap = 0;
     ctx->atomic_groups.clear();
     if (ctx->p.path == SIM_PATH_PLAIN) {       // every robot on the baseline kernels
-        ctx->n_items = ctx->n_items_corner = ctx->n_big = ctx->n_stream = 0;
+        ctx->n_items = ctx->n_items_corner = ctx->n_big = ctx->n_stream = ctx->n_cluster = 0;
+        ctx->cluster_groups.clear();
         VX_CK(ctx->d_plain_f.ensure(3 * (size_t)ctx->M_cap));
         VX_CK(cudaMemsetAsync(ctx->d_plain_f.p, 0, sizeof(float) * 3 * (size_t)ctx->M_cap, ctx->stream));
         return SIM_OK;
@@ -566,6 +586,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     std::vector<std::vector<std::pair<int, int>>> lattice(6), lattice_sp(6);
     std::vector<std::pair<int, std::pair<int, int>>> atomic;   // (threads, (-corners, robot))
     std::vector<int> streamed;
+    std::vector<std::pair<int, int>> clustered;                  // (q, robot)
     ctx->max_stream_corner = 0;
     const int nrob = subset ? (int)subset->size() : ctx->P;
     for (int ri = 0; ri < nrob; ++ri) {
@@ -574,16 +595,24 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         const int C = (nx + 1) * (ny + 1) * (nz + 1);
         const int k = class_of(C);
         const bool fits_sm = C <= kResidentMaxCorner && resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget;
+        const int q = cluster_q(nx, ny, nz);            // >= 2: the cluster lattice kernel can take it
         int kind = ctx->class_kind[k];
         if (ctx->p.path == SIM_PATH_STREAMED) kind = kKindStreamed;
-        else if (ctx->p.accumulate == SIM_ACC_ATOMIC && is_lattice(kind)) kind = kKindAtomic;
-        else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? lattice_default(ctx) : kKindStreamed;
-        if (is_lattice(kind) && C > block) kind = fits_sm ? kKindAtomic : kKindStreamed;
-        if (kind == kKindAtomic && !fits_sm) kind = kKindStreamed;
-        if (kind == kKindAtomic && ctx->ckpt_every > 0) kind = kKindStreamed;   // deterministic for the adjoint
+        else if (ctx->p.accumulate == SIM_ACC_ATOMIC && (is_lattice(kind) || kind == kKindCluster)) kind = kKindAtomic;
+        else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? lattice_default(ctx) : kKindCluster;
+        // what the robot's size allows
+        if (is_lattice(kind) && C > block) kind = q >= 2 ? kKindCluster : kKindAtomic;
+        if (kind == kKindCluster && q < 2)
+            kind = C <= block ? lattice_default(ctx)
+                              : (fits_sm && ctx->p.accumulate != SIM_ACC_GATHER ? kKindAtomic : kKindStreamed);
+        if (kind == kKindAtomic && !fits_sm) kind = q >= 2 && ctx->p.accumulate != SIM_ACC_ATOMIC ? kKindCluster : kKindStreamed;
+        // the adjoint replays large robots on the streamed path
+        if ((kind == kKindAtomic || kind == kKindCluster) && ctx->ckpt_every > 0) kind = kKindStreamed;
         if (kind == kKindStreamed && ctx->p.path == SIM_PATH_RESIDENT) {
-            if (!fits_sm) return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
-            kind = C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC ? lattice_default(ctx) : kKindAtomic;
+            if (C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC) kind = lattice_default(ctx);
+            else if (q >= 2 && ctx->p.accumulate != SIM_ACC_ATOMIC && ctx->ckpt_every == 0) kind = kKindCluster;
+            else if (fits_sm && ctx->p.accumulate != SIM_ACC_GATHER) kind = kKindAtomic;
+            else return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
         }
         // a requested variant wins over the class choice; the direction-compacted one needs the list
         if (kind == kKindLattice && ctx->p.lattice == SIM_LATTICE_COMPACT) kind = kKindLatticeCompact;
@@ -594,6 +623,8 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
             int slot = 0;
             while (kSlot[slot] < C) ++slot;
             (kind == kKindLattice ? lattice : lattice_sp)[slot].push_back({-C, r});
+        } else if (kind == kKindCluster) {
+            clustered.push_back({cluster_q(nx, ny, nz), r});
         } else if (kind == kKindAtomic) {
             int threads = ctx->class_threads[k] > 0 ? ctx->class_threads[k] : ctx->p.threads;
             if (threads <= 0) {
@@ -642,6 +673,16 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         ctx->max_big_spring_cap = std::max(ctx->max_big_spring_cap, g.max_spring_cap);
         ctx->atomic_groups.push_back(g);
     }
+    std::sort(clustered.begin(), clustered.end());
+    std::vector<int> cl_robots;
+    ctx->cluster_groups.clear();
+    for (size_t i = 0; i < clustered.size();) {
+        voxsim_ctx::ClusterGroup g{clustered[i].first, (int)cl_robots.size(), 0};
+        for (; i < clustered.size() && clustered[i].first == g.q; ++i) cl_robots.push_back(clustered[i].second);
+        g.count = (int)cl_robots.size() - g.first;
+        ctx->cluster_groups.push_back(g);
+    }
+    ctx->n_cluster = (int)cl_robots.size();
     ctx->n_items = (int)items.size();
     ctx->n_big = (int)big.size();
     ctx->n_stream = (int)streamed.size();
@@ -667,6 +708,10 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     }
     if (!big.empty())
         VX_CK(cudaMemcpyAsync(ctx->d_big.p, big.data(), sizeof(int) * big.size(), cudaMemcpyHostToDevice, s));
+    VX_CK(ctx->d_cluster.ensure(cl_robots.size()));
+    if (!cl_robots.empty())
+        VX_CK(cudaMemcpyAsync(ctx->d_cluster.p, cl_robots.data(), sizeof(int) * cl_robots.size(),
+                              cudaMemcpyHostToDevice, s));
     // the host vectors are copied from pageable memory: wait so they may go out of scope
     VX_CK(cudaStreamSynchronize(s));
     ctx->drop_graph();
@@ -725,6 +770,28 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
         a.queue = ctx->d_queue.p + 1;
         a.spack = ctx->d_spack.p;
         VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_spring, ctx->num_sms), threads, smem, ctx->stream));
+    }
+    return SIM_OK;
+}
+
+// The cluster lattice kernel: one launch per cluster size, one cluster per robot.
+static sim_status step_cluster(voxsim_ctx* ctx, int n)
+{
+    if (ctx->n_cluster == 0) return SIM_OK;
+    ClusterArgs a{};
+    a.pv = ctx->view();
+    a.cflags = ctx->d_cflags.p;
+    a.prm = ctx->d_prm.p;
+    a.u = ctx->d_x.p;
+    a.v = ctx->d_v.p;
+    a.sc = ctx->d_sc.p;
+    a.nsteps = n;
+    a.c = ctx->stepconst();
+    const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)cluster_max_threads();
+    for (const auto& g : ctx->cluster_groups) {
+        a.robots = ctx->d_cluster.p + g.first;
+        a.q = g.q;
+        VX_LAUNCH(ctx, launch_step_cluster(a, g.count, smem, ctx->stream));
     }
     return SIM_OK;
 }
@@ -880,6 +947,7 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
         if (sim_status st = step_plain(ctx, n_steps)) return st;
     } else {
         if (sim_status st = step_lattice(ctx, n_steps)) return st;
+        if (sim_status st = step_cluster(ctx, n_steps)) return st;
         if (sim_status st = step_resident(ctx, n_steps)) return st;
         if (sim_status st = step_streamed(ctx, n_steps)) return st;
     }
@@ -1242,6 +1310,9 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
             const int t3[3] = {k < 6 ? 128 : 256, k < 6 ? 256 : 512, k < 6 ? 512 : 1024};
             for (int t : t3) cands.push_back({kKindAtomic, t});
         }
+        if (k >= 6 && ctx->p.path != SIM_PATH_STREAMED && cluster_q(ctx->dims[3 * sample[0]], ctx->dims[3 * sample[0] + 1],
+                                                                   ctx->dims[3 * sample[0] + 2]) >= 2)
+            cands.push_back({kKindCluster, 0});
         if (k >= 6 && ctx->p.path != SIM_PATH_RESIDENT) cands.push_back({kKindStreamed, 0});
         if (cands.size() < 2) continue;
         float best_ms = 1e30f;
@@ -1260,6 +1331,7 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
                 }
                 VX_CK(cudaEventRecord(e0, s));
                 if ((result = step_lattice(ctx, n_steps)) != SIM_OK) break;
+                if ((result = step_cluster(ctx, n_steps)) != SIM_OK) break;
                 if ((result = step_resident(ctx, n_steps)) != SIM_OK) break;
                 if ((result = step_streamed(ctx, n_steps)) != SIM_OK) break;
                 VX_CK(cudaEventRecord(e1, s));

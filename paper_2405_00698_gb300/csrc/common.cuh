@@ -219,6 +219,23 @@ cudaError_t launch_stream_adj_init(const StreamAdjArgs& a, int max_corners, cuda
 cudaError_t launch_stream_adj_step(const StreamAdjArgs& a, int max_corners, cudaStream_t s);
 cudaError_t launch_stream_adj_voxels(const StreamAdjArgs& a, int max_corners, cudaStream_t s);
 
+// Cluster lattice path (robots cut into q <= 8 slabs of <= 768 corners, one CTA each, slabs
+// exchanging boundary positions and forces through distributed shared memory).
+struct ClusterArgs {
+    PopView pv;
+    const uint32_t* cflags;
+    const float* prm;        // per robot at 39 * moff: [3][13][C]
+    float4* u;               // per corner displacement (rest height in .w)
+    float4* v;
+    const float2* sc;        // sin / cos of w t per step of this call
+    int nsteps;
+    StepConst c;
+    const int* robots;       // robots of this launch, one cluster each
+    int q;                   // CTAs per cluster
+};
+int cluster_max_threads();
+cudaError_t launch_step_cluster(const ClusterArgs& a, int n_robots, size_t smem, cudaStream_t s);
+
 // The paper's organisation (baseline): one launch per robot per pass, two passes per step.
 cudaError_t launch_step_plain_robot(const int2* ab, const float4* prm, const int* mass_corner, float4* u,
                                     float4* v, float* F, int S, int M, int nx, int ny, const float2* sc, int n,

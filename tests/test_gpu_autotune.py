@@ -30,7 +30,7 @@ def test_autotune_preserves_state_and_parity(vs, orc):
     kind, threads = sim.autotune(20)
     x_after, v_after, _ = sim.state()
     assert np.array_equal(x_before, x_after) and np.array_equal(v_before, v_after)
-    assert set(kind.tolist()) <= {0, 1, 2, 3}
+    assert set(kind.tolist()) <= {0, 1, 2, 3, 4}
     sim.step(300)
     x, _, off = sim.state()
     f = sim.fitness()

@@ -223,9 +223,9 @@ def test_atomic_path_matches_oracle(vs, orc):
     check_population(orc, pop, PHYS, 500, g["f"], g["x"], g["off"], ref)
 
 
-def test_gather_mode_routes_large_robots_to_the_deterministic_streamed_path(vs):
-    """Under bit-reproducible stepping a robot larger than a lattice block runs streamed (the
-    same fixed summation order), and two runs agree bitwise."""
+def test_gather_mode_keeps_large_robots_deterministic(vs):
+    """Under bit-reproducible stepping a robot larger than a lattice block runs on a kernel with
+    the same fixed summation order (a cluster of lattice blocks), and two runs agree bitwise."""
     pop = W.population_uneven(3, seed=26, sizes=(12,))
     out = []
     for _ in range(2):
