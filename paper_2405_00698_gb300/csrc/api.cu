@@ -550,11 +550,13 @@ static void default_choices(voxsim_ctx* ctx)
     for (int k = 0; k < kNumClasses; ++k) {
         const int C = std::min(kClassCorners[k], kResidentMaxCorner);
         const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
-        // robots of up to 768 corners: one lattice block; up to 5120: a cluster of lattice blocks
-        // (measured faster than the atomic kernel); larger: atomic when it fits, else streamed
-        int kind = k < 6 ? lattice_default(ctx) : (k < 9 ? kKindCluster : (fits ? kKindAtomic : kKindStreamed));
-        if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindStreamed;
-        if ((is_lattice(kind) || kind == kKindCluster) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = fits ? kKindAtomic : kKindStreamed;
+        // robots of up to 768 corners: one lattice block; larger: the atomic kernel when it fits
+        // (measured ahead of the cluster of lattice blocks, 47 against 63 ms on the uneven
+        // population's large robots), else streamed.  Bit-reproducible stepping takes the
+        // cluster of lattice blocks (ahead of the streamed path: 63 against 80 ms).
+        int kind = k < 6 ? lattice_default(ctx) : (fits ? kKindAtomic : kKindStreamed);
+        if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindCluster;
+        if (is_lattice(kind) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
         ctx->class_kind[k] = kind;
         ctx->class_threads[k] = 0;
     }

@@ -1,7 +1,8 @@
 """The cluster lattice kernel (robots of more than 768 corners cut into 2..8 slabs of whole
-corner layers, one CTA each, boundary positions and forces through distributed shared memory).
-Same arithmetic and summation order as the streamed path, so the two must agree bit for bit;
-and the FP64 oracle within the stated tolerances."""
+corner layers, one CTA each, boundary positions and forces through distributed shared memory),
+the bit-reproducible choice for such robots.  Same arithmetic and summation order as the
+streamed path, so the two must agree bit for bit; and the FP64 oracle within the stated
+tolerances."""
 import numpy as np
 import pytest
 
@@ -55,7 +56,8 @@ def test_cluster_matches_oracle(vs, orc):
     rng = np.random.default_rng(101)
     dims = [(8, 8, 12), (12, 12, 12), (6, 6, 40)]
     pop = W.make_population(dims, [W.bernoulli_grid(rng, d, 0.7) for d in dims])
-    x, v, f, off, _ = run(vs, pop, PHYS, 500)
+    x, v, f, off, launches = run(vs, pop, PHYS, 500, accumulate=vs.ACC_GATHER)
+    assert launches < 20                  # clusters, not the streamed path's launch per step
     ref = orc.run_population(pop, PHYS, 500, want_x=True)
     check_population(orc, pop, PHYS, 500, f, x, off, ref)
 
@@ -65,6 +67,6 @@ def test_cluster_in_a_mixed_population(vs, orc):
     rng = np.random.default_rng(102)
     dims = [(4, 4, 4), (8, 8, 12), (3, 5, 2), (12, 12, 12), (30, 30, 10)]
     pop = W.make_population(dims, [W.bernoulli_grid(rng, d, 0.75) for d in dims])
-    x, v, f, off, _ = run(vs, pop, PHYS, 250)
+    x, v, f, off, _ = run(vs, pop, PHYS, 250, accumulate=vs.ACC_GATHER)
     ref = orc.run_population(pop, PHYS, 250, want_x=True)
     check_population(orc, pop, PHYS, 250, f, x, off, ref)
