@@ -73,8 +73,8 @@ def test_mlp_population_full_size(vs, orc):
     check_population(orc, pop, PHYS, 1000, f1[pick], x1s, offs, ref1, w=w, kappa=kappa, phi=phi)
     ref = orc.run_population(pop, PHYS, N, w=w, kappa=kappa, phi=phi, want_x=True)
     xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
-    check_population(orc, pop, PHYS, N, f[pick], xs, offs, ref, w=w, kappa=kappa, phi=phi, K=6,
-                     max_sensitive_frac=1.0, perturb=1e-7)
+    check_population(orc, pop, PHYS, N, f[pick], xs, offs, ref, w=w, kappa=kappa, phi=phi, K=8,
+                     max_sensitive_frac=1.0, perturb=1e-7, envelope=2.0)
 
 
 def test_uneven_population_full_size(vs, orc):
@@ -100,7 +100,8 @@ def test_uneven_population_full_size(vs, orc):
     check_population(orc, sub, PHYS, 1000, f1[pick], x1s, offs, ref1)
     ref = orc.run_population(sub, PHYS, N, want_x=True)
     xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
-    check_population(orc, sub, PHYS, N, f[pick], xs, offs, ref, K=6, max_sensitive_frac=1.0, perturb=1e-7)
+    check_population(orc, sub, PHYS, N, f[pick], xs, offs, ref, K=8, max_sensitive_frac=1.0, perturb=1e-7,
+                     envelope=2.0)
 
 
 def test_large_robots_full_size_sample(vs, orc):
