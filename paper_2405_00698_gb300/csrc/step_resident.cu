@@ -5,7 +5,7 @@
 //                       rest height z0 (corners without a mass are carried along unchanged)
 //   v       float4[C]   velocity
 //   F       float[3][C] accumulated by the spring phase, consumed and cleared by the mass phase
-//   springs float4[S]   when they fit, otherwise streamed from device memory (L2) every step:
+//   springs float4[S]   as many as fit, the rest read from device memory (L2) every step:
 //                       (k, alpha L0, beta L0, a | b << 14 | direction << 28), ordered by
 //                       direction then a, so a warp's atomic updates hit distinct masses.
 // Keeping the displacement instead of the position keeps float32 precise: a spring vector is
@@ -26,6 +26,7 @@ struct SmemLayout {
     float* fx;
     float* fy;
     float* fz;
+    uint32_t* massbits;
 };
 
 __device__ __forceinline__ SmemLayout carve(void* base, int max_mass, int max_spring_smem)
@@ -37,7 +38,8 @@ __device__ __forceinline__ SmemLayout carve(void* base, int max_mass, int max_sp
     L.spr = (float4*)p; p += sizeof(float4) * max_spring_smem;
     L.fx = (float*)p; p += sizeof(float) * max_mass;
     L.fy = (float*)p; p += sizeof(float) * max_mass;
-    L.fz = (float*)p;
+    L.fz = (float*)p; p += sizeof(float) * max_mass;
+    L.massbits = (uint32_t*)p;
     return L;
 }
 
@@ -74,15 +76,23 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             L.vel[m] = a.v[mo + m];
             L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
         }
-        const bool spr_in_smem = S <= a.max_spring_smem;
-        const float4* spr = spr_in_smem ? L.spr : a.spr_pack + so;
-        if (spr_in_smem)
-            for (int s = tid; s < S; s += T) L.spr[s] = a.spr_pack[so + s];
+        // as many springs as fit stay in shared memory (the first ones of the direction-major
+        // list); the rest are read from device memory (L2) every step
+        const int nsm = min(S, a.max_spring_smem);
+        const float4* __restrict__ spr_g = a.spr_pack + so;
+        for (int s = tid; s < nsm; s += T) L.spr[s] = spr_g[s];
+        // which corners carry a mass, one bit each
+        for (int w = tid; w < (M + 31) / 32; w += T) {
+            uint32_t bits = 0u;
+            for (int b = 0; b < 32 && 32 * w + b < M; ++b)
+                bits |= (a.cflags[mo + 32 * w + b] >> 31) << b;
+            L.massbits[w] = bits;
+        }
         __syncthreads();
         for (int n = 0; n < a.nsteps; ++n) {
             const float2 sc = a.sc[n];
             for (int s = tid; s < S; s += T) {
-                const float4 q = spr[s];
+                const float4 q = s < nsm ? L.spr[s] : spr_g[s];
                 const unsigned bits = __float_as_uint(q.w);
                 const int ia = bits & 0x3fffu, ib = (bits >> 14) & 0x3fffu, dir = bits >> 28;
                 const float4 ua = L.u[ia], ub = L.u[ib], d0 = sh_d0[dir];
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             }
             __syncthreads();
             for (int m = tid; m < M; m += T) {
-                if (!(a.cflags[mo + m] >> 31)) continue;   // a corner without a mass
+                if (!((L.massbits[m >> 5] >> (m & 31)) & 1u)) continue;   // a corner without a mass
                 float fx = L.fx[m], fy = L.fy[m], fz = L.fz[m] - c.weight;
                 L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
                 float4 u = L.u[m], v = L.vel[m];
@@ -146,7 +156,7 @@ size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate)
 {
     (void)accumulate;
     return sizeof(float4) * 2 * (size_t)max_mass + sizeof(float4) * (size_t)max_spring_smem +
-           sizeof(float) * 3 * (size_t)max_mass;
+           sizeof(float) * 3 * (size_t)max_mass + sizeof(uint32_t) * (((size_t)max_mass + 31) / 32);
 }
 
 cudaError_t launch_step_resident(const ResidentArgs& a, int grid, int threads, size_t smem,
