@@ -134,6 +134,7 @@ struct voxsim_ctx {
     bool have_pop = false;
     std::vector<int> dims;
     std::vector<int64_t> voff, moff, soff;
+    std::vector<int> mass_count;   // masses per robot of the current population (host copy)
     int64_t V_tot = 0, M_cap = 0, S_cap = 0;
     int max_corner = 0;
     int64_t max_spring_cap = 0;
@@ -511,6 +512,10 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         k_spring_keys<<<(P + 255) / 256, 256, 0, s>>>(ctx->d_ns.p, P, ctx->d_keys.p);
         VX_LAUNCH(ctx, cudaGetLastError());
         VX_LAUNCH(ctx, launch_evo_rank(ctx->d_keys.p, P, ctx->d_lpt.p, s));
+        // the mass counts order the work queue (longest first); the plan is built on the host
+        ctx->mass_count.assign(P, 0);
+        VX_CK(cudaMemcpyAsync(ctx->mass_count.data(), ctx->d_nm.p, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        VX_CK(cudaStreamSynchronize(s));
         if (sim_status st = build_work_items(ctx)) return st;
     }
     ctx->step = 0;
@@ -624,7 +629,9 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         if (is_lattice(kind)) {
             int slot = 0;
             while (kSlot[slot] < C) ++slot;
-            (kind == kKindLattice ? lattice : lattice_sp)[slot].push_back({-C, r});
+            // longest first: by mass count when known (the step's cost follows the masses), else corners
+            const int key = (int)ctx->mass_count.size() == ctx->P ? ctx->mass_count[r] : C;
+            (kind == kKindLattice ? lattice : lattice_sp)[slot].push_back({-key, r});
         } else if (kind == kKindCluster) {
             clustered.push_back({cluster_q(nx, ny, nz), r});
         } else if (kind == kKindAtomic) {
