@@ -134,7 +134,8 @@ struct voxsim_ctx {
     bool have_pop = false;
     std::vector<int> dims;
     std::vector<int64_t> voff, moff, soff;
-    std::vector<int> mass_count;   // masses per robot of the current population (host copy)
+    std::vector<int> mass_count;   // masses and springs per robot of the current population (host copies)
+    std::vector<int> spring_count;
     int64_t V_tot = 0, M_cap = 0, S_cap = 0;
     int max_corner = 0;
     int64_t max_spring_cap = 0;
@@ -514,7 +515,9 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         VX_LAUNCH(ctx, launch_evo_rank(ctx->d_keys.p, P, ctx->d_lpt.p, s));
         // the mass counts order the work queue (longest first); the plan is built on the host
         ctx->mass_count.assign(P, 0);
+        ctx->spring_count.assign(P, 0);
         VX_CK(cudaMemcpyAsync(ctx->mass_count.data(), ctx->d_nm.p, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        VX_CK(cudaMemcpyAsync(ctx->spring_count.data(), ctx->d_ns.p, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
         VX_CK(cudaStreamSynchronize(s));
         if (sim_status st = build_work_items(ctx)) return st;
     }
@@ -641,7 +644,9 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
                 threads = sc <= 1536 ? 256 : (sc <= 6144 ? 512 : 1024);
             }
             threads = std::max(32, std::min(1024, (threads + 31) / 32 * 32));
-            atomic.push_back({threads, {-C, r}});
+            // longest first: by spring count when known (a thread per spring), else corners
+            const int key = (int)ctx->spring_count.size() == ctx->P ? ctx->spring_count[r] : C;
+            atomic.push_back({threads, {-key, r}});
         } else {
             streamed.push_back(r);
             ctx->max_stream_corner = std::max(ctx->max_stream_corner, C);
@@ -674,7 +679,8 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         for (; i < atomic.size() && atomic[i].first == g.threads; ++i) {
             const int r = atomic[i].second.second;
             big.push_back(r);
-            g.max_corner = std::max(g.max_corner, -atomic[i].second.first);
+            g.max_corner = std::max(g.max_corner, (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) *
+                                                      (ctx->dims[3 * r + 2] + 1));
             g.max_spring_cap = std::max(g.max_spring_cap, full_springs(ctx->dims[3 * r], ctx->dims[3 * r + 1], ctx->dims[3 * r + 2]));
         }
         g.count = (int)big.size() - g.first;
