@@ -7,10 +7,12 @@
 // -> (. W3^T + b3) [Q x 6]; material = argmax of outputs 0..4 (softmax is monotone; ties to the
 // lowest id), weight = sigmoid(output 5).
 //
-// One CTA (4 warps) per genome at a time, persistent over genomes.  Operands are bfloat16 in
-// shared memory in the 128-byte-swizzled K-major layout the tensor core reads directly:
-//   * gamma tiles of 128 queries arrive by TMA (double-buffered, the next tile prefetched while
-//     the current one is multiplied);
+// One CTA (4 warps) per genome at a time, persistent over genomes, two CTAs per SM (one CTA's
+// weight conversion and epilogues overlap the other's tensor work; measured 1.6x over one CTA
+// per SM with a double-buffered gamma tile).  Operands are bfloat16 in shared memory in the
+// 128-byte-swizzled K-major layout the tensor core reads directly:
+//   * gamma tiles of 128 queries arrive by TMA into one buffer, which after layer 1 holds the
+//     hidden activations (so a CTA needs 107 KB of shared memory);
 //   * W1, W2, W3 are converted from the float32 genome by the CTA's threads into the same
 //     layout (W3 padded to 16 rows);
 //   * the three layers are tcgen05.mma kind::f16 (M = 128; N = 64, 64, 16) accumulating in
@@ -38,15 +40,13 @@ constexpr int kW1Bytes = kHidden * kPeDim * 2;               // 32 KB
 constexpr int kW2Bytes = kHidden * kHidden * 2;              // 8 KB
 constexpr int kW3Rows = 16;
 constexpr int kW3Bytes = kW3Rows * kHidden * 2;              // 2 KB
-constexpr int kHBytes = kTileM * kHidden * 2;                // 16 KB
 constexpr int kTmemCols = 256;
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 struct __align__(1024) Smem {
-    unsigned char a[2][kABytes];
+    unsigned char a[1][kABytes];          // gamma tile; after layer 1 also the hidden activations
     unsigned char w1[kW1Bytes];
     unsigned char w2[kW2Bytes];
-    unsigned char h[kHBytes];
     unsigned char w3[kW3Bytes];
     float b1[kHidden];
     float b2[kHidden];
@@ -227,7 +227,7 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bia
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* __restrict__ genomes,
          MatConst mc, uint8_t* __restrict__ mat, float* __restrict__ w_out, float* __restrict__ kappa,
          float* __restrict__ phi, int* status)
@@ -255,7 +255,6 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
     const uint32_t lane_sel = (uint32_t)(warp * 32) << 16;    // this warp's TMEM lane quarter
     const int ntiles = (Q + kTileM - 1) / kTileM;
     uint32_t tma_phase[2] = {0, 0}, mma_phase = 0;
-    int buf = 0;
     constexpr uint32_t id_h = idesc_bf16(kTileM, kHidden);
     constexpr uint32_t id_o = idesc_bf16(kTileM, kW3Rows);
 
@@ -271,18 +270,12 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
         if (tid < kW3Rows) s.b3[tid] = tid < kOut ? G[kOffB3 + tid] : 0.f;
         proxy_fence();
         __syncthreads();
-        if (tid == 0 && !s.abort) {
-            mbar_expect_tx(&s.tma_bar[buf], kABytes);
-            for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
-                tma_load_2d(s.a[buf] + kb * kTileM * 128, &pe_map, &s.tma_bar[buf], kb * kKBlock, 0);
-        }
         for (int t = 0; t < ntiles; ++t) {
-            const int cur = buf;
-            if (tid == 0 && t + 1 < ntiles && !s.abort) {   // prefetch the next gamma tile
-                mbar_expect_tx(&s.tma_bar[cur ^ 1], kABytes);
+            const int cur = 0;
+            if (tid == 0 && !s.abort) {                     // this tile's gamma rows
+                mbar_expect_tx(&s.tma_bar[0], kABytes);
                 for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
-                    tma_load_2d(s.a[cur ^ 1] + kb * kTileM * 128, &pe_map, &s.tma_bar[cur ^ 1],
-                                kb * kKBlock, (t + 1) * kTileM);
+                    tma_load_2d(s.a[0] + kb * kTileM * 128, &pe_map, &s.tma_bar[0], kb * kKBlock, t * kTileM);
             }
             // layer 1: D1 = gamma_tile . W1^T  (K = 256: 4 swizzle blocks x 4 steps of 16)
             if (tid == 0) {
@@ -299,20 +292,19 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                 }
             }
             tma_phase[cur] ^= 1;
-            buf ^= 1;
             const int row = warp * 32 + lane;
             // epilogue 1 -> H
             mbar_wait(&s.mma_bar, mma_phase, s, status);
             mma_phase ^= 1;
             tc_fence_after();
-            if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, s.h, row);
+            if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, s.a[0], row);
             proxy_fence();
             tc_fence_before();
             __syncthreads();
             // layer 2: D2 = H . W2^T
             if (tid == 0 && !s.abort) {
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(s.h), b0 = smem_u32(s.w2);
+                const uint32_t a0 = smem_u32(s.a[0]), b0 = smem_u32(s.w2);
 #pragma unroll
                 for (int k = 0; k < kHidden / 16; ++k)
                     umma(t_d2, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_h, k > 0);
@@ -321,14 +313,14 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
             mbar_wait(&s.mma_bar, mma_phase, s, status);
             mma_phase ^= 1;
             tc_fence_after();
-            if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, s.h, row);
+            if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, s.a[0], row);
             proxy_fence();
             tc_fence_before();
             __syncthreads();
             // layer 3: D3 = H . W3^T (N = 16, rows 6..15 of W3 are zero)
             if (tid == 0 && !s.abort) {
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(s.h), b0 = smem_u32(s.w3);
+                const uint32_t a0 = smem_u32(s.a[0]), b0 = smem_u32(s.w3);
 #pragma unroll
                 for (int k = 0; k < kHidden / 16; ++k)
                     umma(t_d3, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_o, k > 0);
@@ -405,7 +397,7 @@ cudaError_t launch_mlp_query(int P, int Q, const void* pe_bf16, const float* gen
     const size_t smem = mlp_tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = P < num_sms ? P : num_sms;
+    const int grid = P < 2 * num_sms ? P : 2 * num_sms;
     k_mlp_tc<<<grid, kThreads, smem, s>>>(map, P, Q, genomes, mc, mat, w, kappa, phi, status);
     return cudaGetLastError();
 }
