@@ -148,3 +148,67 @@ def test_adjoint_full_size_sample(vs, orc):
         if max(errs) > 1e-3:
             bad.append((r, errs))
     assert len(bad) <= 1, bad
+
+
+def _fd_pair(args):
+    """FP64 oracle fitness at theta +- h for one parameter (run in a worker process)."""
+    from oracle import oracle as orc_mod
+    grid, dims, n, base, name, v, h = args
+    ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
+    am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
+    fp, hp = orc_mod.fitness_after(grid, dims, PHYS, n, **ap)
+    fm, hm = orc_mod.fitness_after(grid, dims, PHYS, n, **am)
+    return fp, fm, hp == hm
+
+
+def test_adjoint_full_size_finite_differences(vs, orc):
+    """The gradient at full size (512 robots 8x8x8, 2000 steps, checkpoints every 100) against
+    FP64 central finite differences (h = 1e-6) of the oracle on 32 random parameters of each of
+    two sampled robots; parameter pairs whose +h and -h runs take different contact-mode
+    sequences are not differentiable there and are skipped (and counted)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import torch
+    rng = np.random.default_rng(3)
+    P, N, K = 512, 2000, 100
+    pop = W.population_uniform(P, (8, 8, 8), seed=3)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(PHYS)
+    sim.set_checkpointing(K)
+    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+    sim.step(N)
+    _, S = sim.counts()
+    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+    sim.backward(t(np.ones(P)), *g)
+    torch.cuda.synchronize()
+    g = dict(zip(("w", "kappa", "phi"), (a.cpu().numpy() for a in g)))
+    sim.close()
+    pick_rng = np.random.default_rng(44)
+    jobs, meta = [], []
+    for r in W.stratified_subset(S, 2):
+        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+        kept = np.flatnonzero(orc.lcc(pop.grid(r), (8, 8, 8)) > 0)
+        base = {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
+                "phi": phi[a:b].astype(np.float64)}
+        for _ in range(32):
+            name = ("w", "kappa", "phi")[pick_rng.integers(3)]
+            v = int(pick_rng.choice(kept))
+            h = 1e-6 * max(1.0, abs(base[name][v]))
+            jobs.append((pop.grid(r), (8, 8, 8), N, base, name, v, h))
+            meta.append((r, a, name, v, h))
+    with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_fd_pair, jobs))
+    checked, failed, skipped = 0, [], 0
+    for (r, a, name, v, h), (fp, fm, same) in zip(meta, res):
+        if not same:
+            skipped += 1
+            continue
+        fd = (fp - fm) / (2 * h)
+        gr = g[name][a:a + 512]
+        scale = max(abs(fd), 1e-3 * np.abs(gr).max())
+        checked += 1
+        if abs(gr[v] - fd) > 1e-3 * scale:
+            failed.append((r, name, v, float(gr[v]), fd))
+    assert checked >= 16, (checked, skipped)
+    assert len(failed) <= max(1, checked // 20), failed
