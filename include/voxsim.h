@@ -272,6 +272,14 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
                         float* g_phi);
 
+/* Contact mode of every corner of robot `robot` at every step of the most recent recorded
+ * sim_step_n call (checkpointing on): out[n * C + c] for step n and grid corner c of the robot's
+ * C corners, 0 = free (or no mass at that corner), 1 = stuck, 2 = slipping (Section II-C,
+ * Table II: ground contact with static and kinetic friction).  The checkpoint segments are
+ * replayed bit-identically to read them.  out: host uint8 [n_steps][C].  Synchronises the
+ * stream.  Errors: SIM_ESTATE without a recorded run, SIM_EINVAL. */
+sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out);
+
 /* Population diversity (Fig. 3(b) plots a "diversity curve" without defining it; these are the
  * definitions used here), FP64 on the GPU:
  *   out[0] genome diversity: root mean square of the pairwise Euclidean distances between the P

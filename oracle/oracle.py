@@ -89,6 +89,8 @@ def lib():
             L.orc_evo_generation.restype = i32
             L.orc_fitness_after.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, i32, vp]
             L.orc_fitness_after.restype = d
+            L.orc_fitness_after_modes.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+            L.orc_fitness_after_modes.restype = d
             L.orc_robot_adjoint.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, i32, d, vp, vp, vp, vp]
             L.orc_robot_adjoint.restype = d
             L.orc_genome_diversity.argtypes = [i32, i32, vp]; L.orc_genome_diversity.restype = d
@@ -264,6 +266,27 @@ def fitness_after(mat, dims, phys, nsteps, w=None, kappa=None, phi=None, apply_l
     f = lib().orc_fitness_after(nx, ny, nz, _p(m), _p(w), _p(kappa), _p(phi), C.byref(params),
                                 int(bool(apply_lcc)), int(nsteps), C.byref(h))
     return f, h.value
+
+
+def fitness_after_modes(mat, dims, phys, nsteps, w=None, kappa=None, phi=None, apply_lcc=True,
+                        force=None):
+    """(fitness, modes uint8 [nsteps, M] in mass order, contact-mode hash) of a fresh robot after
+    nsteps; with `force` ([nsteps, M] uint8) the contact modes are imposed instead of decided."""
+    m, nx, ny, nz = _grid(mat, dims)
+    V = m.size
+    w, kappa, phi = _f64(w, V), _f64(kappa, V), _f64(phi, V)
+    R = Robot(mat, dims, phys, w=w, kappa=kappa, phi=phi, apply_lcc=apply_lcc)
+    M = R.M
+    del R
+    out = np.zeros((max(nsteps, 1), max(M, 1)), np.uint8)
+    fm = None
+    if force is not None:
+        fm = np.ascontiguousarray(np.asarray(force, dtype=np.uint8).reshape(nsteps, M))
+    h = C.c_uint64()
+    params = OrcParams.of(phys)
+    f = lib().orc_fitness_after_modes(nx, ny, nz, _p(m), _p(w), _p(kappa), _p(phi), C.byref(params),
+                                      int(bool(apply_lcc)), int(nsteps), _p(fm), _p(out), C.byref(h))
+    return f, out[:nsteps, :M], h.value
 
 
 def adjoint(mat, dims, phys, nsteps, dL_df=1.0, w=None, kappa=None, phi=None, apply_lcc=True,

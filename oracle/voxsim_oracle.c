@@ -503,8 +503,14 @@ enum { ORC_FREE = 0, ORC_STICK = 1, ORC_SLIP = 2 };
  *     mu_k F_n is removed along F_h;
  *  4. semi-implicit Euler with velocity damping: v <- c (v + dt F / m), x <- x + dt v.
  * modes (optional, M entries) records the contact mode of every mass and Fpre (optional, 3M)
- * the force before the contact step.  Returns the number of springs skipped for zero length. */
-static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes, double* Fpre)
+ * the force before the contact step.  force (optional, M entries) imposes the contact mode of
+ * every mass instead of deciding it from the state: free adds no ground force; stick and slip
+ * add F_n = k_ground (-z) whatever the sign of z and then zero the horizontal force and velocity
+ * (stick) or remove mu_k F_n along F_h (slip) -- the same piecewise formulas, selected from
+ * outside (used to difference the step map along another run's contact decisions).  Returns the
+ * number of springs skipped for zero length. */
+static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes, double* Fpre,
+                    const uint8_t* force)
 {
     const double t = (double)R->step * p->dt;
     const double wt = 2.0 * M_PI * p->freq * t;
@@ -534,13 +540,14 @@ static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes
     for (int m = 0; m < M; ++m) {
         double* x = R->x + 3 * m; double* v = R->v + 3 * m; double* f = F + 3 * m;
         uint8_t mode = ORC_FREE;
-        if (p->ground_on && x[2] < 0.0) {
+        const int contact = force ? force[m] != ORC_FREE : (p->ground_on && x[2] < 0.0);
+        if (contact) {
             double fn = p->k_ground * (-x[2]);
             f[2] += fn;
             /* ground dashpot on the normal velocity: c_g = 2 zeta sqrt(k_g m) */
             if (p->ground_zeta > 0.0) f[2] -= 2.0 * p->ground_zeta * sqrt(p->k_ground * p->mass) * v[2];
             double fh = sqrt(f[0] * f[0] + f[1] * f[1]);
-            if (fh <= p->mu_s * fn) {
+            if (force ? force[m] == ORC_STICK : fh <= p->mu_s * fn) {
                 mode = ORC_STICK;
                 f[0] = 0.0; f[1] = 0.0; v[0] = 0.0; v[1] = 0.0;
             } else {
@@ -564,7 +571,7 @@ int orc_robot_simulate(orc_robot* R, const orc_params* p, int nsteps)
 {
     double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(R->M > 0 ? R->M : 1));
     int skipped = 0;
-    for (int n = 0; n < nsteps; ++n) skipped += orc_step(R, p, F, NULL, NULL);
+    for (int n = 0; n < nsteps; ++n) skipped += orc_step(R, p, F, NULL, NULL, NULL);
     free(F);
     return skipped;
 }
@@ -737,16 +744,33 @@ int orc_evo_generation(int P, int G, const double* fitness, const float* genomes
 /* Fitness of a freshly built robot after nsteps, plus a hash of its contact-mode sequence, so a
  * finite-difference sample whose +h and -h runs took different contact modes can be discarded.
  * Parameters as for orc_robot_new. */
+double orc_fitness_after_modes(int nx, int ny, int nz, const uint8_t* mat, const double* w,
+                               const double* kappa, const double* phi, const orc_params* p,
+                               int apply_lcc, int nsteps, const uint8_t* force, uint8_t* modes_out,
+                               uint64_t* mode_hash);
+
 double orc_fitness_after(int nx, int ny, int nz, const uint8_t* mat, const double* w,
                          const double* kappa, const double* phi, const orc_params* p,
                          int apply_lcc, int nsteps, uint64_t* mode_hash)
+{
+    return orc_fitness_after_modes(nx, ny, nz, mat, w, kappa, phi, p, apply_lcc, nsteps, NULL, NULL,
+                                   mode_hash);
+}
+
+/* orc_fitness_after with the contact modes of every step recorded (modes_out, nsteps x M in mass
+ * order, optional) or imposed (force, nsteps x M, optional; see orc_step). */
+double orc_fitness_after_modes(int nx, int ny, int nz, const uint8_t* mat, const double* w,
+                               const double* kappa, const double* phi, const orc_params* p,
+                               int apply_lcc, int nsteps, const uint8_t* force, uint8_t* modes_out,
+                               uint64_t* mode_hash)
 {
     orc_robot* R = orc_robot_new(nx, ny, nz, mat, w, kappa, phi, p, apply_lcc);
     double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(R->M > 0 ? R->M : 1));
     uint8_t* modes = (uint8_t*)malloc((size_t)(R->M > 0 ? R->M : 1));
     uint64_t h = 1469598103934665603ull;   /* FNV-1a over all modes of all steps */
     for (int n = 0; n < nsteps; ++n) {
-        orc_step(R, p, F, modes, NULL);
+        orc_step(R, p, F, modes, NULL, force ? force + (size_t)n * (size_t)R->M : NULL);
+        if (modes_out) memcpy(modes_out + (size_t)n * (size_t)R->M, modes, (size_t)R->M);
         for (int m = 0; m < R->M; ++m) { h ^= modes[m]; h *= 1099511628211ull; }
     }
     double f = orc_robot_fitness(R, p);
@@ -780,7 +804,7 @@ double orc_robot_adjoint(int nx, int ny, int nz, const uint8_t* mat, const doubl
     /* forward, keeping x_n, the pre-contact force and the contact modes of every step */
     for (int n = 0; n < nsteps; ++n) {
         memcpy(X + (size_t)n * M3, R->x, sizeof(double) * 3 * (size_t)M);
-        orc_step(R, p, F, modes + (size_t)n * (size_t)M, Fh + (size_t)n * M3);
+        orc_step(R, p, F, modes + (size_t)n * (size_t)M, Fh + (size_t)n * M3, NULL);
     }
     memcpy(X + (size_t)nsteps * M3, R->x, sizeof(double) * 3 * (size_t)M);
     double fit = orc_robot_fitness(R, p);

@@ -1230,6 +1230,97 @@ static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
     return SIM_OK;
 }
 
+// Contact modes of one robot over the recorded run: the checkpoint segments are replayed in
+// recording mode (lattice robots with the per-corner kernel, streamed robots with the streamed
+// kernel, both as in sim_backward) and the robot's mode field copied out segment by segment.
+sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop || !ctx->rec_valid) return fail(SIM_ESTATE, "no recorded forward run");
+    if (robot < 0 || robot >= ctx->P) return fail(SIM_EINVAL, "robot %d out of range", robot);
+    if (!out) return fail(SIM_EINVAL, "null output");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int K = ctx->ckpt_every, N = ctx->rec_n;
+    const size_t Mc = ctx->M_cap;
+    const int r = robot;
+    const int C = (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
+    const int64_t mo = ctx->moff[r];
+    bool streamed = false;
+    for (int q : ctx->stream_robots) streamed = streamed || q == r;
+    VX_CK(ctx->d_sc_rec.ensure(N));
+    VX_LAUNCH(ctx, launch_sincos_table(2.0 * 3.141592653589793 * ctx->p.freq, ctx->p.dt, ctx->rec_step0, N,
+                                       ctx->d_sc_rec.p, s));
+    VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+    VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_v0.ensure(Mc));
+    VX_CK(ctx->d_rep_u1.ensure(Mc)); VX_CK(ctx->d_rep_v1.ensure(Mc));
+    std::vector<uint32_t> fl(C);
+    VX_CK(cudaMemcpyAsync(fl.data(), ctx->d_cflags.p + mo, sizeof(uint32_t) * C, cudaMemcpyDeviceToHost, s));
+    std::vector<float4> rec((size_t)K * C);
+    const int nseg = (N + K - 1) / K;
+    for (int seg = 0; seg < nseg; ++seg) {
+        const int n0 = seg * K, n1 = std::min(N, n0 + K);
+        if (!streamed) {
+            LatticeArgs f{};
+            f.pv = ctx->view();
+            f.corner_order = ctx->d_mass_corner.p;
+            f.cflags = ctx->d_cflags.p;
+            f.prm = ctx->d_prm.p;
+            f.c = ctx->stepconst();
+            f.items = ctx->d_items.p;
+            f.item_robots = ctx->d_item_robots.p;
+            f.n_items = ctx->n_items;
+            f.queue = ctx->d_queue.p;
+            f.rec_u = ctx->d_srec_u.p;
+            f.rec_f = ctx->d_srec_f.p;
+            f.rec_stride = (int64_t)Mc;
+            VX_CK(cudaMemcpyAsync(ctx->d_rep_u0.p, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, s));
+            VX_CK(cudaMemcpyAsync(ctx->d_rep_v0.p, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, s));
+            f.u = ctx->d_rep_u0.p;
+            f.v = ctx->d_rep_v0.p;
+            f.sc = ctx->d_sc_rec.p + n0;
+            f.nsteps = n1 - n0;
+            const int threads = lattice_max_threads();
+            VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+            VX_LAUNCH(ctx, launch_step_lattice(f, std::min(ctx->n_items, ctx->num_sms), threads,
+                                               sizeof(float4) * kLatticeSlotVec4 * (size_t)threads, s));
+        } else {
+            StreamArgs f{};
+            f.pv = ctx->view();
+            f.cflags = ctx->d_cflags.p;
+            f.prm = ctx->d_prm.p;
+            f.sc = ctx->d_sc_rec.p;
+            f.c = ctx->stepconst();
+            f.robots = ctx->d_stream.p;
+            f.n_robots = ctx->n_stream;
+            float4* ru[2] = {ctx->d_rep_u0.p, ctx->d_rep_u1.p};
+            float4* rv[2] = {ctx->d_rep_v0.p, ctx->d_rep_v1.p};
+            for (int i = 0; i < n1 - n0; ++i) {
+                f.u_in = i == 0 ? ctx->d_ckpt_u.p + (size_t)seg * Mc : ru[(i - 1) & 1];
+                f.v_in = i == 0 ? ctx->d_ckpt_v.p + (size_t)seg * Mc : rv[(i - 1) & 1];
+                f.u_out = ru[i & 1];
+                f.v_out = rv[i & 1];
+                f.rec_u = ctx->d_srec_u.p + (size_t)i * Mc;
+                f.rec_f = ctx->d_srec_f.p + (size_t)i * Mc;
+                VX_LAUNCH(ctx, launch_step_streamed(f, n0 + i, ctx->max_stream_corner, s));
+            }
+        }
+        VX_CK(cudaMemcpy2DAsync(rec.data(), sizeof(float4) * C, ctx->d_srec_u.p + mo, sizeof(float4) * Mc,
+                                sizeof(float4) * C, n1 - n0, cudaMemcpyDeviceToHost, s));
+        VX_CK(cudaStreamSynchronize(s));
+        for (int j = 0; j < n1 - n0; ++j)
+            for (int c = 0; c < C; ++c) {
+                uint32_t mode = 0u;
+                if (fl[c] >> 31) std::memcpy(&mode, &rec[(size_t)j * C + c].w, sizeof(mode));
+                out[(size_t)(n0 + j) * C + c] = (uint8_t)mode;
+            }
+    }
+    return SIM_OK;
+}
+
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa, float* g_phi)
 {
     if (sim_status st = check_ctx(ctx)) return st;

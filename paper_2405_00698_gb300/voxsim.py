@@ -25,7 +25,7 @@ GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
-           "sim_backward", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 
@@ -98,6 +98,7 @@ def lib():
                                   vp, vp],
             "sim_set_checkpointing": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
+            "sim_get_contact_modes": [vp, i32, vp],
             "sim_autotune": [vp, i32, vp, vp],
             "sim_diversity": [vp, vp, i32, i32, vp],
             "sim_get_counts": [vp, vp, vp],
@@ -285,6 +286,14 @@ class Simulator:
     # -- differentiation ---------------------------------------------------------------------
     def set_checkpointing(self, k: int):
         _check(lib().sim_set_checkpointing(self._h, int(k)))
+
+    def contact_modes(self, robot: int, n_steps: int):
+        """Contact mode (0 free, 1 stuck, 2 slipping) of every grid corner of one robot at every
+        step of the recorded run: uint8 [n_steps, corners]."""
+        nx, ny, nz = (int(v) for v in self.dims[robot])
+        out = np.zeros((n_steps, (nx + 1) * (ny + 1) * (nz + 1)), np.uint8)
+        _check(lib().sim_get_contact_modes(self._h, int(robot), out.ctypes.data))
+        return out
 
     def backward(self, dL_df, g_w, g_kappa, g_phi):
         ptrs = [_ptr(t)[0] for t in (dL_df, g_w, g_kappa, g_phi)]

@@ -220,3 +220,67 @@ def test_adjoint_full_size_finite_differences(vs, orc):
     assert checked >= 16, (checked, skipped)
     assert len(failed) <= checked // 2, errs
     assert not errs or errs[-1] <= 1e-1, errs
+
+
+def _fd_pair_forced(args):
+    """FP64 oracle fitness at theta +- h along an imposed contact-mode sequence."""
+    from oracle import oracle as orc_mod
+    grid, dims, n, base, name, v, h, modes = args
+    ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
+    am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
+    fp, _, _ = orc_mod.fitness_after_modes(grid, dims, PHYS, n, force=modes, **ap)
+    fm, _, _ = orc_mod.fitness_after_modes(grid, dims, PHYS, n, force=modes, **am)
+    return fp, fm
+
+
+def test_adjoint_full_size_along_the_gpu_contact_modes(vs, orc):
+    """The same full-size gradient against FP64 central differences taken along the contact
+    modes the GPU run took (sim_get_contact_modes): with the stick/slip decisions shared, both
+    sides differentiate the same piecewise-smooth map, and every sampled parameter meets 1e-3."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import torch
+    rng = np.random.default_rng(3)
+    P, N, K = 512, 2000, 100
+    pop = W.population_uniform(P, (8, 8, 8), seed=3)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sim = vs.Simulator(PHYS)
+    sim.set_checkpointing(K)
+    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+    sim.step(N)
+    _, S = sim.counts()
+    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+    sim.backward(t(np.ones(P)), *g)
+    torch.cuda.synchronize()
+    g = dict(zip(("w", "kappa", "phi"), (a.cpu().numpy() for a in g)))
+    picks = W.stratified_subset(S, 2)
+    corner_modes = {r: sim.contact_modes(r, N) for r in picks}
+    sim.close()
+    pick_rng = np.random.default_rng(45)
+    jobs, meta = [], []
+    for r in picks:
+        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+        base = {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
+                "phi": phi[a:b].astype(np.float64)}
+        R = orc.Robot(pop.grid(r), (8, 8, 8), PHYS, **base)
+        mass_corner = R.topology()["mass_corner"]
+        modes = np.ascontiguousarray(corner_modes[r][:, mass_corner])
+        assert (modes != 0).any()
+        kept = np.flatnonzero(orc.lcc(pop.grid(r), (8, 8, 8)) > 0)
+        for _ in range(32):
+            name = ("w", "kappa", "phi")[pick_rng.integers(3)]
+            v = int(pick_rng.choice(kept))
+            h = 1e-6 * max(1.0, abs(base[name][v]))
+            jobs.append((pop.grid(r), (8, 8, 8), N, base, name, v, h, modes))
+            meta.append((r, a, name, v, h))
+    with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_fd_pair_forced, jobs))
+    failed = []
+    for (r, a, name, v, h), (fp, fm) in zip(meta, res):
+        fd = (fp - fm) / (2 * h)
+        gr = g[name][a:a + 512]
+        scale = max(abs(fd), 1e-3 * np.abs(gr).max())
+        if abs(gr[v] - fd) > 1e-3 * scale:
+            failed.append((r, name, v, float(gr[v]), fd, abs(gr[v] - fd) / scale))
+    assert len(failed) <= 1, failed

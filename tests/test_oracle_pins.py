@@ -551,3 +551,45 @@ def test_crossover_rate(orc):
     assert np.array_equal(out["genomes"][rows].astype(np.float32), g[out["parents"][rows, 0]])
     none = orc.evo_generation(f, g, E, 5, 0, 0, 0.1, W.Evolution(cross_rate=0.0).keep_threshold())
     assert np.all(none["mask"][E:] == 1)
+
+
+# ------------------------------------------------------------------------------------------
+# Imposed contact modes: the step map along a given mode sequence
+# ------------------------------------------------------------------------------------------
+
+def test_imposed_natural_modes_reproduce_the_run(orc):
+    """Imposing the modes a run decided on reproduces that run exactly."""
+    rng = np.random.default_rng(21)
+    mat = W.uniform_materials(rng, (4, 3, 3))
+    f0, modes, h0 = orc.fitness_after_modes(mat, (4, 3, 3), PHYS, 500)
+    assert (modes != 0).any()                   # contact happens
+    f1, modes1, h1 = orc.fitness_after_modes(mat, (4, 3, 3), PHYS, 500, force=modes)
+    assert f1 == f0 and h1 == h0 and np.array_equal(modes1, modes)
+
+
+def test_imposed_modes_make_every_parameter_differentiable(orc):
+    """Along a fixed mode sequence the map is smooth: FP64 central differences match the oracle's
+    adjoint (which holds the modes fixed) for every sampled parameter, including those whose free
+    +h / -h runs switch modes."""
+    rng = np.random.default_rng(22)
+    dims, n = (3, 3, 3), 600
+    mat = W.uniform_materials(rng, dims)
+    mat[0, :, :] = np.maximum(mat[0, :, :], 1)
+    V = mat.size
+    w = rng.uniform(0.5, 1.0, V); kappa = np.asarray(PHYS.k_mat)[mat.reshape(-1)].astype(float)
+    phi = np.asarray(PHYS.phase_mat)[mat.reshape(-1)] + rng.uniform(-0.5, 0.5, V)
+    _, modes, _ = orc.fitness_after_modes(mat, dims, PHYS, n, w, kappa, phi)
+    _, gw, gk, gp = orc.adjoint(mat, dims, PHYS, n, 1.0, w, kappa, phi)
+    grads = {"w": gw, "kappa": gk, "phi": gp}
+    base = {"w": w, "kappa": kappa, "phi": phi}
+    occ = np.flatnonzero(orc.lcc(mat, dims) > 0)
+    for name in ("w", "kappa", "phi"):
+        for v in rng.choice(occ, 6, replace=False):
+            h = 1e-6 * max(1.0, abs(base[name][v]))
+            ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
+            am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
+            fp, _, _ = orc.fitness_after_modes(mat, dims, PHYS, n, force=modes, **ap)
+            fm, _, _ = orc.fitness_after_modes(mat, dims, PHYS, n, force=modes, **am)
+            fd = (fp - fm) / (2 * h)
+            scale = max(abs(fd), 1e-3 * np.abs(grads[name]).max())
+            assert abs(grads[name][v] - fd) <= 1e-5 * scale, (name, int(v), grads[name][v], fd)
