@@ -35,6 +35,18 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Asynchronous global -> shared copy of 16 or 8 bytes (cp.async), its commit and its wait.
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes_pow)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    if (bytes_pow == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -96,14 +108,32 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                 });
             }
             const float z0 = in ? a.u0[o].w : 0.f;
+            // each step's record is copied into shared memory one step ahead (cp.async), so its
+            // load latency overlaps the previous step
+            float4* stage_u = sm4 + (size_t)kLatticeSlotVec4 * kBlock;           // [2][kBlock]
+            float2* stage_f = reinterpret_cast<float2*>(stage_u + 2 * kBlock);   // [2][kBlock]
+            int sb = 0;
+            if (in) {
+                const int64_t ro = (int64_t)(a.n1 - 1 - a.n0) * a.rec_stride + o;
+                cp_async(&stage_u[tid], &a.rec_u[ro], 16);
+                cp_async(&stage_f[tid], &a.rec_f[ro], 8);
+            }
+            cp_async_commit();
             for (int n = a.n1 - 1; n >= a.n0; --n) {
-                const int64_t ro = (int64_t)(n - a.n0) * a.rec_stride + o;
+                cp_async_wait_all();
                 float4 un = make_float4(0.f, 0.f, 0.f, 0.f);
                 float2 fh = make_float2(0.f, 0.f);
                 if (in) {
-                    un = a.rec_u[ro];
-                    fh = a.rec_f[ro];
+                    un = stage_u[sb * kBlock + tid];
+                    fh = stage_f[sb * kBlock + tid];
+                    if (n > a.n0) {
+                        const int64_t ro = (int64_t)(n - 1 - a.n0) * a.rec_stride + o;
+                        cp_async(&stage_u[(sb ^ 1) * kBlock + tid], &a.rec_u[ro], 16);
+                        cp_async(&stage_f[(sb ^ 1) * kBlock + tid], &a.rec_f[ro], 8);
+                    }
                 }
+                cp_async_commit();
+                sb ^= 1;
                 // mass part: (lambda_u, lambda_v) of step n+1 -> lambda_F and lambda_v of step n
                 float lFx = 0.f, lFy = 0.f, lFz = 0.f;
                 if (mass) mass_adjoint(__float_as_uint(un.w), z0 + un.z, fh, lux, luy, luz, lvx, lvy, lvz, lFx, lFy, lFz, c);

@@ -1150,7 +1150,8 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
         a.first = seg == nseg - 1;
         a.last = seg == 0;
         VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
-        VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem, s));
+        // slots plus the double-buffered record staging (a float4 and a float2 per thread)
+        VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem + (size_t)threads * 2 * (16 + 8), s));
     }
     return SIM_OK;
 }
