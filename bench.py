@@ -292,6 +292,7 @@ def run_ours(args):
         sim.close()
         rec["batched_vs_plain"] = measure_uneven(vs, stream, args, peaks)
         rec["adjoint"] = measure_adjoint(vs, stream, args)
+        rec["adjoint_records"] = measure_adjoint(vs, stream, args, records=True)
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
         rec["streamed_adjoint"] = measure_streamed_adjoint(vs, stream, args, peaks)
@@ -368,9 +369,11 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
             "speedup_vs_plain": batched / res["plain"]}
 
 
-def measure_adjoint(vs, stream, args, P=512, N=2000, K=100):
+def measure_adjoint(vs, stream, args, P=512, N=2000, K=100, records=False):
     """512 robots 8x8x8, per-voxel (w, kappa, phi), 2000 steps with checkpoints every 100:
-    forward with recording plus the reverse sweep, as gradient evaluations per second."""
+    forward with recording plus the reverse sweep, as gradient evaluations per second.
+    records: the forward also keeps every step's record (24 B per corner per step, 17.9 GB
+    here) and the backward sweeps them without replaying the segments."""
     import torch
     rng = np.random.default_rng(3)
     pop = W.population_uniform(P, (8, 8, 8), seed=3)
@@ -378,6 +381,7 @@ def measure_adjoint(vs, stream, args, P=512, N=2000, K=100):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     sim = vs.Simulator(W.CONFIG, stream=stream)
     sim.set_checkpointing(K)
+    sim.set_trajectory_records(records)
     args_pop = (t(pop.mats), t(w), t(kappa), t(phi))
     n = pop.mats.size
     gw = torch.empty(n, device="cuda"); gk = torch.empty_like(gw); gp = torch.empty_like(gw)
@@ -392,7 +396,9 @@ def measure_adjoint(vs, stream, args, P=512, N=2000, K=100):
     bwd = _timed(stream, lambda: sim.backward(dl, gw, gk, gp))
     _, S = sim.counts()
     sim.close()
-    return {"workload": f"{P} robots 8x8x8, {N} steps, checkpoints every {K}", "grads_per_s": P / ((fwd + bwd) * 1e-3),
+    kept = ", every step's record kept" if records else ""
+    return {"workload": f"{P} robots 8x8x8, {N} steps, checkpoints every {K}{kept}",
+            "grads_per_s": P / ((fwd + bwd) * 1e-3),
             "unit": "robot gradients/s (forward with checkpoints + reverse sweep)", "forward_ms": fwd,
             "backward_ms": bwd, "backward_spring_updates_per_s": float(S.sum()) * N / (bwd * 1e-3)}
 
@@ -617,6 +623,7 @@ def run_case(args):
         P = args.robots if args.robots != P_ROBOTS else 512
         N = args.sim_steps if args.sim_steps != SIM_STEPS else 2000
         print(json.dumps({"case": args.case, **measure_adjoint(vs, stream, args, P=P, N=N)}))
+        print(json.dumps({"case": args.case, **measure_adjoint(vs, stream, args, P=P, N=N, records=True)}))
     else:
         P = args.robots if args.robots != P_ROBOTS else 16
         print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P)}))

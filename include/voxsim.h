@@ -259,6 +259,21 @@ sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t
  * Errors: SIM_EINVAL (k_steps < 0, SIM_ACC_ATOMIC, damped parameters), SIM_ENOMEM. */
 sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 
+/* Keep every step's record of the recorded run (on = 1) instead of only its checkpoints
+ * (on = 0, the default).  While on and checkpointing is on (sim_set_checkpointing), each
+ * sim_step_n call also stores, for every step and every grid corner of the robots on the
+ * resident lattice kernel, the state before the update with its contact mode and the horizontal
+ * spring force before contact (24 bytes per corner per step: n_steps x 24 B x the population's
+ * grid corners, e.g. about 18 GB for 512 robots of 8x8x8 voxels over 2000 steps), and
+ * sim_backward sweeps those records backwards in one pass without replaying the forward steps
+ * (the same forward run and contact modes bit for bit, the same gradients up to the order of
+ * the per-voxel atomic sums).  Streamed robots keep their checkpointed replay, and so does every
+ * robot when the routing of robots to kernels has changed since the recorded call (a
+ * sim_autotune in between).  A sim_step_n call that cannot allocate the records fails with
+ * SIM_ENOMEM.  Changing the setting discards the recorded run; turning it off frees the records.
+ * Errors: SIM_EINVAL (on not 0 or 1). */
+sim_status sim_set_trajectory_records(voxsim_ctx* ctx, int32_t on);
+
 /* Reverse-mode gradient of L = sum_r dL_df[r] * fitness_r over the most recent recorded
  * sim_step_n call, with respect to the per-voxel material weight w, stiffness kappa and
  * actuation phase phi (k_v = w_v kappa_v, a_v = w_v amp_mat[material], phase phi_v).  The
@@ -296,7 +311,9 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
  * admissible kernel (the lattice-gather kernel in its two variants, the cluster lattice kernel,
  * the atomic resident kernel at three block sizes, the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
  * the current state (CUDA events), and the fastest is kept for that class.  The state is
- * restored afterwards; the choices persist for later populations of this context.  Modes that
+ * restored afterwards; the choices persist for later populations of this context.  The trial
+ * runs record nothing: a recorded run (sim_step_n with checkpointing on) stays available to
+ * sim_backward, which replays its checkpoints.  Modes that
  * require bit-reproducibility (SIM_ACC_GATHER, checkpointing) only consider deterministic
  * kernels.  kind_out / threads_out: int32 [10] host arrays (either may be NULL) receiving per
  * class 0 = lattice (per corner), 1 = atomic resident, 2 = streamed, 3 = lattice

@@ -208,6 +208,16 @@ struct voxsim_ctx {
     int rec_n = 0;
     DevBuf<float4> d_ckpt_u, d_ckpt_v;
     DevBuf<float2> d_sc_rec;
+    // whole-trajectory records of the lattice-kernel robots (sim_set_trajectory_records): the
+    // forward keeps every step's record and sim_backward sweeps them without replaying
+    bool keep_records = false;   // requested
+    bool rec_full = false;       // the recorded call kept them
+    // the routing of robots to kernels changes with every build_work_items; records kept under
+    // another routing than the current one are not used (the checkpoints are replayed instead)
+    uint64_t items_version = 0, rec_items_version = 0;
+    bool records_usable() const { return rec_full && rec_items_version == items_version; }
+    DevBuf<float4> d_trec_u;
+    DevBuf<float2> d_trec_f;
     // streamed adjoint: per-step records of a segment, adjoints, sensitivity sums, replay state
     DevBuf<float4> d_srec_u, d_slu, d_slv, d_slF0, d_slF1, d_rep_u0, d_rep_u1, d_rep_v0, d_rep_v1;
     DevBuf<float2> d_srec_f;
@@ -581,6 +591,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
 {
     static const int kSlot[6] = {64, 128, 192, 256, 384, 768};
     const int block = lattice_max_threads();
+    ++ctx->items_version;
     if (!ctx->tuned) default_choices(ctx);
     ctx->max_big_corner = 0;
     ctx->max_big_spring_cap = 0;
@@ -747,7 +758,9 @@ static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
     return SIM_OK;
 }
 
-static sim_status step_lattice(voxsim_ctx* ctx, int n)
+// record: the call is sim_step_n's with checkpointing on (checkpoints, and the whole-trajectory
+// records when they are kept, are written; every other caller steps without recording).
+static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
 {
     if (ctx->n_items == 0) return SIM_OK;
     LatticeArgs a{};
@@ -764,11 +777,16 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n)
     a.item_robots = ctx->d_item_robots.p;
     a.n_items = ctx->n_items;
     a.queue = ctx->d_queue.p;
-    if (ctx->ckpt_every > 0) {                  // (buffers sized by sim_step_n)
+    if (record) {                               // (buffers sized by sim_step_n)
         a.ckpt_u = ctx->d_ckpt_u.p;
         a.ckpt_v = ctx->d_ckpt_v.p;
         a.ckpt_stride = ctx->M_cap;
         a.ckpt_every = ctx->ckpt_every;
+        if (ctx->keep_records) {                // every step's record, for a replay-free backward
+            a.rec_u = ctx->d_trec_u.p;
+            a.rec_f = ctx->d_trec_f.p;
+            a.rec_stride = (int64_t)ctx->M_cap;
+        }
     }
     const int threads = lattice_max_threads();
     const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
@@ -873,7 +891,7 @@ static sim_status step_plain(voxsim_ctx* ctx, int n)
 
 // Streamed robots: one launch per step, positions double-buffered; an odd number of steps
 // leaves the newest positions in the alternate buffer, which are copied back per robot.
-static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
+static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s, bool record)
 {
     StreamArgs a{};
     a.pv = ctx->view();
@@ -883,7 +901,7 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
     a.c = ctx->stepconst();
     a.robots = ctx->d_stream.p;
     a.n_robots = ctx->n_stream;
-    const int K = ctx->ckpt_every;
+    const int K = record ? ctx->ckpt_every : 0;
     for (int i = 0; i < n; ++i) {
         // the state at the start of every K-th step goes to its segment's checkpoint
         a.ckpt_u = K > 0 && i % K == 0 ? ctx->d_ckpt_u.p + (size_t)(i / K) * ctx->M_cap : nullptr;
@@ -908,18 +926,18 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s)
 // Streamed robots: one launch per step, positions double-buffered (an odd number of steps
 // leaves the newest positions in the alternate buffer, copied back per robot).  The sequence is
 // captured once into a CUDA graph per step count and replayed.
-static sim_status step_streamed(voxsim_ctx* ctx, int n)
+static sim_status step_streamed(voxsim_ctx* ctx, int n, bool record)
 {
     if (ctx->n_stream == 0) return SIM_OK;
     cudaStream_t s = ctx->stream;
     const void* key = ctx->d_sc.p;   // the step table may move when it grows
-    const void* ckpt = ctx->ckpt_every > 0 ? (const void*)ctx->d_ckpt_u.p : nullptr;
+    const void* ckpt = record ? (const void*)ctx->d_ckpt_u.p : nullptr;
     if (!(ctx->stream_graph && ctx->stream_graph_n == n && ctx->stream_graph_key == key &&
-          ctx->stream_graph_ckpt == ckpt && ctx->stream_graph_every == ctx->ckpt_every)) {
+          ctx->stream_graph_ckpt == ckpt && ctx->stream_graph_every == (record ? ctx->ckpt_every : 0))) {
         ctx->drop_graph();
         if (!ctx->capture_stream) VX_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         VX_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        sim_status st = enqueue_streamed(ctx, n, ctx->capture_stream);
+        sim_status st = enqueue_streamed(ctx, n, ctx->capture_stream, record);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (st != SIM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -930,7 +948,7 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n)
         ctx->stream_graph_n = n;
         ctx->stream_graph_key = key;
         ctx->stream_graph_ckpt = ckpt;
-        ctx->stream_graph_every = ctx->ckpt_every;
+        ctx->stream_graph_every = record ? ctx->ckpt_every : 0;
     }
     VX_CK(cudaGraphLaunch(ctx->stream_graph, s));
     ctx->launches += n;
@@ -950,10 +968,18 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
                               ctx->d_sc.p, s));
     if (ctx->ckpt_every > 0 && ctx->n_big > 0)
         return fail(SIM_EINVAL, "checkpointing needs the deterministic kernels (robots on the atomic kernel)");
-    if (ctx->ckpt_every > 0) {
+    const bool record = ctx->ckpt_every > 0;
+    // the buffers of the previous recorded call may be reallocated below: it is gone either way
+    ctx->rec_valid = false;
+    ctx->rec_full = false;
+    if (record) {
         const int nseg = (n_steps + ctx->ckpt_every - 1) / ctx->ckpt_every;
         VX_CK(ctx->d_ckpt_u.ensure((size_t)nseg * ctx->M_cap));
         VX_CK(ctx->d_ckpt_v.ensure((size_t)nseg * ctx->M_cap));
+        if (ctx->keep_records && ctx->n_items > 0) {
+            VX_CK(ctx->d_trec_u.ensure((size_t)n_steps * ctx->M_cap));
+            VX_CK(ctx->d_trec_f.ensure((size_t)n_steps * ctx->M_cap));
+        }
     }
     cudaEvent_t ev[2];
     if (sim_status st = timing_pair(ctx, ev)) return st;
@@ -961,18 +987,18 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
     if (ctx->p.path == SIM_PATH_PLAIN) {
         if (sim_status st = step_plain(ctx, n_steps)) return st;
     } else {
-        if (sim_status st = step_lattice(ctx, n_steps)) return st;
+        if (sim_status st = step_lattice(ctx, n_steps, record)) return st;
         if (sim_status st = step_cluster(ctx, n_steps)) return st;
         if (sim_status st = step_resident(ctx, n_steps)) return st;
-        if (sim_status st = step_streamed(ctx, n_steps)) return st;
+        if (sim_status st = step_streamed(ctx, n_steps, record)) return st;
     }
     VX_CK(cudaEventRecord(ev[1], s));
-    if (ctx->ckpt_every > 0) {
+    if (record) {
         ctx->rec_valid = true;
+        ctx->rec_full = ctx->keep_records && ctx->n_items > 0;
+        ctx->rec_items_version = ctx->items_version;
         ctx->rec_step0 = ctx->step;
         ctx->rec_n = n_steps;
-    } else {
-        ctx->rec_valid = false;
     }
     ctx->step += n_steps;
     return SIM_OK;
@@ -1079,21 +1105,41 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps)
     return SIM_OK;
 }
 
+sim_status sim_set_trajectory_records(voxsim_ctx* ctx, int32_t on)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (on != 0 && on != 1) return fail(SIM_EINVAL, "on must be 0 or 1");
+    ctx->keep_records = on != 0;
+    ctx->rec_valid = false;
+    ctx->rec_full = false;
+    if (!on) {
+        DeviceGuard g(ctx->device);
+        ctx->d_trec_u.release();
+        ctx->d_trec_f.release();
+    }
+    return SIM_OK;
+}
+
 // The adjoint of the robots on the lattice kernels: per checkpoint segment, last to first, the
 // forward per-corner lattice kernel replays the segment from a copy of its checkpoint in
 // recording mode, then the reverse-sweep kernel runs over the records; adjoints and sensitivity
-// sums are carried between segments in device memory.  The checkpoints stay intact, so the
-// backward pass may be repeated (other dL_df) on the same recorded run.
+// sums are carried between segments in device memory.  When the forward kept every step's
+// record, one reverse sweep runs over the whole run and nothing is replayed.  The checkpoints
+// and records stay intact, so the backward pass may be repeated (other dL_df) on the same
+// recorded run.
 static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
 {
     cudaStream_t s = ctx->stream;
-    const int K = ctx->ckpt_every, N = ctx->rec_n;
+    const bool full = ctx->records_usable();
+    const int N = ctx->rec_n, K = full ? N : ctx->ckpt_every;
     const size_t Mc = ctx->M_cap;
-    VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
-    VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
-    VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
-    VX_CK(ctx->d_sacc.ensure(39 * Mc));
-    VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_v0.ensure(Mc));
+    if (!full) {
+        VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
+        VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+        VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
+        VX_CK(ctx->d_sacc.ensure(39 * Mc));
+        VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_v0.ensure(Mc));
+    }
     const int threads = lattice_max_threads();
     const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
     const int grid = std::min(ctx->n_items, ctx->num_sms);
@@ -1116,8 +1162,8 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     a.prm = ctx->d_prm.p;
     a.mat = ctx->d_mat.p;
     a.u0 = ctx->d_x.p;
-    a.rec_u = ctx->d_srec_u.p;
-    a.rec_f = ctx->d_srec_f.p;
+    a.rec_u = full ? ctx->d_trec_u.p : ctx->d_srec_u.p;
+    a.rec_f = full ? ctx->d_trec_f.p : ctx->d_srec_f.p;
     a.rec_stride = (int64_t)Mc;
     a.lu = ctx->d_slu.p;
     a.lv = ctx->d_slv.p;
@@ -1135,16 +1181,18 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     const int nseg = (N + K - 1) / K;
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
-        VX_CK(cudaMemcpyAsync(ctx->d_rep_u0.p, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
-                              cudaMemcpyDeviceToDevice, s));
-        VX_CK(cudaMemcpyAsync(ctx->d_rep_v0.p, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
-                              cudaMemcpyDeviceToDevice, s));
-        f.u = ctx->d_rep_u0.p;
-        f.v = ctx->d_rep_v0.p;
-        f.sc = ctx->d_sc_rec.p + n0;
-        f.nsteps = n1 - n0;
-        VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
-        VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, s));
+        if (!full) {
+            VX_CK(cudaMemcpyAsync(ctx->d_rep_u0.p, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, s));
+            VX_CK(cudaMemcpyAsync(ctx->d_rep_v0.p, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, s));
+            f.u = ctx->d_rep_u0.p;
+            f.v = ctx->d_rep_v0.p;
+            f.sc = ctx->d_sc_rec.p + n0;
+            f.nsteps = n1 - n0;
+            VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
+            VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, s));
+        }
         a.n0 = n0;
         a.n1 = n1;
         a.first = seg == nseg - 1;
@@ -1262,7 +1310,10 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
     const int nseg = (N + K - 1) / K;
     for (int seg = 0; seg < nseg; ++seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
-        if (!streamed) {
+        const float4* src = ctx->d_srec_u.p;
+        if (!streamed && ctx->records_usable()) {   // the forward kept every step's record
+            src = ctx->d_trec_u.p + (size_t)n0 * Mc;
+        } else if (!streamed) {
             LatticeArgs f{};
             f.pv = ctx->view();
             f.corner_order = ctx->d_mass_corner.p;
@@ -1309,7 +1360,7 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
                 VX_LAUNCH(ctx, launch_step_streamed(f, n0 + i, ctx->max_stream_corner, s));
             }
         }
-        VX_CK(cudaMemcpy2DAsync(rec.data(), sizeof(float4) * C, ctx->d_srec_u.p + mo, sizeof(float4) * Mc,
+        VX_CK(cudaMemcpy2DAsync(rec.data(), sizeof(float4) * C, src + mo, sizeof(float4) * Mc,
                                 sizeof(float4) * C, n1 - n0, cudaMemcpyDeviceToHost, s));
         VX_CK(cudaStreamSynchronize(s));
         for (int j = 0; j < n1 - n0; ++j)
@@ -1437,10 +1488,10 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
                     VX_CK(cudaMemcpyAsync(ctx->d_v_alt.p, snap_v.p, sizeof(float4) * Mc, cudaMemcpyDeviceToDevice, s));
                 }
                 VX_CK(cudaEventRecord(e0, s));
-                if ((result = step_lattice(ctx, n_steps)) != SIM_OK) break;
+                if ((result = step_lattice(ctx, n_steps, false)) != SIM_OK) break;
                 if ((result = step_cluster(ctx, n_steps)) != SIM_OK) break;
                 if ((result = step_resident(ctx, n_steps)) != SIM_OK) break;
-                if ((result = step_streamed(ctx, n_steps)) != SIM_OK) break;
+                if ((result = step_streamed(ctx, n_steps, false)) != SIM_OK) break;
                 VX_CK(cudaEventRecord(e1, s));
                 VX_CK(cudaEventSynchronize(e1));
                 VX_CK(cudaEventElapsedTime(&ms, e0, e1));

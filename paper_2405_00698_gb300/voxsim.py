@@ -25,7 +25,7 @@ GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
-           "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
+           "sim_set_trajectory_records", "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
            "sim_get_timing")
 
 
@@ -97,6 +97,7 @@ def lib():
             "evo_gradient_step": [vp, vp, i32, i32, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float,
                                   vp, vp],
             "sim_set_checkpointing": [vp, i32],
+            "sim_set_trajectory_records": [vp, i32],
             "sim_backward": [vp, vp, vp, vp, vp],
             "sim_get_contact_modes": [vp, i32, vp],
             "sim_autotune": [vp, i32, vp, vp],
@@ -286,6 +287,10 @@ class Simulator:
     # -- differentiation ---------------------------------------------------------------------
     def set_checkpointing(self, k: int):
         _check(lib().sim_set_checkpointing(self._h, int(k)))
+
+    def set_trajectory_records(self, on: bool):
+        """Keep every step's record of the recorded run, so that backward needs no replay."""
+        _check(lib().sim_set_trajectory_records(self._h, 1 if on else 0))
 
     def contact_modes(self, robot: int, n_steps: int):
         """Contact mode (0 free, 1 stuck, 2 slipping) of every grid corner of one robot at every
