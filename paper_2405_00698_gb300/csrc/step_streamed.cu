@@ -17,12 +17,12 @@
 namespace vx {
 namespace {
 
-// Loads of 4 directions in flight per batch and at least 4 blocks of 256 threads per SM (64
-// registers): measured 0.085 ms per step on 16 robots 40x40x40 against 0.101 ms for loads behind
-// each direction's mask test; batches of 1, 2 or 13 directions and 1, 3 or 5 blocks per SM were
-// slower.
+// Loads of 3 directions in flight per batch and at least 4 blocks of 256 threads per SM (64
+// registers, no spills): measured 0.140 ms per step on 32 robots 40x40x40, against 0.159 ms for
+// batches of 4, 0.155 / 0.140 / 0.154 / 0.266 ms for batches of 2 / 5 / 7 / 13, and 0.175 /
+// 0.173 ms with 3 / 5 blocks per SM (batches of 3 / 5).
 constexpr int kStreamThreads = 256;
-constexpr int kStreamBatch = 4;
+constexpr int kStreamBatch = 3;
 constexpr int kStreamMinBlocks = 4;
 
 __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
