@@ -17,13 +17,14 @@
 namespace vx {
 namespace {
 
-// Loads of 3 directions in flight per batch and at least 4 blocks of 256 threads per SM (64
-// registers, no spills): measured 0.140 ms per step on 32 robots 40x40x40, against 0.159 ms for
-// batches of 4, 0.155 / 0.140 / 0.154 / 0.266 ms for batches of 2 / 5 / 7 / 13, and 0.175 /
-// 0.173 ms with 3 / 5 blocks per SM (batches of 3 / 5).
-constexpr int kStreamThreads = 256;
+// Loads of 3 directions in flight per batch and at least 8 blocks of 128 threads per SM (64
+// registers, no spills): measured 0.137 ms per step on 32 robots 40x40x40.  With 4 blocks of 256
+// threads: 0.140 ms, against 0.159 ms for batches of 4, 0.155 / 0.140 / 0.154 / 0.266 ms for
+// batches of 2 / 5 / 7 / 13, and 0.175 / 0.173 ms with 3 / 5 blocks per SM (batches of 3 / 5);
+// 2 blocks of 512 threads 0.145 ms, 10 blocks of 128 (48 registers, spills) 0.163 ms.
+constexpr int kStreamThreads = 128;
 constexpr int kStreamBatch = 3;
-constexpr int kStreamMinBlocks = 4;
+constexpr int kStreamMinBlocks = 8;
 
 __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
 k_step_streamed(StreamArgs a, int n)
