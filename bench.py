@@ -59,7 +59,7 @@ def parse():
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
-    ap.add_argument("--case", choices=["streamed", "streamed_adjoint", "paper_preset", "adjoint"], default=None,
+    ap.add_argument("--case", choices=["streamed", "streamed_adjoint", "paper_preset", "adjoint", "uneven"], default=None,
                     help="run one extra measurement alone (for profiling; --robots sets its robots)")
     return ap.parse_args()
 
@@ -629,6 +629,10 @@ def run_case(args):
         print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
     elif args.case == "paper_preset":
         print(json.dumps({"case": args.case, **measure_paper_preset(vs, stream, args)}))
+    elif args.case == "uneven":
+        P = args.robots if args.robots != P_ROBOTS else 4096
+        N = args.sim_steps if args.sim_steps != SIM_STEPS else 5000
+        print(json.dumps({"case": args.case, **measure_uneven(vs, stream, args, peaks, P=P, N=N)}))
     elif args.case == "adjoint":
         P = args.robots if args.robots != P_ROBOTS else 512
         N = args.sim_steps if args.sim_steps != SIM_STEPS else 2000
