@@ -267,44 +267,6 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
         }
     }
     if (tid == 0) pv.n_spring[r] = S;
-    if (spr_pack_all) {
-    // 8. the atomic kernel's copy, direction-major: all springs of direction 0 by ascending
-    //    corner, then direction 1, ...  Within a warp the endpoints of one direction are distinct,
-    //    so the force accumulation does not collide.  Packed as (k, alpha L0, beta L0,
-    //    corner a | corner b << 14 | direction << 28).
-    int dbase = 0;
-    for (int d = 0; d < 13; ++d) {
-        int nd = 0;
-        for (int m = m_beg; m < m_end; ++m) {
-            int c = mass_corner[m];
-            int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
-            int bi = ci + c_dir[d][0], bj = cj + c_dir[d][1], bk = ck + c_dir[d][2];
-            if (bi < 0 || bj < 0 || bi >= cx || bj >= cy || bk >= cz) continue;
-            if (spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, nullptr,
-                                 nullptr, nullptr) > 0)
-                ++nd;
-        }
-        int total;
-        int pos = dbase + block_exclusive_scan(nd, sh_scan, &total);
-        const int cls = (c_dir[d][0] != 0) + (c_dir[d][1] != 0) + (c_dir[d][2] != 0);
-        const float L0 = (float)(cls == 1 ? e1 : (cls == 2 ? e2 : e3));
-        for (int m = m_beg; m < m_end; ++m) {
-            int c = mass_corner[m];
-            int ci = c % cx, cj = (c / cx) % cy, ck = c / (cx * cy);
-            int bi = ci + c_dir[d][0], bj = cj + c_dir[d][1], bk = ck + c_dir[d][2];
-            if (bi < 0 || bj < 0 || bi >= cx || bj >= cy || bk >= cz) continue;
-            float k, al, be;
-            if (spring_incidence(ci, cj, ck, d, nx, ny, nz, mat, w, kappa, phi, mc, &k, &al,
-                                 &be) == 0)
-                continue;
-            const unsigned ca = (unsigned)c, cb = (unsigned)(bi + cx * (bj + cy * bk));
-            unsigned bits = ca | (cb << 14) | ((unsigned)d << 28);
-            spr_pack_all[so + pos] = make_float4(k, al * L0, be * L0, __uint_as_float(bits));
-            ++pos;
-        }
-        dbase += total;
-    }
-    }
     if (!cflags_all) return;
     // 9. the lattice kernel's tables, indexed by corner: forward-spring mask (bits 0..12),
     //    backward-spring mask (bits 16..28: a spring from corner c - offset(d) to c), mass bit 31,
@@ -344,6 +306,44 @@ k_topology(PopView pv, const uint8_t* __restrict__ mat_raw_all, uint8_t* __restr
             if ((cflags[ai + cx * (aj + cy * ak)] >> d) & 1u) bw |= 1u << (16 + d);
         }
         cflags[c] |= bw;
+    }
+    if (!spr_pack_all) return;
+    __syncthreads();
+    // 10. the atomic kernel's copy of the springs, direction-major (all springs of direction 0,
+    //     then direction 1, ...), and within a direction interleaved over the residue of the
+    //     corner id mod 32: round j holds the j-th spring (by ascending corner) of every residue
+    //     that has one, in residue order.  Consecutive entries then have corners that differ mod
+    //     32, so a warp's float atomics and float4 loads at either endpoint fall on distinct
+    //     shared-memory banks, also in sparse robots, where ascending corners leave gaps.
+    //     Packed as (k, alpha L0, beta L0, corner a | corner b << 14 | direction << 28) from the
+    //     planes of step 9.  Warp w takes direction w, lane l the corners a = l (mod 32).
+    __shared__ int sh_cnt[13][32];
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (T + 31) >> 5;
+    for (int d = warp; d < 13; d += nwarps) {
+        int cnt = 0;
+        for (int a = lane; a < C; a += 32) cnt += (int)((cflags[a] >> d) & 1u);
+        sh_cnt[d][lane] = cnt;
+    }
+    __syncthreads();
+    float4* pack = spr_pack_all + so;
+    for (int d = warp; d < 13; d += nwarps) {
+        int dbase = 0;
+        for (int e = 0; e < d; ++e)
+            for (int b = 0; b < 32; ++b) dbase += sh_cnt[e][b];
+        const int off = c_dir[d][0] + cx * (c_dir[d][1] + cy * c_dir[d][2]);
+        int k = 0;                             // rank of this lane's next spring in its residue
+        for (int a = lane; a < C; a += 32) {
+            if (!((cflags[a] >> d) & 1u)) continue;
+            int pos = dbase;                   // springs of earlier rounds, then earlier residues
+            for (int b = 0; b < 32; ++b) {
+                const int nb = sh_cnt[d][b];
+                pos += min(nb, k) + ((b < lane && nb > k) ? 1 : 0);
+            }
+            const unsigned bits = (unsigned)a | ((unsigned)(a + off) << 14) | ((unsigned)d << 28);
+            pack[pos] = make_float4(prm[d * C + a], prm[(13 + d) * C + a], prm[(26 + d) * C + a],
+                                    __uint_as_float(bits));
+            ++k;
+        }
     }
 }
 
