@@ -150,6 +150,35 @@ def test_adjoint_full_size_sample(vs, orc):
     assert len(bad) <= 1, bad
 
 
+def test_trajectory_records_full_size(vs):
+    """The adjoint with every step's record kept in device memory (the bench's second adjoint
+    line: 512 robots 8x8x8, 2000 steps, 17.9 GB of records, no replay) against the checkpointed
+    replay of the same run: the forward runs agree bitwise, the gradients up to the order of the
+    per-voxel atomic sums (1e-5 of the largest entry)."""
+    import torch
+    rng = np.random.default_rng(3)
+    P, N, K = 512, 2000, 100
+    pop = W.population_uniform(P, (8, 8, 8), seed=3)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = []
+    for records in (False, True):
+        sim = vs.Simulator(PHYS)
+        sim.set_checkpointing(K)
+        sim.set_trajectory_records(records)
+        sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+        sim.step(N)
+        f = sim.fitness()
+        g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+        sim.backward(t(np.ones(P)), *g)
+        torch.cuda.synchronize()
+        out.append((f, [a.cpu().numpy() for a in g]))
+        sim.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for x, y in zip(out[0][1], out[1][1]):
+        assert np.abs(y - x).max() <= 1e-5 * np.abs(x).max()
+
+
 def _fd_pair(args):
     """FP64 oracle fitness at theta +- h for one parameter (run in a worker process)."""
     from oracle import oracle as orc_mod
