@@ -16,6 +16,8 @@
 //         recorded positions and adjoint forces, keeps its own share, accumulates the spring's
 //         sensitivities to k, alpha L0 and beta L0 in registers and leaves the other endpoint's
 //         share in a shared-memory plane, which that endpoint adds in direction order.
+// When the forward run kept every step's record (whole-trajectory records), nothing is replayed
+// and a single launch sweeps the whole run.
 // The adjoints and sensitivity sums are carried from one segment's launch to the next in device
 // memory; the last launch scatters the sums onto the voxels with atomics (one add per spring
 // and incident voxel).
