@@ -296,6 +296,7 @@ def run_ours(args):
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
         rec["streamed_adjoint"] = measure_streamed_adjoint(vs, stream, args, peaks)
+        rec["streamed_adjoint_records"] = measure_streamed_adjoint(vs, stream, args, peaks, records=True)
         rec["paper_preset"] = measure_paper_preset(vs, stream, args)
     if rank == 0:
         print(json.dumps(rec))
@@ -483,11 +484,12 @@ def measure_paper_preset(vs, stream, args, N=20000):
             "paper_figure": 7892537853, "note": "the paper's figure is on an RTX 3090 with unstated unit and workload"}
 
 
-def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100):
+def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100, records=False):
     """The adjoint on large robots (16 robots 40x40x40 at occupancy 0.7, state in HBM): forward
     with checkpoints every 100 steps, then the backward pass (segment replays with recording and
     the reverse sweep), as robot gradients per second and as algorithmic HBM bytes against the
-    measured peak.  A 500-step sample of the 5000-step workload."""
+    measured peak.  A 500-step sample of the 5000-step workload.  records: the forward also keeps
+    every step's record (24 B per corner per step, 13 GB here) and the backward only sweeps."""
     import torch
     rng = np.random.default_rng(6)
     pop = W.workload_large(P, seed=5, n=n)
@@ -495,6 +497,7 @@ def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     sim = vs.Simulator(W.CONFIG, stream=stream)
     sim.set_checkpointing(K)
+    sim.set_trajectory_records(records)
     args_pop = (t(pop.mats), t(w), t(kappa), t(phi))
     g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
     dl = torch.ones(P, dtype=torch.float64, device="cuda")
@@ -507,12 +510,15 @@ def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100):
     M, S = sim.counts()
     sim.close()
     Ssum, Msum = float(S.astype(np.int64).sum()), float(M.astype(np.int64).sum())
-    # algorithmic device-memory bytes per step: forward 12 B per spring + 64 B per mass; backward
-    # (replay with records, then the reverse step) 48 B per spring + 224 B per mass
-    fwd_gbs = (12.0 * Ssum + 64.0 * Msum) * N / (fwd * 1e-3) / 1e9
-    bwd_gbs = (48.0 * Ssum + 224.0 * Msum) * N / (bwd * 1e-3) / 1e9
+    # algorithmic device-memory bytes per step: forward 12 B per spring + 64 B per mass (+ 24 B
+    # per mass of records when kept); backward: the replay with records (12 B per spring + 88 B
+    # per mass, none when the records are kept) and the reverse step (36 B per spring: parameters
+    # and sensitivity sums read and written; 136 B per mass: records and adjoints)
+    fwd_gbs = (12.0 * Ssum + (88.0 if records else 64.0) * Msum) * N / (fwd * 1e-3) / 1e9
+    bwd_gbs = ((36.0 if records else 48.0) * Ssum + (136.0 if records else 224.0) * Msum) * N / (bwd * 1e-3) / 1e9
+    kept = ", every step's record kept" if records else ""
     return {"workload": f"{P} robots {n}^3, occupancy 0.7, per-voxel parameters, {N} steps (sample of 5000), "
-                        f"checkpoints every {K}",
+                        f"checkpoints every {K}{kept}",
             "grads_per_s": P / ((fwd + bwd) * 1e-3), "forward_ms": fwd, "backward_ms": bwd,
             "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": fwd_gbs / peaks["hbm_gbs"]},
@@ -641,6 +647,7 @@ def run_case(args):
     else:
         P = args.robots if args.robots != P_ROBOTS else 16
         print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P)}))
+        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P, records=True)}))
 
 
 def main():

@@ -261,16 +261,16 @@ sim_status sim_set_checkpointing(voxsim_ctx* ctx, int32_t k_steps);
 
 /* Keep every step's record of the recorded run (on = 1) instead of only its checkpoints
  * (on = 0, the default).  While on and checkpointing is on (sim_set_checkpointing), each
- * sim_step_n call also stores, for every step and every grid corner of the robots on the
- * resident lattice kernel, the state before the update with its contact mode and the horizontal
- * spring force before contact (24 bytes per corner per step: n_steps x 24 B x the population's
- * grid corners, e.g. about 18 GB for 512 robots of 8x8x8 voxels over 2000 steps), and
- * sim_backward sweeps those records backwards in one pass without replaying the forward steps
- * (the same forward run and contact modes bit for bit, the same gradients up to the order of
- * the per-voxel atomic sums).  Streamed robots keep their checkpointed replay, and so does every
- * robot when the routing of robots to kernels has changed since the recorded call (a
- * sim_autotune in between).  A sim_step_n call that cannot allocate the records fails with
- * SIM_ENOMEM.  Changing the setting discards the recorded run; turning it off frees the records.
+ * sim_step_n call also stores, for every step and every grid corner, the state before the update
+ * with its contact mode and the horizontal spring force before contact (24 bytes per corner per
+ * step: n_steps x 24 B x the population's grid corners, e.g. about 18 GB for 512 robots of
+ * 8x8x8 voxels over 2000 steps), and sim_backward sweeps those records backwards in one pass
+ * without replaying the forward steps (the same forward run and contact modes bit for bit, the
+ * same gradients up to the order of the per-voxel atomic sums), for the robots on the resident
+ * lattice kernel and on the streamed path alike.  Records written under another routing of robots
+ * to kernels than the current one (a sim_autotune in between) are not used: the checkpoints are
+ * replayed instead.  A sim_step_n call that cannot allocate the records fails with SIM_ENOMEM.
+ * Changing the setting discards the recorded run; turning it off frees the records.
  * Errors: SIM_EINVAL (on not 0 or 1). */
 sim_status sim_set_trajectory_records(voxsim_ctx* ctx, int32_t on);
 

@@ -171,6 +171,7 @@ struct voxsim_ctx {
     int stream_graph_n = -1;
     const void* stream_graph_key = nullptr;   // buffers the graph was captured with
     const void* stream_graph_ckpt = nullptr;  // checkpoint buffer it writes (NULL: none)
+    const void* stream_graph_rec = nullptr;   // whole-trajectory record buffer it writes (NULL: none)
     int stream_graph_every = 0;
     void drop_graph()
     {
@@ -179,6 +180,7 @@ struct voxsim_ctx {
         stream_graph_n = -1;
         stream_graph_key = nullptr;
         stream_graph_ckpt = nullptr;
+        stream_graph_rec = nullptr;
         stream_graph_every = 0;
     }
     // device buffers
@@ -902,10 +904,14 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s, bool 
     a.robots = ctx->d_stream.p;
     a.n_robots = ctx->n_stream;
     const int K = record ? ctx->ckpt_every : 0;
+    const bool keep = record && ctx->keep_records;
     for (int i = 0; i < n; ++i) {
         // the state at the start of every K-th step goes to its segment's checkpoint
         a.ckpt_u = K > 0 && i % K == 0 ? ctx->d_ckpt_u.p + (size_t)(i / K) * ctx->M_cap : nullptr;
         a.ckpt_v = K > 0 && i % K == 0 ? ctx->d_ckpt_v.p + (size_t)(i / K) * ctx->M_cap : nullptr;
+        // and, when the whole trajectory is kept, every step's record
+        a.rec_u = keep ? ctx->d_trec_u.p + (size_t)i * ctx->M_cap : nullptr;
+        a.rec_f = keep ? ctx->d_trec_f.p + (size_t)i * ctx->M_cap : nullptr;
         a.u_in = (i & 1) ? ctx->d_x_alt.p : ctx->d_x.p;
         a.u_out = (i & 1) ? ctx->d_x.p : ctx->d_x_alt.p;
         a.v_in = (i & 1) ? ctx->d_v_alt.p : ctx->d_v.p;
@@ -932,8 +938,10 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n, bool record)
     cudaStream_t s = ctx->stream;
     const void* key = ctx->d_sc.p;   // the step table may move when it grows
     const void* ckpt = record ? (const void*)ctx->d_ckpt_u.p : nullptr;
+    const void* trec = record && ctx->keep_records ? (const void*)ctx->d_trec_u.p : nullptr;
     if (!(ctx->stream_graph && ctx->stream_graph_n == n && ctx->stream_graph_key == key &&
-          ctx->stream_graph_ckpt == ckpt && ctx->stream_graph_every == (record ? ctx->ckpt_every : 0))) {
+          ctx->stream_graph_ckpt == ckpt && ctx->stream_graph_rec == trec &&
+          ctx->stream_graph_every == (record ? ctx->ckpt_every : 0))) {
         ctx->drop_graph();
         if (!ctx->capture_stream) VX_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         VX_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -948,6 +956,7 @@ static sim_status step_streamed(voxsim_ctx* ctx, int n, bool record)
         ctx->stream_graph_n = n;
         ctx->stream_graph_key = key;
         ctx->stream_graph_ckpt = ckpt;
+        ctx->stream_graph_rec = trec;
         ctx->stream_graph_every = record ? ctx->ckpt_every : 0;
     }
     VX_CK(cudaGraphLaunch(ctx->stream_graph, s));
@@ -976,7 +985,7 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
         const int nseg = (n_steps + ctx->ckpt_every - 1) / ctx->ckpt_every;
         VX_CK(ctx->d_ckpt_u.ensure((size_t)nseg * ctx->M_cap));
         VX_CK(ctx->d_ckpt_v.ensure((size_t)nseg * ctx->M_cap));
-        if (ctx->keep_records && ctx->n_items > 0) {
+        if (ctx->keep_records) {
             VX_CK(ctx->d_trec_u.ensure((size_t)n_steps * ctx->M_cap));
             VX_CK(ctx->d_trec_f.ensure((size_t)n_steps * ctx->M_cap));
         }
@@ -995,7 +1004,7 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps)
     VX_CK(cudaEventRecord(ev[1], s));
     if (record) {
         ctx->rec_valid = true;
-        ctx->rec_full = ctx->keep_records && ctx->n_items > 0;
+        ctx->rec_full = ctx->keep_records;
         ctx->rec_items_version = ctx->items_version;
         ctx->rec_step0 = ctx->step;
         ctx->rec_n = n_steps;
@@ -1210,14 +1219,19 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
 static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
 {
     cudaStream_t s = ctx->stream;
-    const int K = ctx->ckpt_every, N = ctx->rec_n;
+    const bool full = ctx->records_usable();      // every step's record kept: no replay
+    const int N = ctx->rec_n, K = full ? N : ctx->ckpt_every;
     const size_t Mc = ctx->M_cap;
-    VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
-    VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+    if (!full) {
+        VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
+        VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+        VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_u1.ensure(Mc));
+        VX_CK(ctx->d_rep_v0.ensure(Mc)); VX_CK(ctx->d_rep_v1.ensure(Mc));
+    }
+    float4* const rec_u = full ? ctx->d_trec_u.p : ctx->d_srec_u.p;
+    float2* const rec_f = full ? ctx->d_trec_f.p : ctx->d_srec_f.p;
     VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
     VX_CK(ctx->d_slF0.ensure(Mc)); VX_CK(ctx->d_slF1.ensure(Mc));
-    VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_u1.ensure(Mc));
-    VX_CK(ctx->d_rep_v0.ensure(Mc)); VX_CK(ctx->d_rep_v1.ensure(Mc));
     VX_CK(ctx->d_sacc.ensure(39 * Mc));
     StreamAdjArgs b{};
     b.pv = ctx->view();
@@ -1253,7 +1267,7 @@ static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
         // replay from the checkpoint, recording every step
-        for (int i = 0; i < n1 - n0; ++i) {
+        for (int i = 0; i < n1 - n0 && !full; ++i) {
             f.u_in = i == 0 ? ctx->d_ckpt_u.p + (size_t)seg * Mc : ru[(i - 1) & 1];
             f.v_in = i == 0 ? ctx->d_ckpt_v.p + (size_t)seg * Mc : rv[(i - 1) & 1];
             f.u_out = ru[i & 1];
@@ -1266,11 +1280,11 @@ static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
         // part of the step before it
         for (int j = n1; j >= n0; --j) {
             b.step = j < n1 ? j : -1;
-            b.rec_u = j < n1 ? ctx->d_srec_u.p + (size_t)(j - n0) * Mc : nullptr;
+            b.rec_u = j < n1 ? rec_u + (size_t)(j - n0) * Mc : nullptr;
             b.lF_in = j < n1 ? lF[j & 1] : nullptr;
             const bool mass = j - 1 >= n0;
-            b.mrec_u = mass ? ctx->d_srec_u.p + (size_t)(j - 1 - n0) * Mc : nullptr;
-            b.mrec_f = mass ? ctx->d_srec_f.p + (size_t)(j - 1 - n0) * Mc : nullptr;
+            b.mrec_u = mass ? rec_u + (size_t)(j - 1 - n0) * Mc : nullptr;
+            b.mrec_f = mass ? rec_f + (size_t)(j - 1 - n0) * Mc : nullptr;
             b.lF_out = mass ? lF[(j - 1) & 1] : nullptr;
             VX_LAUNCH(ctx, launch_stream_adj_step(b, maxc, s));
         }
@@ -1311,7 +1325,7 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
     for (int seg = 0; seg < nseg; ++seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
         const float4* src = ctx->d_srec_u.p;
-        if (!streamed && ctx->records_usable()) {   // the forward kept every step's record
+        if (ctx->records_usable()) {           // the forward kept every step's record
             src = ctx->d_trec_u.p + (size_t)n0 * Mc;
         } else if (!streamed) {
             LatticeArgs f{};

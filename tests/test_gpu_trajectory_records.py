@@ -1,5 +1,6 @@
 """Whole-trajectory records (sim_set_trajectory_records): the forward keeps every step's record
-of the resident lattice robots in device memory and the backward sweeps it without replaying.
+in device memory (resident lattice and streamed robots) and the backward sweeps it without
+replaying.
 Against the checkpointed replay of the same run: the forward (fitness) and the contact modes are
 bitwise the same, the gradients the same up to the order of the per-voxel atomic sums
 (relative 1e-5 of the largest entry, as between checkpoint intervals); against the FP64
@@ -86,9 +87,8 @@ def test_records_match_oracle_adjoint(vs, orc):
 
 
 def test_records_repeatable_and_mixed_with_streamed_robots(vs):
-    """A population with lattice and streamed robots: the lattice robots sweep their records,
-    the streamed robot replays its checkpoints; a second backward on the same run gives the
-    scaled gradient; both equal the all-checkpointed run."""
+    """A population with lattice and streamed robots, both sweeping their records; a second
+    backward on the same run gives the scaled gradient; both equal the all-checkpointed run."""
     rng = np.random.default_rng(122)
     shapes = ((3, 3, 3), (9, 9, 9), (4, 3, 2))
     pop = W.make_population(shapes, [W.bernoulli_grid(rng, d, 0.8) for d in shapes])
@@ -96,6 +96,24 @@ def test_records_repeatable_and_mixed_with_streamed_robots(vs):
     fa, ga, _ = run(vs, pop, w, kappa, phi, 180, 50, False)
     fb, gb, _ = run(vs, pop, w, kappa, phi, 180, 50, True, repeat=2)
     assert np.array_equal(fa, fb)
+    for x, y in zip(ga[0], gb[0]):
+        assert close(y, x)
+    for g1, g2 in zip(gb[0], gb[1]):
+        assert close(g2, 2.0 * g1)
+
+
+def test_streamed_records_equal_checkpointed_replay(vs):
+    """Robots on the streamed path keep their records too (written by the streamed step kernel
+    during the forward run): the same forward, contact modes and gradients as the replay."""
+    rng = np.random.default_rng(125)
+    pop = W.population_bernoulli(3, (6, 5, 4), 0.8, seed=125)
+    w, kappa, phi = W.voxel_params(rng, pop)
+    fa, ga, ma = run(vs, pop, w, kappa, phi, 230, 60, False, modes_of=(0, 2), path=vs.PATH_STREAMED)
+    fb, gb, mb = run(vs, pop, w, kappa, phi, 230, 60, True, modes_of=(0, 2), repeat=2, path=vs.PATH_STREAMED)
+    assert np.array_equal(fa, fb)
+    for x, y in zip(ma, mb):
+        assert np.array_equal(x, y)
+        assert (x > 0).any()
     for x, y in zip(ga[0], gb[0]):
         assert close(y, x)
     for g1, g2 in zip(gb[0], gb[1]):
