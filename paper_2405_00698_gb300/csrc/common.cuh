@@ -148,9 +148,11 @@ struct LatticeArgs {
     const float2* sc;        // sin / cos of w t per step of this call
     int nsteps;
     StepConst c;
-    const int4* items;       // (first robot in item_robots, robots, threads per robot, 0)
+    const int4* items;       // (first robot in item_robots, robots, threads per robot, kind:
+                             // 0 per corner, 1 direction-compacted, 2 per corner split)
     const int* item_robots;
     int n_items;
+    int has_split;           // the items include split ones (run by the split instantiation)
     int* queue;              // work counter, zeroed before the launch
     // checkpoints for the adjoint (NULL when off): state at steps 0, K, 2K, ... of the call
     float4* ckpt_u;

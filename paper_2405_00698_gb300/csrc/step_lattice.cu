@@ -34,11 +34,17 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 // keeps its registers).  RECORD: the adjoint's replay of a checkpoint segment, which also writes
 // every step's state before the update with its contact mode, and the horizontal spring force
 // before contact.
-template <bool DAMPED, bool RECORD>
+// SPLIT (with dashpots): split items (item.w == 2: one robot of up to 384 corners alone in a
+// block, when the population leaves SMs idle) give every corner a second thread in another warp: the owner evaluates
+// directions 0..6, the helper directions 7..12 (writing their planes only), and after the
+// barrier the owner adds the helper's six plane entries in direction order before the backward
+// gather, so the sums are formed in the same order from the same values: the same bits as the
+// unsplit step, with the longest chain of spring evaluations per step cut from 13 to 7.
+template <bool DAMPED, bool RECORD, bool SPLIT>
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
-    __shared__ int sh_item[4];
+    __shared__ int sh_item[5];
     const int tid = threadIdx.x;
     const StepConst c = a.c;
     for (;;) {
@@ -47,6 +53,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             if (it < a.n_items) {
                 const int4 item = a.items[it];
                 sh_item[0] = item.x; sh_item[1] = item.y; sh_item[2] = item.z; sh_item[3] = 1;
+                sh_item[4] = item.w;
             } else {
                 sh_item[3] = 0;
             }
@@ -54,6 +61,9 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
         __syncthreads();
         if (!sh_item[3]) break;
         const int first = sh_item[0], count = sh_item[1], gthreads = sh_item[2];
+        // split groups only in the SPLIT instantiation (launched when the plan has some); the
+        // other instantiations run a split item as one unsplit group of 2 S threads
+        const bool split = SPLIT && sh_item[4] == 2;
         const int group = tid / gthreads, lt = tid % gthreads;
         __syncthreads();   // everyone has read the item before thread 0 may overwrite it
         if (group < count) {
@@ -62,37 +72,44 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
-            // shared-memory slot of this group (S = gthreads corners): u, then 13 force planes
-            const int S = gthreads;
+            // shared-memory slot of this group (S corners): u, then 13 force planes; a split
+            // group has 2 S threads, owners [0, S) and helpers [S, 2 S) (whole warps each)
+            const int S = split ? gthreads / 2 : gthreads;
+            const bool hlp = split && lt >= S;
+            const int li = hlp ? lt - S : lt;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
             float4* sv = su + S;               // velocities (read by spring dashpots)
             float4* fb = sv + S;               // plane d at fb + d * S: force on a of spring (a, d)
-            // thread lt owns the lt-th mass (ascending corner order: neighbouring threads touch
+            // thread li owns the li-th mass (ascending corner order: neighbouring threads touch
             // neighbouring shared-memory rows); threads past the mass count only take part in the
             // barriers
             const int M = a.pv.n_mass[r];
-            const bool in = lt < M;
-            const int cidx = in ? a.corner_order[mo + lt] : 0;
+            const bool in = li < M;
+            const int cidx = in ? a.corner_order[mo + li] : 0;
             const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
             float pk[13], pa[13], pb[13];
             const float* prm = a.prm + 39 * mo;
             for_each_dir([&](auto t) {
                 constexpr int d = decltype(t)::value;
-                const bool has = (fl >> d) & 1u;
+                const bool has = ((fl >> d) & 1u) && (!split || hlp == (d >= 7));
                 pk[d] = has ? prm[(0 * 13 + d) * C + cidx] : 0.f;
                 pa[d] = has ? prm[(1 * 13 + d) * C + cidx] : 0.f;
                 pb[d] = has ? prm[(2 * 13 + d) * C + cidx] : 0.f;
             });
             float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool mass = (fl >> 31) & 1u;
-            if (in) {
+            const bool mass = ((fl >> 31) & 1u) && !hlp;
+            if (in && !hlp) {
                 su[cidx] = u;
                 if (DAMPED) sv[cidx] = v;
             }
             group_sync(bar, gthreads);
             for (int n = 0; n < a.nsteps; ++n) {
-                if (a.ckpt_u && in && n % a.ckpt_every == 0) {   // state at the start of segment n / K
+                if (hlp && in) {                   // the owner's state after the previous step
+                    u = su[cidx];
+                    if (DAMPED) v = sv[cidx];
+                }
+                if (a.ckpt_u && in && !hlp && n % a.ckpt_every == 0) {   // state at the start of segment n / K
                     const int64_t o = (int64_t)(n / a.ckpt_every) * a.ckpt_stride + mo + cidx;
                     a.ckpt_u[o] = u;
                     a.ckpt_v[o] = v;
@@ -107,6 +124,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                 // 2.6 % more with the far end's load predicated off (u from the register).
                 if (in) for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
+                    if (split && hlp != (d >= 7)) return;   // the other thread's direction
                     const bool has = (fl >> d) & 1u;
                     if constexpr (DAMPED) {
                         // with dashpots an absent spring would also load a velocity and take a
@@ -126,8 +144,15 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     fb[d * S + cidx] = make_float4(e.gx, e.gy, e.gz, 0.f);
                 });
                 group_sync(bar, gthreads);
-                // phase B: backward springs (c - offset(d), c), then the mass update
-                for_each_dir([&](auto t) {
+                // phase B (owners): the helper's forward springs in direction order, then the
+                // backward springs (c - offset(d), c), then the mass update
+                if (split && in && !hlp) for_each_dir_in<7, 6>([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    if (!((fl >> d) & 1u)) return;
+                    const float4 g = fb[d * S + cidx];
+                    Fxy = __fadd2_rn(Fxy, make_float2(g.x, g.y)); Fz = __fadd_rn(Fz, g.z);
+                });
+                if (!hlp) for_each_dir([&](auto t) {
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> (16 + d)) & 1u)) return;
                     const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];   // force on a
@@ -148,7 +173,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                 }
                 group_sync(bar, gthreads);
             }
-            if (in) {
+            if (in && !hlp) {
                 a.u[mo + cidx] = u;
                 a.v[mo + cidx] = v;
             }
@@ -314,9 +339,10 @@ int lattice_max_threads() { return kMaxLatticeThreads; }
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
-    auto kernel = a.rec_u ? k_step_lattice<false, true>
+    auto kernel = a.rec_u ? k_step_lattice<false, true, false>
                 : a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
-                          : (a.c.damped ? k_step_lattice<true, false> : k_step_lattice<false, false>);
+                : a.c.damped ? (a.has_split ? k_step_lattice<true, false, true> : k_step_lattice<true, false, false>)
+                             : k_step_lattice<false, false, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<grid, threads, smem, s>>>(a);
