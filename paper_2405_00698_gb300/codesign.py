@@ -95,7 +95,8 @@ def param_bounds(V: int, device="cuda"):
 
 
 def rank_order(f: np.ndarray) -> np.ndarray:
-    """The genetic operators' ranking: fitness descending, index ascending on ties, NaN last."""
+    """The genetic operators' ranking: fitness descending, index ascending on ties, NaN counted as
+    -infinity (after every finite fitness, tied with -infinity by index)."""
     key = np.where(np.isnan(f), -np.inf, f)
     return np.argsort(-key, kind="stable")
 
