@@ -48,6 +48,30 @@ def test_streamed_equals_lattice_with_dashpots(vs):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+def test_split_groups_with_degenerate_robots(vs, orc):
+    """A population smaller than the SM count with dashpots runs its robots of up to 384 corners
+    as split groups (a helper thread per corner): an empty robot, one voxel, two equal
+    components, a rod, a 6x6x6 robot (343 corners: the largest split slot) and a 5x5x5 robot
+    against the oracle, and bitwise against the streamed path (which never splits)."""
+    rng = np.random.default_rng(99)
+    grids = [np.zeros((2, 2, 2), np.uint8), np.full((1, 1, 1), 4, np.uint8),
+             np.array([[[1, 0, 2]]], np.uint8), np.full((1, 1, 12), 3, np.uint8),
+             W.uniform_materials(rng, (6, 6, 6)), W.uniform_materials(rng, (5, 5, 5))]
+    pop = W.make_population([g.shape[::-1] for g in grids], grids)
+    out = []
+    for kw in ({}, {"path": 2}):
+        sim = vs.Simulator(PHYS, **kw)
+        sim.set_population_from(pop)
+        sim.step(1500)
+        out.append(sim.state() + (sim.fitness(),))
+        sim.close()
+    (x, v, off, f), (x2, v2, _, f2) = out
+    assert np.array_equal(x, x2) and np.array_equal(v, v2) and np.array_equal(f, f2)
+    assert f[0] == 0.0
+    ref = orc.run_population(pop, PHYS, 1500, want_x=True)
+    check_population(orc, pop, PHYS, 1500, f, x, off, ref)
+
+
 def test_paper_evolution_crossover_rate(vs, orc):
     import torch
     rng = np.random.default_rng(99)
