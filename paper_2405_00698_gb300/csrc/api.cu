@@ -42,6 +42,10 @@ namespace {
 
 sim_status cuda_fail(cudaError_t e, const char* what)
 {
+    // the error is returned to the caller, so it must not also stay pending in the runtime's
+    // last-error state, where the caller's next unrelated CUDA check would find it (a failed
+    // allocation leaves the context usable)
+    (void)cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }

@@ -120,6 +120,32 @@ def test_streamed_records_equal_checkpointed_replay(vs):
         assert close(g2, 2.0 * g1)
 
 
+def test_records_that_do_not_fit_fail_cleanly(vs):
+    """Records of 100,000 steps of 512 robots 8x8x8 would need ~900 GB: sim_step_n fails with
+    SIM_ENOMEM before stepping, no recorded run is left, and the context keeps working."""
+    import torch
+    pop = W.population_uniform(512, (8, 8, 8), seed=126)
+    sim = vs.Simulator(PHYS)
+    sim.set_checkpointing(100)
+    sim.set_trajectory_records(True)
+    sim.set_population_from(pop)
+    with pytest.raises(vs.VoxsimError) as err:
+        sim.step(100_000)
+    assert err.value.status == vs.SIM_ENOMEM
+    g = torch.empty(pop.mats.size, device="cuda")
+    with pytest.raises(vs.VoxsimError):
+        sim.backward(torch.ones(pop.P, dtype=torch.float64, device="cuda"), g, g, g)
+    sim.set_trajectory_records(False)
+    sim.step(50)
+    f = sim.fitness()
+    sim.close()
+    ref = vs.Simulator(PHYS)
+    ref.set_population_from(pop)
+    ref.step(50)
+    assert np.array_equal(f, ref.fitness())
+    ref.close()
+
+
 def test_switching_records_discards_the_recorded_run(vs):
     import torch
     pop = W.population_uniform(2, (3, 3, 3), seed=123)
