@@ -73,18 +73,26 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_step_cluster(ClusterArgs
         const float2 sc = a.sc[n];
         float2 Fxy = make_float2(0.f, 0.f);
         float Fz = 0.f;
-        // phase A: forward springs (c, c + offset(d))
-        for_each_dir([&](auto tg) {
+        // phase A: forward springs (c, c + offset(d)).  Without dashpots no branch per
+        // direction: an absent spring has zero parameters and the corner's own u as far end (its
+        // load predicated off), so its force is an exact zero that leaves the sums' bits
+        // unchanged, as in the one-block lattice kernel
+        if (in) for_each_dir([&](auto tg) {
             constexpr int d = decltype(tg)::value;
-            if (!((fl >> d) & 1u)) return;
+            const bool has = (fl >> d) & 1u;
+            if constexpr (DAMPED) {
+                if (!has) return;
+            }
             const int nb = cidx + lattice_offset<d>(X, XY);
-            float4 ub, vb;
-            if (lattice_dir(d, 2) == 1 && top) {
-                ub = su_next[nb - c1];
-                if (DAMPED) vb = sv_next[nb - c1];
-            } else {
-                ub = su[nb - c0];
-                if (DAMPED) vb = sv[nb - c0];
+            float4 ub = u, vb = v;
+            if (has) {
+                if (lattice_dir(d, 2) == 1 && top) {
+                    ub = su_next[nb - c1];
+                    if (DAMPED) vb = sv_next[nb - c1];
+                } else {
+                    ub = su[nb - c0];
+                    if (DAMPED) vb = sv[nb - c0];
+                }
             }
             SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z), a.c.edge,
                                               lattice_rest<d>(a.c), lattice_rest_sq<d>(a.c), pk[d], pa[d], pb[d],
