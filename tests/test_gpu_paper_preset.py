@@ -72,6 +72,26 @@ def test_split_groups_with_degenerate_robots(vs, orc):
     check_population(orc, pop, PHYS, 1500, f, x, off, ref)
 
 
+def test_split_and_unsplit_groups_in_one_launch(vs, orc):
+    """With dashpots and few robots, robots of up to 384 corners run split while an 8x8x8 robot
+    (729 corners) runs unsplit in the same launch of the split instantiation: bitwise against the
+    streamed path and against the oracle."""
+    rng = np.random.default_rng(100)
+    shapes = [(8, 8, 8), (5, 5, 5), (3, 4, 2)]
+    pop = W.make_population(shapes, [W.uniform_materials(rng, d) for d in shapes])
+    out = []
+    for kw in ({}, {"path": 2}):
+        sim = vs.Simulator(PHYS, **kw)
+        sim.set_population_from(pop)
+        sim.step(800)
+        out.append(sim.state() + (sim.fitness(),))
+        sim.close()
+    (x, v, off, f), (x2, v2, _, f2) = out
+    assert np.array_equal(x, x2) and np.array_equal(v, v2) and np.array_equal(f, f2)
+    ref = orc.run_population(pop, PHYS, 800, want_x=True)
+    check_population(orc, pop, PHYS, 800, f, x, off, ref)
+
+
 def test_paper_evolution_crossover_rate(vs, orc):
     import torch
     rng = np.random.default_rng(99)
