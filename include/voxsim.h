@@ -157,11 +157,12 @@ typedef struct voxsim_ctx voxsim_ctx;
  * NULL out pointer or non-positive dt / mass / edge, SIM_ECUDA if the device cannot be used. */
 sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, voxsim_ctx** out);
 
-/* Release every device buffer of the context (synchronises its stream first).  NULL is a no-op. */
+/* Release every device buffer of the context (synchronises its stream first) and the context
+ * itself, which must not be used afterwards.  NULL is a no-op.  Always returns SIM_OK. */
 sim_status sim_destroy(voxsim_ctx* ctx);
 
 /* Message of the most recent failed call on this thread ("" if none).  Valid until the next
- * call on this thread. */
+ * call on this thread.  ctx may be NULL (the message is per thread, not per context). */
 const char* sim_last_error(const voxsim_ctx* ctx);
 
 /* Replace the population: P robots, robot r on a dims[3r] x dims[3r+1] x dims[3r+2] voxel grid
@@ -189,7 +190,8 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
 /* Fitness of every robot: centroid displacement along +x since the initial pose (the paper
  * names "fitness", Section III; the displacement is the workloads' definition), reduced in
  * FP64.  Empty robots score 0; a robot with a non-finite coordinate, or one beyond dead_bound,
- * scores -infinity.  out: double [P] in `mem`. */
+ * scores -infinity.  out: double [P] in `mem` (host: the call synchronises the stream).
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL for a NULL out, SIM_ECUDA. */
 sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
 
 /* One generation of the evolutionary step, fully on the GPU (Section II-C; Table I):
@@ -328,25 +330,29 @@ sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs
 
 /* Current state: positions and velocities (float32 [total masses][3], robots in order, masses
  * in ascending corner order); mass_offsets: int32 [P+1] prefix offsets (host) or NULL.  Any
- * output may be NULL.  mem applies to x_out and v_out. */
+ * output may be NULL.  mem applies to x_out and v_out.  Synchronises the stream.
+ * Errors: SIM_ESTATE without a population, SIM_ENOMEM, SIM_ECUDA. */
 sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* mass_offsets,
                          int32_t mem);
 
 /* Decoded voxels before / after the largest-component filter and the per-voxel parameters
- * actually simulated (host arrays over all voxels; any may be NULL). */
+ * actually simulated (host arrays over all voxels; any may be NULL).  Synchronises the stream.
+ * Errors: SIM_ESTATE without a population, SIM_ECUDA. */
 sim_status sim_get_voxels(voxsim_ctx* ctx, uint8_t* mat_decoded, uint8_t* mat_kept, float* w,
                           float* kappa, float* phi);
 
 /* Topology (host arrays, robots concatenated, sized by sim_get_counts): mass_corner int32 per
  * mass; spring_ab int32 [springs][2] (mass indices within the robot, a < b, sorted by (a, b));
  * spring_params float [springs][4] = rest length, stiffness, alpha, beta with the actuated rest
- * length L0 (1 + alpha sin(w t) + beta cos(w t)).  Any may be NULL. */
+ * length L0 (1 + alpha sin(w t) + beta cos(w t)).  Any may be NULL.  Synchronises the stream.
+ * Errors: SIM_ESTATE without a population, SIM_ENOMEM, SIM_ECUDA. */
 sim_status sim_get_topology(voxsim_ctx* ctx, int32_t* mass_corner, int32_t* spring_ab,
                             float* spring_params);
 
 /* Since the last call: cumulative device time of the time-stepping kernels (milliseconds,
  * CUDA events on the context's stream) and the number of kernels the library launched (all
- * entry points).  Synchronises the stream and resets both. */
+ * entry points).  Synchronises the stream and resets both.  Either output may be NULL.
+ * Errors: SIM_EINVAL for a NULL context, SIM_ECUDA. */
 sim_status sim_get_timing(voxsim_ctx* ctx, double* step_ms, int64_t* launches);
 
 #ifdef __cplusplus
