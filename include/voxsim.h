@@ -182,7 +182,9 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
 /* Advance every robot by n_steps time steps (Section II-C: each spring's force with its
  * sinusoidal rest-length actuation, accumulation onto masses, gravity, ground contact with
  * static / kinetic friction, semi-implicit Euler with velocity damping; Table II).  Time of
- * step n is n * dt from the last sim_set_population.  When checkpointing is on
+ * step n is n * dt from the last sim_set_population.  Kinetic friction removes mu_k F_n along
+ * the horizontal force but never more than that force (with Table II's mu_s < mu_k it would
+ * otherwise reverse it).  When checkpointing is on
  * (sim_set_checkpointing), the call records the states the adjoint needs.
  * Errors: SIM_ESTATE without a population, SIM_EINVAL for n_steps < 0. */
 sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
@@ -291,8 +293,10 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
 
 /* Contact mode of every corner of robot `robot` at every step of the most recent recorded
  * sim_step_n call (checkpointing on): out[n * C + c] for step n and grid corner c of the robot's
- * C corners, 0 = free (or no mass at that corner), 1 = stuck, 2 = slipping (Section II-C,
- * Table II: ground contact with static and kinetic friction).  The checkpoint segments are
+ * C corners, 0 = free (or no mass at that corner), 1 = stuck, 2 = slipping, 3 = slipping with
+ * the kinetic friction saturated (mu_k F_n >= |F_h|, possible only when mu_k > mu_s as in
+ * Table II: the horizontal force is cancelled, never reversed) (Section II-C, Table II: ground
+ * contact with static and kinetic friction).  The checkpoint segments are
  * replayed bit-identically to read them.  out: host uint8 [n_steps][C].  Synchronises the
  * stream.  Errors: SIM_ESTATE without a recorded run, SIM_EINVAL. */
 sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out);

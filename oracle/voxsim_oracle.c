@@ -485,8 +485,9 @@ void orc_robot_set_state(orc_robot* R, const double* x, const double* v, long st
 /* Time stepping (Section II-C: per-spring and per-mass updates; Table II constants).           */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Contact mode of one mass in one step: 0 no contact, 1 stick, 2 slip. */
-enum { ORC_FREE = 0, ORC_STICK = 1, ORC_SLIP = 2 };
+/* Contact mode of one mass in one step: 0 no contact, 1 stick, 2 slip, 3 slip with the kinetic
+ * friction saturated (mu_k F_n >= |F_h|: the horizontal force is cancelled, the velocity kept). */
+enum { ORC_FREE = 0, ORC_STICK = 1, ORC_SLIP = 2, ORC_SLIP_HELD = 3 };
 
 /* One time step of one robot at time t = step * dt.
  *  1. every mass starts from its weight (0, 0, -m g);
@@ -500,14 +501,17 @@ enum { ORC_FREE = 0, ORC_STICK = 1, ORC_SLIP = 2 };
  *     F_n = k_ground (-z) added to F_z (and, with a ground damping ratio zeta_g > 0, the dashpot
  *     -2 zeta_g sqrt(k_ground m) v_z); with F_h = (F_x, F_y): if |F_h| <= mu_s F_n the mass
  *     sticks (F_h = 0 and horizontal velocity = 0), otherwise it slips and kinetic friction
- *     mu_k F_n is removed along F_h;
+ *     mu_k F_n is removed along F_h, never more than |F_h| itself: Table II prints
+ *     mu_s = 0.6 < mu_k = 1.0, and with mu_s F_n < |F_h| < mu_k F_n the full kinetic term would
+ *     reverse the horizontal force; the reading taken is that friction at most cancels it
+ *     (mode 3: F_h = 0, the velocity kept);
  *  4. semi-implicit Euler with velocity damping: v <- c (v + dt F / m), x <- x + dt v.
  * modes (optional, M entries) records the contact mode of every mass and Fpre (optional, 3M)
  * the force before the contact step.  force (optional, M entries) imposes the contact mode of
  * every mass instead of deciding it from the state: free adds no ground force; stick and slip
  * add F_n = k_ground (-z) whatever the sign of z and then zero the horizontal force and velocity
- * (stick) or remove mu_k F_n along F_h (slip) -- the same piecewise formulas, selected from
- * outside (used to difference the step map along another run's contact decisions).  Returns the
+ * (stick), remove mu_k F_n along F_h (slip) or zero the horizontal force only (saturated slip)
+ * -- the same piecewise formulas, selected from outside (used to difference the step map along another run's contact decisions).  Returns the
  * number of springs skipped for zero length. */
 static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes, double* Fpre,
                     const uint8_t* force)
@@ -550,6 +554,9 @@ static int orc_step(orc_robot* R, const orc_params* p, double* F, uint8_t* modes
             if (force ? force[m] == ORC_STICK : fh <= p->mu_s * fn) {
                 mode = ORC_STICK;
                 f[0] = 0.0; f[1] = 0.0; v[0] = 0.0; v[1] = 0.0;
+            } else if (force ? force[m] == ORC_SLIP_HELD : p->mu_k * fn >= fh) {
+                mode = ORC_SLIP_HELD;             /* kinetic friction cancels F_h exactly */
+                f[0] = 0.0; f[1] = 0.0;
             } else {
                 mode = ORC_SLIP;
                 double scale = 1.0 - p->mu_k * fn / fh;
@@ -837,6 +844,11 @@ double orc_robot_adjoint(int nx, int ny, int nz, const uint8_t* mat, const doubl
             } else if (md[m] == ORC_STICK) {
                 lF[3 * m + 0] = 0.0; lF[3 * m + 1] = 0.0; lF[3 * m + 2] = lFt[2];
                 lv[3 * m + 0] = 0.0; lv[3 * m + 1] = 0.0; lv[3 * m + 2] = lvt[2];
+                lx[3 * m + 2] += lFt[2] * (-p->k_ground);
+            } else if (md[m] == ORC_SLIP_HELD) {
+                /* F_h cancelled, velocity kept: only the normal force depends on the state */
+                lF[3 * m + 0] = 0.0; lF[3 * m + 1] = 0.0; lF[3 * m + 2] = lFt[2];
+                for (int q = 0; q < 3; ++q) lv[3 * m + q] = lvt[q];
                 lx[3 * m + 2] += lFt[2] * (-p->k_ground);
             } else {
                 double fn = p->k_ground * (-xn[3 * m + 2]);

@@ -30,6 +30,11 @@ __device__ __forceinline__ void mass_adjoint(unsigned mode, float z, float2 fh, 
         lFx = 0.f; lFy = 0.f; lFz = fz;
         lvx = 0.f; lvy = 0.f; lvz = tz;
         luz += -c.k_ground * fz;
+    } else if (mode == kSlipHeld) {
+        // saturated kinetic friction: the horizontal force was cancelled, the velocity kept
+        lFx = 0.f; lFy = 0.f; lFz = fz;
+        lvx = tx; lvy = ty; lvz = tz;
+        luz += -c.k_ground * fz;
     } else {
         // slip: F~_h = F_h (1 - mu_k F_n / |F_h|), F~_z = F_z + F_n
         const float fn = c.k_ground * -z;

@@ -159,15 +159,18 @@ __device__ __forceinline__ void spring_dashpot(SpringEval& e, float dvx, float d
     e.gz = __fmaf_rn(fd, e.dz, e.gz);
 }
 
-// Contact modes of a mass in one step.
-enum : unsigned { kFree = 0u, kStick = 1u, kSlip = 2u };
+// Contact modes of a mass in one step (kSlipHeld: slipping with the kinetic friction saturated at
+// the horizontal force it opposes).
+enum : unsigned { kFree = 0u, kStick = 1u, kSlip = 2u, kSlipHeld = 3u };
 
 // Gravity, ground contact with static / kinetic friction, and the semi-implicit Euler update of
 // one mass, given the summed spring force F.  Returns the contact mode.
 //   below the ground (z = z0 + uz < 0): normal force F_n = k_g (-z) added to F_z (and the ground
 //   dashpot -c_g v_z of the paper's preset); with
 //   F_h = (F_x, F_y): stick (|F_h| <= mu_s F_n) zeroes F_h and the horizontal velocity, slip
-//   removes mu_k F_n along F_h;
+//   removes mu_k F_n along F_h but never more than |F_h| (with Table II's mu_s = 0.6 < mu_k = 1.0
+//   a full kinetic term could reverse F_h; when mu_k F_n >= |F_h| the horizontal force is
+//   cancelled and the velocity kept);
 //   v <- c (v + dt F / m), u <- u + dt v.
 __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, float Fy, float Fz,
                                                 const StepConst& c)
@@ -184,10 +187,16 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
             mode = kStick;
             Fx = 0.f; Fy = 0.f; v.x = 0.f; v.y = 0.f;
         } else {
-            mode = kSlip;
-            const float s = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(c.mu_k, fn), fh));
-            Fx = __fmul_rn(Fx, s);
-            Fy = __fmul_rn(Fy, s);
+            const float r = __fdiv_rn(__fmul_rn(c.mu_k, fn), fh);
+            if (r >= 1.0f) {
+                mode = kSlipHeld;
+                Fx = 0.f; Fy = 0.f;
+            } else {
+                mode = kSlip;
+                const float s = __fsub_rn(1.0f, r);
+                Fx = __fmul_rn(Fx, s);
+                Fy = __fmul_rn(Fy, s);
+            }
         }
     }
     v.x = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fx, v.x));

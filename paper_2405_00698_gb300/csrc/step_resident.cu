@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
                     if (fh <= c.mu_s * fn) {
                         fx = 0.f; fy = 0.f; v.x = 0.f; v.y = 0.f;
                     } else {
-                        const float s2 = 1.0f - c.mu_k * fn / fh;
+                        // kinetic friction removes at most |F_h| (saturated: F_h cancelled)
+                        const float r = c.mu_k * fn / fh;
+                        const float s2 = r >= 1.0f ? 0.0f : 1.0f - r;
                         fx *= s2; fy *= s2;
                     }
                 }

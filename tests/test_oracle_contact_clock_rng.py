@@ -222,3 +222,35 @@ def test_rng_draws_are_splitmix64_outputs(orc, seed, outputs):
     generation 0, child 0, gene 0 with purposes 0..4."""
     for n, out in enumerate(outputs):
         assert orc.rng_draw(seed, 0, 0, 0, n) == out >> 32, n
+
+
+# Table II prints mu_s = 0.6 below mu_k = 1.0.  A corner with mu_s F_n < |F_h| < mu_k F_n then
+# slips, and a kinetic friction of mu_k F_n would exceed the force it opposes and reverse it.
+# The reading taken: kinetic friction removes at most |F_h| (the slipping corner keeps its
+# velocity, the horizontal force drops to zero), i.e. F_h <- F_h - min(mu_k F_n, |F_h|) F_h / |F_h|.
+@pytest.mark.parametrize("shear", [(0.004, 0.0), (0.003, -0.002)])
+@pytest.mark.parametrize("ratio", [0.4, 0.8, 1.5])
+def test_paper_friction_never_reverses_the_horizontal_force(orc, shear, ratio):
+    phys = W.PAPER
+    assert phys.mu_s < phys.mu_k
+    mat = 4
+    k = phys.k_mat[mat]
+    v0 = (0.02, -0.01)      # a uniform drift: no dashpot force, but stick and slip differ
+    r, x0, x, v, bottom = sheared_cube(orc, phys, mat, shear, 0.0, v0)
+    F = hooke_forces(x, x0, k)
+    fh_max = max(math.hypot(*F[i, :2]) for i in range(8) if bottom[i])
+    p = fh_max / (phys.k_ground * ratio)
+    r, x0, x, v, bottom = sheared_cube(orc, phys, mat, shear, p, v0)
+    F = hooke_forces(x, x0, k)
+    v1_ref, regimes = friction_expectation(phys, F, v, p, bottom, phys.mu_s, phys.mu_k, clamp=True)
+    assert all(abs(q - phys.mu_s) > 1e-6 and abs(q - phys.mu_k) > 1e-6 for _, q in regimes.values())
+    r.simulate(1)
+    _, v1 = r.state()
+    assert np.allclose(v1, v1_ref, rtol=0, atol=1e-12)
+    for i, (kind, q) in regimes.items():
+        dv = v1[i, :2] - v[i, :2]
+        if kind == "slip":
+            # the horizontal velocity change never points against the spring force
+            assert dv @ F[i, :2] >= -1e-15
+            if q < phys.mu_k:                    # saturated: no horizontal force at all
+                assert np.array_equal(v1[i, :2], v[i, :2] * phys.damping)
