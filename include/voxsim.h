@@ -193,7 +193,8 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
  * names "fitness", Section III; the displacement is the workloads' definition), reduced in
  * FP64.  Empty robots score 0; a robot with a non-finite coordinate, or one beyond dead_bound,
  * scores -infinity.  out: double [P] in `mem` (host: the call synchronises the stream).
- * Errors: SIM_ESTATE without a population, SIM_EINVAL for a NULL out, SIM_ECUDA. */
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL for a NULL out or a `mem` other than
+ * SIM_MEM_HOST / SIM_MEM_DEVICE, SIM_ECUDA. */
 sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
 
 /* One generation of the evolutionary step, fully on the GPU (Section II-C; Table I):
@@ -216,10 +217,11 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
                           uint64_t generation, int32_t* parents_out, uint8_t* mask_out);
 
 /* evo_generation without any device allocation, for callers that cannot call cudaMalloc: a
- * serving or control process whose memory pool already owns the whole device, code that must not
- * allocate once its loop is running, or work being recorded into a CUDA graph (an allocation
- * would synchronise the device or be refused).  The paper has no counterpart; it is the same
- * operation as evo_generation (same kernels, same results) with two differences:
+ * serving or control process whose memory pool already holds the whole device (another
+ * cudaMalloc would fail), or code that must not allocate once its loop is running (cudaMalloc
+ * and cudaFree can synchronise the device and stall the loop).  The paper has no counterpart; it
+ * is the same operation as evo_generation (same kernels, same results bit for bit) with two
+ * differences:
  *   - it needs no context: the caller passes the CUDA stream (NULL = legacy default stream) and
  *     the work runs on the current device;
  *   - its only scratch (the rank order of the population) is a fixed device array of 16384
@@ -230,7 +232,10 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
  * all the entries it reads, so nothing needs clearing); calls that overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture.  Errors as for evo_generation. */
+ * current) and keeps it for the life of the process; make that first call before any stream
+ * capture.  The kept address does not survive cudaDeviceReset (the array may come back at
+ * another address): a process that resets a device must not call this entry point on that
+ * device afterwards.  Errors as for evo_generation. */
 sim_status evo_generation_static(const double* fitness, const float* genomes_in,
                                  float* genomes_out, int32_t P, int32_t G, const evo_params* e,
                                  uint64_t generation, int32_t* parents_out, uint8_t* mask_out,
@@ -335,7 +340,8 @@ sim_status sim_get_counts(voxsim_ctx* ctx, int32_t* n_masses, int32_t* n_springs
 /* Current state: positions and velocities (float32 [total masses][3], robots in order, masses
  * in ascending corner order); mass_offsets: int32 [P+1] prefix offsets (host) or NULL.  Any
  * output may be NULL.  mem applies to x_out and v_out.  Synchronises the stream.
- * Errors: SIM_ESTATE without a population, SIM_ENOMEM, SIM_ECUDA. */
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL for an unknown `mem`, SIM_ENOMEM,
+ * SIM_ECUDA. */
 sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* mass_offsets,
                          int32_t mem);
 

@@ -1033,6 +1033,7 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem)
     if (sim_status st = check_ctx(ctx)) return st;
     if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
     if (ctx->P > 0 && !out) return fail(SIM_EINVAL, "null output");
+    if (mem != SIM_MEM_HOST && mem != SIM_MEM_DEVICE) return fail(SIM_EINVAL, "bad mem %d", mem);
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     double* dst = mem == SIM_MEM_DEVICE ? out : ctx->d_fit.p;
@@ -1560,6 +1561,7 @@ sim_status sim_get_state(voxsim_ctx* ctx, float* x_out, float* v_out, int32_t* m
 {
     if (sim_status st = check_ctx(ctx)) return st;
     if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    if (mem != SIM_MEM_HOST && mem != SIM_MEM_DEVICE) return fail(SIM_EINVAL, "bad mem %d", mem);
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
     const int P = ctx->P;
