@@ -165,6 +165,15 @@ sim_status sim_destroy(voxsim_ctx* ctx);
  * call on this thread.  ctx may be NULL (the message is per thread, not per context). */
 const char* sim_last_error(const voxsim_ctx* ctx);
 
+/* The device status words that sim_set_population's kernels raise, mapped to the status and
+ * message the call returns: words[1] bit 2 (a bounded wait of the tensor-core MLP query gave up;
+ * the kernel drains its copies and MMAs before it frees its tensor memory) and words[0] bit 0 (the
+ * component labelling hit its iteration bound) give SIM_ETIMEOUT, words[0] bit 1 (a material
+ * id out of range in device-memory genomes) SIM_EINVAL, none SIM_OK.  words: host int32 [4].
+ * Needs no device: it lets a caller (and the test-suite) check the mapping without making a
+ * device-side wait run out.  The paper has no counterpart.  Errors: SIM_EINVAL for NULL. */
+sim_status sim_check_status_words(const int32_t* words);
+
 /* Replace the population: P robots, robot r on a dims[3r] x dims[3r+1] x dims[3r+2] voxel grid
  * (each 1..64; host array).  Voxel (i, j, k) of robot r is entry i + nx*(j + ny*k) of its grid,
  * grids concatenated in robot order.  Decoding by `mode` (see SIM_MODE_*); for SIM_MODE_MLP
@@ -175,7 +184,9 @@ const char* sim_last_error(const voxsim_ctx* ctx);
  * ci + (nx+1)*(cj + (ny+1)*ck)); springs join the 28 corner pairs of every kept voxel, one
  * spring per distinct pair, with stiffness and actuation terms averaged over the kept voxels
  * that share it; the initial pose is the lattice at rest with its lowest mass at z = 0, and the
- * step counter restarts at 0.  Errors: SIM_EINVAL (sizes, mode, pointers), SIM_ENOMEM. */
+ * step counter restarts at 0.  Errors: SIM_EINVAL (sizes, mode, pointers, material ids out
+ * of range), SIM_ENOMEM, SIM_ETIMEOUT (a bounded device-side wait or iteration of the decode or
+ * topology kernels gave up, see sim_check_status_words). */
 sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, int32_t mode,
                               const void* genomes, const float* B, int32_t mem);
 

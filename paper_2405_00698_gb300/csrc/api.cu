@@ -312,6 +312,21 @@ sim_status copy_out(void* dst, const void* src, size_t bytes, int mem, cudaStrea
     return SIM_OK;
 }
 
+// Status words the decode and topology kernels raise (device int32 [4], zeroed per population):
+//   word 0 bit 0: the component labelling of a robot hit its iteration bound;
+//   word 0 bit 1: a material id of device-memory genomes was out of range (decoded as empty);
+//   word 1 bit 2: a bounded wait of the tensor-core MLP query gave up (the CTA aborted).
+sim_status status_from_words(const int32_t* w)
+{
+    if (w[1] & 4)
+        return fail(SIM_ETIMEOUT, "MLP query: a bounded wait on the tensor-core pipeline gave up "
+                                  "(copies and MMAs drained, decoded materials invalid)");
+    if (w[0] & 1)
+        return fail(SIM_ETIMEOUT, "topology: the component labelling hit its iteration bound");
+    if (w[0] & 2) return fail(SIM_EINVAL, "material id out of range 0..4 in device genomes");
+    return SIM_OK;
+}
+
 __global__ void k_spring_keys(const int* ns, int P, double* keys)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -323,6 +338,12 @@ __global__ void k_spring_keys(const int* ns, int P, double* keys)
 extern "C" {
 
 const char* sim_last_error(const voxsim_ctx*) { return g_err.c_str(); }
+
+sim_status sim_check_status_words(const int32_t* words)
+{
+    if (!words) return fail(SIM_EINVAL, "null status words");
+    return status_from_words(words);
+}
 
 sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, voxsim_ctx** out)
 {
@@ -535,7 +556,10 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         ctx->spring_count.assign(P, 0);
         VX_CK(cudaMemcpyAsync(ctx->mass_count.data(), ctx->d_nm.p, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
         VX_CK(cudaMemcpyAsync(ctx->spring_count.data(), ctx->d_ns.p, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        int32_t words[4] = {0, 0, 0, 0};
+        VX_CK(cudaMemcpyAsync(words, ctx->d_status.p, sizeof(words), cudaMemcpyDeviceToHost, s));
         VX_CK(cudaStreamSynchronize(s));
+        if (sim_status st = status_from_words(words)) return st;
         if (sim_status st = build_work_items(ctx)) return st;
     }
     ctx->step = 0;

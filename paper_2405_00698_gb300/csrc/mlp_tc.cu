@@ -126,6 +126,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, Smem& s
     return false;
 }
 
+// Bounded wait on an mbarrier phase that ignores the abort flag: after an abort, the issuing
+// thread waits (again at most kSpinLimit polls) for the copy or MMA it still has in flight before
+// the CTA frees its tensor memory and exits.  Returns whether the phase completed.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t phase)
+{
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
 {
     asm volatile(
@@ -257,8 +267,13 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
     uint32_t tma_phase[2] = {0, 0}, mma_phase = 0;
     constexpr uint32_t id_h = idesc_bf16(kTileM, kHidden);
     constexpr uint32_t id_o = idesc_bf16(kTileM, kW3Rows);
+    // issuing thread only: the TMA batch and the MMA commit whose completion it has not yet
+    // observed (at most one of each: nothing new is issued once the CTA has aborted)
+    bool tma_out = false, mma_out = false;
+    uint32_t tma_out_phase = 0, mma_out_phase = 0;
+    bool stop = false;
 
-    for (int g = blockIdx.x; g < P; g += gridDim.x) {
+    for (int g = blockIdx.x; g < P && !stop; g += gridDim.x) {
         const float* G = genomes + (size_t)g * kGenome;
         load_weights(G + kOffW1, kHidden, kPeDim, kHidden, s.w1);
         load_weights(G + kOffW2, kHidden, kHidden, kHidden, s.w2);
@@ -276,10 +291,13 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                 mbar_expect_tx(&s.tma_bar[0], kABytes);
                 for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
                     tma_load_2d(s.a[0] + kb * kTileM * 128, &pe_map, &s.tma_bar[0], kb * kKBlock, t * kTileM);
+                tma_out = true;
+                tma_out_phase = tma_phase[0];
             }
             // layer 1: D1 = gamma_tile . W1^T  (K = 256: 4 swizzle blocks x 4 steps of 16)
-            if (tid == 0) {
+            if (tid == 0 && tma_out) {
                 if (mbar_wait(&s.tma_bar[cur], tma_phase[cur], s, status)) {
+                    tma_out = false;
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(s.a[cur]), b0 = smem_u32(s.w1);
 #pragma unroll
@@ -289,12 +307,14 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                         umma(t_d1, sw128_desc(a0 + ao), sw128_desc(b0 + bo), id_h, k > 0);
                     }
                     umma_commit(&s.mma_bar);
+                    mma_out = true;
+                    mma_out_phase = mma_phase;
                 }
             }
             tma_phase[cur] ^= 1;
             const int row = warp * 32 + lane;
             // epilogue 1 -> H
-            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            if (mbar_wait(&s.mma_bar, mma_phase, s, status) && tid == 0) mma_out = false;
             mma_phase ^= 1;
             tc_fence_after();
             if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, s.a[0], row);
@@ -309,8 +329,10 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                 for (int k = 0; k < kHidden / 16; ++k)
                     umma(t_d2, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_h, k > 0);
                 umma_commit(&s.mma_bar);
+                mma_out = true;
+                mma_out_phase = mma_phase;
             }
-            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            if (mbar_wait(&s.mma_bar, mma_phase, s, status) && tid == 0) mma_out = false;
             mma_phase ^= 1;
             tc_fence_after();
             if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, s.a[0], row);
@@ -325,8 +347,10 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                 for (int k = 0; k < kHidden / 16; ++k)
                     umma(t_d3, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_o, k > 0);
                 umma_commit(&s.mma_bar);
+                mma_out = true;
+                mma_out_phase = mma_phase;
             }
-            mbar_wait(&s.mma_bar, mma_phase, s, status);
+            if (mbar_wait(&s.mma_bar, mma_phase, s, status) && tid == 0) mma_out = false;
             mma_phase ^= 1;
             tc_fence_after();
             if (!s.abort) {
@@ -350,8 +374,16 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                 }
             }
             tc_fence_before();
-            __syncthreads();
+            // one decision for the whole CTA: after an abort no thread touches the tiles again
+            if (__syncthreads_or(s.abort)) { stop = true; break; }
         }
+    }
+    // after an abort the issuing thread first waits (bounded) for its copy and MMA still in
+    // flight, so the tensor memory is not freed under an MMA and no copy lands in the shared
+    // memory of an exited CTA
+    if (tid == 0 && stop) {
+        if (tma_out) mbar_drain(&s.tma_bar[0], tma_out_phase);
+        if (mma_out) mbar_drain(&s.mma_bar, mma_out_phase);
     }
     tc_fence_before();
     __syncthreads();

@@ -26,7 +26,7 @@ GENOME_LEN = 20998
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
            "sim_set_trajectory_records", "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
-           "sim_get_timing")
+           "sim_get_timing", "sim_check_status_words")
 
 
 class VoxsimError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
             "sim_get_voxels": [vp, vp, vp, vp, vp, vp],
             "sim_get_topology": [vp, vp, vp, vp],
             "sim_get_timing": [vp, vp, vp],
+            "sim_check_status_words": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
