@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the voxel soft-robot co-design hot path on GB300.
 
-One bench step = one full co-design generation of the MLP-encoded population: positional
-encoding + MLP spatial query of 1024 genomes on an 8x8x8 grid, largest component, topology,
-10,000 time steps of every robot, FP64 fitness, then elite selection / crossover / mutation of
-the 1024 x 20,998 weight matrix, all on the GPU.  Prints one JSON line (rank 0).
+One bench step = the MLP-encoded population's whole run: 10 co-design generations from the
+seeded population, each one positional encoding + MLP spatial query of 1024 genomes on an 8x8x8
+grid, largest component, topology, 10,000 time steps of every robot, FP64 fitness, then elite
+selection / crossover / mutation of the 1024 x 20,998 weight matrix, all on the GPU.  Every step
+starts from the same seeded genomes, so the timed work does not depend on --steps or --warmup.
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,10 +34,10 @@ sys.path.insert(0, ROOT)
 from paper_2405_00698_gb300 import workloads as W  # noqa: E402
 
 METRIC = "spring-updates/s"
-WORKLOAD = dict(workload="mlp-encoded population: 1024 genomes, 8x8x8 grid, 10,000 steps per "
-                "generation, 1 generation per step", robots=1024, grid=[8, 8, 8], sim_steps=10000,
-                genome=W.GENOME_LEN)
-P_ROBOTS, GRID, SIM_STEPS = 1024, (8, 8, 8), 10000
+WORKLOAD = dict(workload="mlp-encoded population: 1024 genomes, 8x8x8 grid, 10 generations of "
+                "10,000 steps from the seeded population per step", robots=1024, grid=[8, 8, 8],
+                sim_steps=10000, genome=W.GENOME_LEN)
+P_ROBOTS, GRID, SIM_STEPS, GENERATIONS = 1024, (8, 8, 8), 10000, 10
 SMEM_PEAK_NOTE = "152 SMs x 128 B/clk x 2.07 GHz (unit counts and maximum SM clock)"
 SMEM_PEAK_GBS = 152 * 128 * 2.07
 # DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
@@ -49,11 +51,12 @@ LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of k_step_lattice (152 robots, 1000 step
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--robots", type=int, default=P_ROBOTS, help=argparse.SUPPRESS)
     ap.add_argument("--sim-steps", type=int, default=SIM_STEPS, help=argparse.SUPPRESS)
+    ap.add_argument("--generations", type=int, default=GENERATIONS, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", choices=["auto", "corner", "compact"], default="auto",
                     help="variant of the lattice-gather kernel")
@@ -167,7 +170,7 @@ def run_ours(args):
     if rank == 0 or world == 1:
         B.build()
     dist_barrier(world)
-    P, N = args.robots, args.sim_steps
+    P, N, NG = args.robots, args.sim_steps, args.generations
     phys = W.CONFIG
     evo = W.Evolution()
     genomes_h, Bmat_h = W.workload_mlp(P, seed=shards.shard_seed(1, rank))
@@ -175,82 +178,103 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     lattice = {"auto": vs.LATTICE_AUTO, "corner": vs.LATTICE_CORNER, "compact": vs.LATTICE_COMPACT}[args.lattice]
     sim = vs.Simulator(phys, device=local, stream=stream, lattice=lattice)
-    g_a = torch.from_numpy(genomes_h).cuda()
-    g_b = torch.empty_like(g_a)
+    seed_d = torch.from_numpy(genomes_h).cuda()          # the seeded population, device-resident
+    g_a = torch.empty_like(seed_d)
+    g_b = torch.empty_like(seed_d)
     Bmat = torch.from_numpy(Bmat_h).cuda()
     fit = torch.empty(P, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    state = {"gen": 0, "g_in": g_a, "g_out": g_b}
+    def run_config(stats=None):
+        """The whole workload once: NG generations (decode, 10,000 steps, fitness, evolution)
+        from the seeded population, so every step does identical work whatever --steps and
+        --warmup are.  stats (untimed only) collects per-generation spring and mass counts."""
+        g_in, g_out = g_a, g_b
+        g_in.copy_(seed_d)
+        for gen in range(NG):
+            sim.set_population(dims, g_in, vs.MODE_MLP, B=Bmat)
+            sim.step(N)
+            sim.fitness(fit)
+            sim.evo_generation(fit, g_in, g_out, evo, gen)
+            if stats is not None:
+                M, S = sim.counts()
+                stats.append((int(S.astype(np.int64).sum()), int(M.astype(np.int64).sum())))
+            g_in, g_out = g_out, g_in
+        return g_in
 
-    def generation():
-        sim.set_population(dims, state["g_in"], vs.MODE_MLP, B=Bmat)
-        sim.step(N)
-        sim.fitness(fit)
-        sim.evo_generation(fit, state["g_in"], state["g_out"], evo, state["gen"])
-        state["gen"] += 1
-        state["g_in"], state["g_out"] = state["g_out"], state["g_in"]
-
-    for _ in range(args.warmup):
-        generation()
+    # warm-up; the first pass also counts the springs and masses of every generation (the
+    # evolution is deterministic, so every later pass simulates the same populations)
+    stats = []
+    final_ref = run_config(stats).clone()
+    for _ in range(max(args.warmup - 1, 0)):
+        run_config()
     torch.cuda.synchronize()
     sim.timing()
-    # the population entering the timed loop, so the end-to-end pass can replay the same
-    # generations (the evolution is deterministic)
-    replay_from = (state["g_in"].clone(), state["gen"])
+    springs_per_step = sum(sp for sp, _ in stats) * N
+    masses_per_step = sum(ms for _, ms in stats) * N
     # timed region: device-resident inputs, L2 flushed between steps (outside the events)
     clocks = ClockSampler(local)
     clocks.start()
     dist_barrier(world)
     torch.cuda.synchronize()
-    total_ms, updates, kernel_ms, launches, masses = 0.0, 0, 0.0, 0, 0
+    total_ms, kernel_ms, launches = 0.0, 0.0, 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g_in_this = state["g_in"]
-        generation()
+        final = run_config()
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
-        # spring count of the population this step simulated (read after the timed span)
         k_ms, n_launch = sim.timing()
         kernel_ms += k_ms
         launches += n_launch
-        M, S = sim.counts()
-        updates += int(S.astype(np.int64).sum()) * N
-        masses += int(M.astype(np.int64).sum()) * N
-        del g_in_this
     torch.cuda.synchronize()
     dist_barrier(world)
     clk = clocks.stop()
+    # the timed passes evolved exactly the warm-up's populations
+    assert torch.equal(final, final_ref), "the timed workload differs from the warm-up's"
+    updates, masses = springs_per_step * args.steps, masses_per_step * args.steps
     value, updates_all, secs = shards.job_throughput(float(updates), total_ms * 1e-3, "cuda")
     # the paper's unit is ambiguous (springs, masses or both per step): springs + masses too
     sm_value, _, _ = shards.job_throughput(float(updates + masses), total_ms * 1e-3, "cuda")
     total_ms = secs * 1e3
 
-    # end to end through the public API over the same generations as the timed steps: every
-    # step copies that generation's genomes in from pinned host memory and reads the fitness back
-    state["g_in"].copy_(replay_from[0])
-    state["gen"] = replay_from[1]
-    del replay_from
-    pinned = torch.empty(genomes_h.shape, dtype=torch.float32).pin_memory()
+    # end to end through the C ABI with host buffers: each step the seeded genomes (and B) go in
+    # through sim_set_population from pinned host memory (the library's copy is also the first
+    # generation's evolution input, genomes_in NULL) and every generation's fitness comes back
+    # through sim_fitness into pinned host memory
+    pinned = torch.from_numpy(genomes_h).pin_memory()
+    pinned_B = torch.from_numpy(Bmat_h).pin_memory()
     fit_h = torch.empty(P, dtype=torch.float64).pin_memory()
-    e2e_ms, e2e_updates = 0.0, 0
+
+    def run_config_e2e():
+        g_in, g_out = None, g_a
+        for gen in range(NG):
+            if gen == 0:
+                sim.set_population(dims, pinned, vs.MODE_MLP, B=pinned_B)
+            else:
+                sim.set_population(dims, g_in, vs.MODE_MLP, B=Bmat)
+            sim.step(N)
+            sim.fitness(fit)                      # device: the evolution's input
+            sim.fitness(fit_h)                    # host: the caller's read of the result
+            sim.evo_generation(fit, g_in, g_out, evo, gen)
+            g_in, g_out = g_out, (g_b if g_out is g_a else g_a)
+        return g_in
+
+    run_config_e2e()                              # warm-up of the host-buffer path
+    e2e_ms = 0.0
     for _ in range(args.steps):
-        pinned.copy_(state["g_in"])               # (untimed) this generation's inputs on the host
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        state["g_in"].copy_(pinned, non_blocking=True)
-        generation()
-        fit_h.copy_(fit, non_blocking=True)
+        final = run_config_e2e()
         stream.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        M, S = sim.counts()
-        e2e_updates += int(S.astype(np.int64).sum()) * N
         sim.timing()
-    e2e_value, _, _ = shards.job_throughput(float(e2e_updates), e2e_ms * 1e-3, "cuda")
+    assert torch.equal(final, final_ref), "the end-to-end pass evolved other populations"
+    del final_ref
+    e2e_value, _, _ = shards.job_throughput(float(springs_per_step * args.steps), e2e_ms * 1e-3, "cuda")
 
     peaks, peak_src = measured_peaks()
     # dominant kernel: the resident step kernel; algorithmic shared-memory bytes per step
@@ -270,11 +294,14 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded MLP genomes, U(-1/sqrt(fan_in), 1/sqrt(fan_in)); B ~ N(0, 2^2))",
-        "config": dict(WORKLOAD, l2="flushed between timed steps (256 MB write)",
+        "config": dict(WORKLOAD, generations=NG, l2="flushed between timed steps (256 MB write)",
                        parallelism=f"population shards x{world}" if world > 1 else "single GPU"),
         "e2e": {"value": e2e_value, "unit": "spring-updates/s",
-                "h2d_bytes_per_step": int(genomes_h.nbytes),
-                "d2h_bytes_per_step": int(P * 8)},
+                "h2d_bytes_per_step": int(genomes_h.nbytes + Bmat_h.nbytes),
+                "d2h_bytes_per_step": int(P * 8 * NG),
+                "path": "C ABI host buffers: sim_set_population(SIM_MEM_HOST) of the seeded genomes, "
+                        "sim_fitness(SIM_MEM_HOST) every generation"},
+        "springs_per_generation": [sp for sp, _ in stats],
         "gpu_launches": launches,
         "spring_plus_mass_updates_per_s": sm_value,
         "roofline": {"bound": "smem", "kernel": "k_step_lattice",

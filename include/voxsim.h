@@ -221,8 +221,12 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
  * fitness: double [P]; genomes_in / genomes_out: float [P][G] (may alias: the input is copied
  * first); parents_out: int32 [P][2] or NULL (elites name themselves twice); mask_out: uint8
  * [P][G] or NULL (1 = gene from parent A, 0 for elites).  All device memory of the context's
- * GPU.  Limits: 1 <= E <= P <= 65536, G <= 2^26, generation < 2^19.
- * Errors: SIM_EINVAL, SIM_ENOMEM (library scratch). */
+ * GPU.  genomes_in may be NULL when the last sim_set_population read its genome rows (MLP
+ * genomes, material logits or parameter rows) from host memory: the library's device copy of
+ * them is then the input, so a population that starts on the host is uploaded once.
+ * Limits: 1 <= E <= P <= 65536, G <= 2^26, generation < 2^19.
+ * Errors: SIM_EINVAL, SIM_ENOMEM (library scratch), SIM_ESTATE (NULL genomes_in without host
+ * genome rows; P x G must then equal their size). */
 sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* genomes_in,
                           float* genomes_out, int32_t P, int32_t G, const evo_params* e,
                           uint64_t generation, int32_t* parents_out, uint8_t* mask_out);

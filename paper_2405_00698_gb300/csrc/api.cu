@@ -197,6 +197,10 @@ struct voxsim_ctx {
     DevBuf<float> d_prm;
     DevBuf<uint8_t> d_in_u8, d_mat_raw, d_mat;
     DevBuf<float> d_in_f32, d_in_f32b, d_in_f32c, d_w, d_kappa, d_phi;
+    // floats of genome rows (MLP genomes, material logits or parameter rows) that the last
+    // sim_set_population copied from host memory into d_in_f32 (0: none), which evo_generation
+    // can take as its input instead of a second upload
+    int64_t host_genome_floats = 0;
     DevBuf<int> d_label, d_count, d_corner_mass, d_mass_corner;
     DevBuf<int2> d_sab;
     DevBuf<float4> d_sp, d_spack, d_x0, d_x, d_v, d_x_alt, d_v_alt;
@@ -468,6 +472,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
         VX_CK(cudaMemcpyAsync(ctx->d_soff.p, soff.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice, s));
     }
     VX_CK(cudaMemsetAsync(ctx->d_status.p, 0, 4 * sizeof(int), s));
+    ctx->host_genome_floats = 0;
     const MatConst mc = ctx->matconst();
     // decode
     if (P > 0) {
@@ -486,6 +491,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
                 VX_CK(ctx->d_in_f32.ensure(5 * (size_t)V));
                 if (sim_status st = copy_in(genomes, sizeof(float) * 5 * V, mem, ctx->d_in_f32.p, s)) return st;
                 src = ctx->d_in_f32.p;
+                ctx->host_genome_floats = 5 * V;
             }
             VX_LAUNCH(ctx, launch_decode_logits(src, V, mc, ctx->d_mat_raw.p, ctx->d_w.p, ctx->d_kappa.p,
                                        ctx->d_phi.p, s));
@@ -515,6 +521,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
                 if (sim_status st = copy_in(m, V, mem, ctx->d_in_u8.p, s)) return st;
                 if (sim_status st = copy_in(rows, 12 * V, mem, ctx->d_in_f32.p, s)) return st;
                 m = ctx->d_in_u8.p; rows = ctx->d_in_f32.p;
+                ctx->host_genome_floats = 3 * V;
             }
             VX_LAUNCH(ctx, launch_decode_param_rows(m, rows, V / P, V, ctx->d_mat_raw.p, ctx->d_w.p,
                                                     ctx->d_kappa.p, ctx->d_phi.p, ctx->d_status.p, s));
@@ -529,6 +536,7 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
                 if (sim_status st = copy_in(B, sizeof(float) * kPeRows * 3, mem, ctx->d_in_f32b.p, s)) return st;
                 gsrc = ctx->d_in_f32.p;
                 bsrc = ctx->d_in_f32b.p;
+                ctx->host_genome_floats = (int64_t)P * kGenome;
             }
             VX_CK(ctx->d_pe.ensure((size_t)Q * kPeDim * 2));
             VX_LAUNCH(ctx, launch_pe_table(d[0], d[1], d[2], bsrc, ctx->d_pe.p, s));
@@ -1072,7 +1080,15 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
                           uint64_t generation, int32_t* parents_out, uint8_t* mask_out)
 {
     if (sim_status st = check_ctx(ctx)) return st;
-    if (!e || !fitness || !genomes_in || !genomes_out) return fail(SIM_EINVAL, "null argument");
+    if (!e || !fitness || !genomes_out) return fail(SIM_EINVAL, "null argument");
+    if (!genomes_in) {       // the genome rows the last sim_set_population copied from the host
+        if (ctx->host_genome_floats == 0)
+            return fail(SIM_ESTATE, "genomes_in is NULL but the population was not set from host genome rows");
+        if ((int64_t)P * G != ctx->host_genome_floats)
+            return fail(SIM_EINVAL, "P x G = %lld does not match the %lld floats of the population's genome rows",
+                        (long long)P * G, (long long)ctx->host_genome_floats);
+        genomes_in = ctx->d_in_f32.p;
+    }
     if (P < 1 || P > 65535) return fail(SIM_EINVAL, "P must be in 1..65535");
     if (G < 1 || G > (1 << 26)) return fail(SIM_EINVAL, "G must be in 1..2^26");
     if (e->elites < 1 || e->elites > P) return fail(SIM_EINVAL, "elites must be in 1..P");

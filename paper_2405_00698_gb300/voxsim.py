@@ -294,7 +294,8 @@ class Simulator:
         _check(lib().sim_set_trajectory_records(self._h, 1 if on else 0))
 
     def contact_modes(self, robot: int, n_steps: int):
-        """Contact mode (0 free, 1 stuck, 2 slipping) of every grid corner of one robot at every
+        """Contact mode (0 free, 1 stuck, 2 slipping, 3 slipping with the kinetic friction
+        saturated) of every grid corner of one robot at every
         step of the recorded run: uint8 [n_steps, corners]."""
         nx, ny, nz = (int(v) for v in self.dims[robot])
         out = np.zeros((n_steps, (nx + 1) * (ny + 1) * (nz + 1)), np.uint8)
@@ -309,8 +310,9 @@ class Simulator:
     def evo_generation(self, fitness, genomes_in, genomes_out, evo, generation: int,
                        parents=None, mask=None):
         """All tensors on the device: fitness f64 [P], genomes f32 [P, G] (in and out may be the
-        same tensor), parents i32 [P, 2] or None, mask u8 [P, G] or None."""
-        P, G = genomes_in.shape
+        same tensor; genomes_in None: the genome rows the last set_population read from host
+        memory), parents i32 [P, 2] or None, mask u8 [P, G] or None."""
+        P, G = genomes_out.shape
         e = EvoParams(int(evo.elites(P)), int(evo.mut_threshold()), float(evo.sigma),
                       int(evo.keep_threshold()), int(evo.seed))
         self._sync_inputs(MEM_DEVICE)

@@ -109,3 +109,30 @@ def test_bad_arguments(sim):
     g = torch.zeros((4, 8), device="cuda")
     with pytest.raises(voxsim.VoxsimError):
         sim.evo_generation(f, g, g, W.Evolution(), 1 << 19)
+
+
+def test_evolution_from_the_host_uploaded_genomes(sim):
+    """A population set from host MLP genomes evolves from the library's own device copy
+    (genomes_in NULL): bit for bit the generation of the same genomes passed from the device.
+    Without host genome rows, or with a size that does not match them, NULL is refused."""
+    import torch
+    from paper_2405_00698_gb300 import voxsim as vs
+    rng = np.random.default_rng(17)
+    P = 40
+    genomes, B = W.mlp_genomes(rng, P), W.pe_matrix(rng)
+    dims = np.tile(np.int32([4, 4, 4]), (P, 1))
+    pinned = torch.from_numpy(genomes).pin_memory()
+    sim.set_population(dims, pinned, vs.MODE_MLP, B=torch.from_numpy(B).pin_memory())
+    f = torch.from_numpy(np.round(rng.standard_normal(P), 1)).cuda()
+    evo = W.Evolution(seed=5)
+    a = torch.empty((P, W.GENOME_LEN), device="cuda")
+    sim.evo_generation(f, None, a, evo, 3)
+    b = torch.empty_like(a)
+    sim.evo_generation(f, torch.from_numpy(genomes).cuda(), b, evo, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    with pytest.raises(vs.VoxsimError):                   # size mismatch
+        sim.evo_generation(f[:20], None, a[:20], evo, 3)
+    sim.set_population(dims, torch.from_numpy(genomes).cuda(), vs.MODE_MLP, B=torch.from_numpy(B).cuda())
+    with pytest.raises(vs.VoxsimError):                   # device genomes: no library copy
+        sim.evo_generation(f, None, a, evo, 3)
