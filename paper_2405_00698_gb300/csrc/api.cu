@@ -150,6 +150,11 @@ struct voxsim_ctx {
     // direction-compacted variant's)
     int n_items = 0, n_items_corner = 0, n_big = 0, max_big_corner = 0;
     bool has_split = false;        // some lattice items are split (two threads per corner)
+    // mass-packed plan of the per-corner lattice robots (used for stepping that records nothing
+    // per step; the replays of the adjoint run the per-corner plan, which gives the same bits)
+    int n_pitems = 0;
+    size_t pitem_smem = 0;
+    DevBuf<int4> d_pitems, d_pgroups;
     bool have_pack = false;   // the packed spring list exists for the current population
     int64_t max_big_spring_cap = 0;
     // per size class (by corner count): kind (0 lattice per corner, 1 atomic, 2 streamed,
@@ -288,6 +293,8 @@ struct voxsim_ctx {
 
 extern "C" {
 static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subset = nullptr);
+static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vector<std::pair<int, int>>>& lattice,
+                                     bool damped);
 }
 
 namespace {
@@ -355,7 +362,7 @@ sim_status sim_create(const sim_params* p, int32_t device, void* cuda_stream, vo
     *out = nullptr;
     if (!(p->dt > 0) || !(p->mass > 0) || !(p->edge > 0))
         return fail(SIM_EINVAL, "dt, mass and edge must be positive");
-    if (p->lattice < SIM_LATTICE_AUTO || p->lattice > SIM_LATTICE_COMPACT)
+    if (p->lattice < SIM_LATTICE_AUTO || p->lattice > SIM_LATTICE_PACKED)
         return fail(SIM_EINVAL, "unknown lattice variant %d", p->lattice);
     int ndev = 0;
     VX_CK(cudaGetDeviceCount(&ndev));
@@ -678,7 +685,9 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         }
         // a requested variant wins over the class choice; the direction-compacted one needs the list
         if (kind == kKindLattice && ctx->p.lattice == SIM_LATTICE_COMPACT) kind = kKindLatticeCompact;
-        if (kind == kKindLatticeCompact && (ctx->p.lattice == SIM_LATTICE_CORNER || !ctx->have_pack)) kind = kKindLattice;
+        if (kind == kKindLatticeCompact &&
+            (ctx->p.lattice == SIM_LATTICE_CORNER || ctx->p.lattice == SIM_LATTICE_PACKED || !ctx->have_pack))
+            kind = kKindLattice;
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER)
             return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners on the resident path", block);
         if (is_lattice(kind)) {
@@ -731,6 +740,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
             if (split && !v.empty()) ctx->has_split = true;
         }
     }
+    if (sim_status st = build_packed_items(ctx, lattice, damped)) return st;
     std::sort(atomic.begin(), atomic.end());
     std::vector<int> big;
     for (size_t i = 0; i < atomic.size();) {
@@ -792,6 +802,87 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     return SIM_OK;
 }
 
+// Mass-packed plan of the per-corner lattice robots: groups of T = (masses rounded up to a warp)
+// threads, packed first-fit by decreasing T into 768-thread blocks under the shared-memory
+// budget (C displacements, C velocities with dashpots, 13 T plane entries and 32 rows for
+// absent springs per group) and at most 15 groups (named barriers 1..15).  Used when the
+// population has more lattice robots than SMs (or SIM_LATTICE_PACKED asks for it); with fewer,
+// one robot per block is already the spread the per-corner plan gives (with the split items of
+// the dashpot preset).  When the packed blocks would not fill every SM, the thread capacity of a
+// block shrinks so that the work spreads over all of them.
+static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vector<std::pair<int, int>>>& lattice,
+                                     bool damped)
+{
+    ctx->n_pitems = 0;
+    ctx->pitem_smem = 0;
+    size_t n = 0;
+    for (const auto& v : lattice) n += v.size();
+    const bool masses_known = (int)ctx->mass_count.size() == ctx->P;
+    if (n == 0 || !masses_known || ctx->p.lattice == SIM_LATTICE_CORNER || ctx->has_split) return SIM_OK;
+    if (ctx->p.lattice != SIM_LATTICE_PACKED && n <= (size_t)ctx->num_sms) return SIM_OK;
+    struct Grp { int T, C, r; };
+    std::vector<Grp> gs;
+    int64_t sumT = 0;
+    int maxT = 32;
+    for (const auto& v : lattice)
+        for (const auto& e : v) {
+            const int r = e.second, M = ctx->mass_count[r];
+            if (M <= 0) continue;                       // nothing to step
+            const int C = (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
+            const int T = (M + 31) / 32 * 32;
+            gs.push_back({T, C, r});
+            sumT += T;
+            maxT = std::max(maxT, T);
+        }
+    if (gs.empty()) return SIM_OK;
+    std::sort(gs.begin(), gs.end(), [](const Grp& a, const Grp& b) {
+        return a.T != b.T ? a.T > b.T : (a.C != b.C ? a.C > b.C : a.r < b.r);
+    });
+    const int block = lattice_max_threads();
+    const size_t budget = ctx->smem_optin > 2048 ? ctx->smem_optin - 1024 : ctx->smem_optin;
+    int cap = block;
+    if (sumT < (int64_t)block * ctx->num_sms) {
+        const int64_t per = (sumT + ctx->num_sms - 1) / ctx->num_sms;
+        cap = (int)std::max<int64_t>(maxT, (per + 31) / 32 * 32);
+    }
+    auto need = [&](const Grp& g) {
+        return sizeof(float4) * ((damped ? 2 : 1) * (size_t)g.C + 13 * (size_t)g.T + 32);
+    };
+    struct Bin { int threads; size_t smem; std::vector<int> members; };
+    std::vector<Bin> bins;
+    for (int i = 0; i < (int)gs.size(); ++i) {
+        const size_t b = need(gs[i]);
+        if (b > budget) return fail(SIM_EINVAL, "robot %d does not fit a lattice block", gs[i].r);
+        Bin* home = nullptr;
+        for (Bin& bin : bins)
+            if (bin.threads + gs[i].T <= cap && bin.smem + b <= budget && bin.members.size() < 15) { home = &bin; break; }
+        if (!home) { bins.push_back({0, 0, {}}); home = &bins.back(); }
+        home->threads += gs[i].T;
+        home->smem += b;
+        home->members.push_back(i);
+    }
+    std::vector<int4> items, groups;
+    for (const Bin& bin : bins) {
+        items.push_back(make_int4((int)groups.size(), (int)bin.members.size(), 0, 0));
+        int t0 = 0;
+        size_t off = 0;
+        for (int i : bin.members) {
+            groups.push_back(make_int4(gs[i].r, t0, gs[i].T, (int)(off / sizeof(float4))));
+            t0 += gs[i].T;
+            off += need(gs[i]);
+        }
+        ctx->pitem_smem = std::max(ctx->pitem_smem, bin.smem);
+    }
+    VX_CK(ctx->d_pitems.ensure(items.size()));
+    VX_CK(ctx->d_pgroups.ensure(groups.size()));
+    VX_CK(cudaMemcpyAsync(ctx->d_pitems.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, ctx->stream));
+    VX_CK(cudaMemcpyAsync(ctx->d_pgroups.p, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vectors go out of scope: the copies must have read them
+    VX_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->n_pitems = (int)items.size();
+    return SIM_OK;
+}
+
 // Next free event pair of the timing pool (grown on demand).
 static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
 {
@@ -842,7 +933,15 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
     VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, 2 * sizeof(int), ctx->stream));
     // per-corner variant: items [0, n_items_corner); direction-compacted variant: the rest
     const int n_corner = ctx->n_items_corner, n_spring = ctx->n_items - ctx->n_items_corner;
-    if (n_corner > 0) {
+    if (n_corner > 0 && ctx->n_pitems > 0 && !a.rec_u) {
+        // the same robots in mass-packed groups (identical bits; checkpoints written alike)
+        LatticeArgs b = a;
+        b.items = ctx->d_pitems.p;
+        b.groups = ctx->d_pgroups.p;
+        b.n_items = ctx->n_pitems;
+        VX_LAUNCH(ctx, launch_step_lattice_packed(b, std::min(ctx->n_pitems, ctx->num_sms), ctx->pitem_smem,
+                                                  ctx->stream));
+    } else if (n_corner > 0) {
         a.n_items = n_corner;
         VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_corner, ctx->num_sms), threads, smem, ctx->stream));
     }
@@ -1532,7 +1631,8 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
         std::vector<std::pair<int, int>> cands;
         if (k < 6 && ctx->p.accumulate != SIM_ACC_ATOMIC) {
             if (ctx->p.lattice != SIM_LATTICE_COMPACT) cands.push_back({kKindLattice, 0});
-            if (ctx->p.lattice != SIM_LATTICE_CORNER && ctx->have_pack) cands.push_back({kKindLatticeCompact, 0});
+            if (ctx->p.lattice != SIM_LATTICE_CORNER && ctx->p.lattice != SIM_LATTICE_PACKED && ctx->have_pack)
+                cands.push_back({kKindLatticeCompact, 0});
         }
         if (fits && ctx->p.accumulate != SIM_ACC_GATHER) {
             const int t3[3] = {k < 6 ? 128 : 256, k < 6 ? 256 : 512, k < 6 ? 512 : 1024};

@@ -149,8 +149,11 @@ struct LatticeArgs {
     int nsteps;
     StepConst c;
     const int4* items;       // (first robot in item_robots, robots, threads per robot, kind:
-                             // 0 per corner, 1 direction-compacted, 2 per corner split)
+                             // 0 per corner, 1 direction-compacted, 2 per corner split); for the
+                             // mass-packed kernel (first group in groups, groups, 0, 0)
     const int* item_robots;
+    const int4* groups;      // mass-packed kernel: per group (robot, first thread, threads,
+                             // shared-memory offset in float4)
     int n_items;
     int has_split;           // the items include split ones (run by the split instantiation)
     int* queue;              // work counter, zeroed before the launch
@@ -280,6 +283,8 @@ int lattice_max_threads();
 constexpr int kLatticeSlotVec4 = 15;     // shared float4 per corner slot: u, v, 13 force planes
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s);
+// Mass-packed lattice kernel: 768-thread blocks shared by groups of robots sized by mass count.
+cudaError_t launch_step_lattice_packed(const LatticeArgs& a, int grid, size_t smem, cudaStream_t s);
 size_t resident_smem_bytes(int max_mass, int max_spring_smem, int accumulate);
 
 cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, const float4* x0,

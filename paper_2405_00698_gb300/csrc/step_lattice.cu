@@ -332,9 +332,156 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_compact(
     }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Mass-packed variant of the per-corner step.  The kernel above gives every robot a slot sized
+// by its grid corners, and threads past the robot's mass count only join the barriers: an
+// evolved 8x8x8 robot of ~400 masses leaves half of a 768-thread block idle.  Here a block's
+// 768 threads are shared by several robots, each group sized by its mass count (a multiple of
+// 32 threads), so a block runs as many masses as it has threads.  What makes that fit in shared
+// memory is indexing the force planes by the thread slot of the spring's far end (the reader)
+// instead of by corner: a robot needs 13 planes of T entries (T = its threads) and its
+// displacements by corner (C entries), not 13 planes of C entries.  The far end's slot rides in
+// the .w lane of its shared displacement, which the spring evaluation loads anyway.
+// Per step:
+//   phase A: for each forward spring (c, c + off(d)) the owner computes the force f from its own
+//            displacement and the far end's, adds f to its own total, and writes f into plane d
+//            at the far end's slot (absent springs write a never-read row per lane);
+//   phase B: each thread subtracts the plane-d entries at its own slot for its backward springs
+//            (contiguous, conflict-free rows), then the mass update.
+// The sums run over the same values in the same order as the per-corner kernel (own forward
+// springs by direction, then backward springs by direction): identical bits, so the adjoint's
+// replay (which runs the per-corner kernel) reproduces a run of this one.
+// Shared memory of a group: C float4 displacements (+ C velocities with dashpots), 13 T float4
+// plane entries, 32 float4 rows for absent springs.
+// ----------------------------------------------------------------------------------------------
+template <bool DAMPED>
+__global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(LatticeArgs a)
+{
+    extern __shared__ __align__(16) float4 sm4[];
+    __shared__ int sh_item[3];
+    const int tid = threadIdx.x;
+    const StepConst c = a.c;
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(a.queue, 1);
+            if (it < a.n_items) {
+                const int4 item = a.items[it];
+                sh_item[0] = item.x; sh_item[1] = item.y; sh_item[2] = 1;
+            } else {
+                sh_item[2] = 0;
+            }
+        }
+        __syncthreads();
+        if (!sh_item[2]) break;
+        const int first = sh_item[0], count = sh_item[1];
+        __syncthreads();   // everyone has read the item before thread 0 may overwrite it
+        // this thread's group: the one whose thread range [t0, t0 + T) holds it (groups are
+        // whole warps; threads past the last group only wait for the next item)
+        int group = -1;
+        int4 gi = make_int4(0, 0, 0, 0);
+        for (int j = 0; j < count; ++j) {
+            const int4 q = a.groups[first + j];
+            if (tid >= q.y && tid < q.y + q.z) { group = j; gi = q; }
+        }
+        if (group >= 0) {
+            const int r = gi.x, T = gi.z, lt = tid - gi.y;
+            const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
+            const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
+            const int64_t mo = a.pv.moff[r];
+            const int bar = 1 + group;
+            float4* su = sm4 + gi.w;                 // displacements by corner, slot id in .w
+            float4* sv = su + C;                     // velocities by corner (dashpots only)
+            float4* fb = DAMPED ? sv + C : su + C;   // plane d at fb + d * T, by the reader's slot
+            float4* junk = fb + 13 * T;              // absent springs' rows (never read)
+            const int M = a.pv.n_mass[r];
+            const bool in = lt < M;
+            const int cidx = in ? a.corner_order[mo + lt] : 0;
+            const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
+            const float slot = __int_as_float(lt);
+            float pk[13], pa[13], pb[13];
+            const float* prm = a.prm + 39 * mo;
+            for_each_dir([&](auto t) {
+                constexpr int d = decltype(t)::value;
+                const bool has = (fl >> d) & 1u;
+                pk[d] = has ? prm[(0 * 13 + d) * C + cidx] : 0.f;
+                pa[d] = has ? prm[(1 * 13 + d) * C + cidx] : 0.f;
+                pb[d] = has ? prm[(2 * 13 + d) * C + cidx] : 0.f;
+            });
+            float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) {
+                su[cidx] = make_float4(u.x, u.y, u.z, slot);
+                if (DAMPED) sv[cidx] = v;
+            }
+            group_sync(bar, T);
+            for (int n = 0; n < a.nsteps; ++n) {
+                if (a.ckpt_u && in && n % a.ckpt_every == 0) {   // state at the start of segment n / K
+                    const int64_t o = (int64_t)(n / a.ckpt_every) * a.ckpt_stride + mo + cidx;
+                    a.ckpt_u[o] = u;
+                    a.ckpt_v[o] = v;
+                }
+                const float2 sc = a.sc[n];
+                float2 Fxy = make_float2(0.f, 0.f);
+                float Fz = 0.f;
+                // phase A: forward springs, no branch per direction (an absent spring has zero
+                // parameters and the corner itself as far end: an exact zero force)
+                if (in) for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    const bool has = (fl >> d) & 1u;
+                    if constexpr (DAMPED) {
+                        if (!has) return;
+                    }
+                    float4 ub = u;
+                    if (has) ub = su[cidx + lattice_offset<d>(X, XY)];
+                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
+                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
+                                                      pk[d], pa[d], pb[d], sc.x, sc.y);
+                    if constexpr (DAMPED) {
+                        const float4 vb = sv[cidx + lattice_offset<d>(X, XY)];
+                        spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[d], c);
+                    }
+                    Fxy = __fadd2_rn(Fxy, make_float2(e.gx, e.gy)); Fz = __fadd_rn(Fz, e.gz);
+                    float4* dst = has ? fb + d * T + __float_as_int(ub.w) : junk + (lt & 31);
+                    *dst = make_float4(e.gx, e.gy, e.gz, 0.f);
+                });
+                group_sync(bar, T);
+                // phase B: backward springs (c - offset(d), c) from this slot's rows, then the update
+                if (in) {
+                    for_each_dir([&](auto t) {
+                        constexpr int d = decltype(t)::value;
+                        if (!((fl >> (16 + d)) & 1u)) return;
+                        const float4 g = fb[d * T + lt];   // force on the spring's first end
+                        Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
+                    });
+                    if ((fl >> 31) & 1u) {
+                        mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                        su[cidx] = make_float4(u.x, u.y, u.z, slot);
+                        if (DAMPED) sv[cidx] = v;
+                    }
+                }
+                group_sync(bar, T);
+            }
+            if (in) {
+                a.u[mo + cidx] = u;
+                a.v[mo + cidx] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int lattice_max_threads() { return kMaxLatticeThreads; }
+
+cudaError_t launch_step_lattice_packed(const LatticeArgs& a, int grid, size_t smem, cudaStream_t s)
+{
+    auto kernel = a.c.damped ? k_step_lattice_packed<true> : k_step_lattice_packed<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, kMaxLatticeThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)

@@ -20,7 +20,7 @@ MODE_MATERIALS, MODE_LOGITS, MODE_MLP, MODE_PARAMS, MODE_PARAM_ROWS = 0, 1, 2, 3
 ACC_AUTO, ACC_ATOMIC, ACC_GATHER = 0, 1, 2
 MLP_TENSOR, MLP_SIMT = 0, 1
 PATH_AUTO, PATH_RESIDENT, PATH_STREAMED, PATH_PLAIN = 0, 1, 2, 3
-LATTICE_AUTO, LATTICE_CORNER, LATTICE_COMPACT = 0, 1, 2
+LATTICE_AUTO, LATTICE_CORNER, LATTICE_COMPACT, LATTICE_PACKED = 0, 1, 2, 3
 GENOME_LEN = 20998
 
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",

@@ -1,9 +1,10 @@
-"""The two variants of the lattice-gather kernel (per-corner threads; springs compacted per
-direction onto the first threads) evaluate the same springs with the same arithmetic and sum
+"""The variants of the lattice-gather kernel (a thread per mass in a slot sized by the robot's
+corners; springs compacted per direction onto the first threads; several robots per block in
+groups sized by their mass counts) evaluate the same springs with the same arithmetic and sum
 every mass's forces in the same order, so they must agree bit for bit: on uniform, uneven and
 MLP-decoded populations, with the spring and ground dashpots of the paper's preset, and as the
-forward run the checkpointed adjoint replays.  The compacted variant is also held against the
-FP64 oracle directly."""
+forward run the checkpointed adjoint replays.  The compacted and the mass-packed variants are
+also held against the FP64 oracle directly."""
 import numpy as np
 import pytest
 
@@ -43,12 +44,24 @@ CASES = {
 
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("phys_name", ["CONFIG", "PAPER"])
-def test_variants_agree_bitwise(vs, case, phys_name):
+@pytest.mark.parametrize("variant", ["COMPACT", "PACKED"])
+def test_variants_agree_bitwise(vs, case, phys_name, variant):
     pop = CASES[case]()
     phys = getattr(W, phys_name)
     n = 600 if phys_name == "CONFIG" else 1500
     a = run(vs, pop, phys, n, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
-    b = run(vs, pop, phys, n, vs.LATTICE_COMPACT, path=vs.PATH_RESIDENT)
+    b = run(vs, pop, phys, n, getattr(vs, "LATTICE_" + variant), path=vs.PATH_RESIDENT)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+
+
+def test_packed_blocks_on_a_large_uneven_population(vs):
+    """More lattice robots than SMs: the default packs several robots of mixed mass counts into
+    each block (up to 15 groups, the shared-memory budget binding for many small robots); the
+    result is bitwise the one-robot-per-slot kernel's."""
+    pop = W.population_uneven(700, seed=78, sizes=(2, 3, 4, 6, 8), occ=(0.2, 0.95))
+    a = run(vs, pop, W.CONFIG, 300, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
+    b = run(vs, pop, W.CONFIG, 300, vs.LATTICE_AUTO, path=vs.PATH_RESIDENT)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     assert np.array_equal(a[2], b[2])
 
@@ -58,18 +71,20 @@ def test_variants_agree_on_mlp_population(vs):
     G, B = W.workload_mlp(P=48, seed=74)
     dims = np.tile(np.array([8, 8, 8], np.int32), (48, 1))
     out = []
-    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT):
+    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT, vs.LATTICE_PACKED):
         sim = vs.Simulator(W.CONFIG, lattice=lattice)
         sim.set_population(dims, torch.from_numpy(G).cuda(), vs.MODE_MLP, B=torch.from_numpy(B).cuda())
         sim.step(400)
         out.append(sim.state()[:2])
         sim.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
 
 
-def test_compact_variant_matches_oracle(vs, orc):
+@pytest.mark.parametrize("variant", ["COMPACT", "PACKED"])
+def test_variant_matches_oracle(vs, orc, variant):
     pop = W.population_uneven(24, seed=75, sizes=(3, 4, 6, 8), occ=(0.3, 0.7))
-    x, v, f, off = run(vs, pop, W.CONFIG, 1000, vs.LATTICE_COMPACT)
+    x, v, f, off = run(vs, pop, W.CONFIG, 1000, getattr(vs, "LATTICE_" + variant))
     ref = orc.run_population(pop, W.CONFIG, 1000, want_x=True)
     check_population(orc, pop, W.CONFIG, 1000, f, x, off, ref)
 
@@ -84,7 +99,7 @@ def test_adjoint_after_either_variant(vs):
     w, kappa, phi = W.voxel_params(rng, pop)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     grads = []
-    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT):
+    for lattice in (vs.LATTICE_CORNER, vs.LATTICE_COMPACT, vs.LATTICE_PACKED):
         sim = vs.Simulator(W.CONFIG, lattice=lattice)
         sim.set_checkpointing(50)
         sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
@@ -95,8 +110,9 @@ def test_adjoint_after_either_variant(vs):
         torch.cuda.synchronize()
         grads.append([a.cpu().numpy() for a in g])
         sim.close()
-    for a, b in zip(*grads):
-        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+    for other in grads[1:]:
+        for a, b in zip(grads[0], other):
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
 
 
 def test_autotune_reports_the_variant(vs):
