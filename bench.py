@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--sim-steps", type=int, default=SIM_STEPS, help=argparse.SUPPRESS)
     ap.add_argument("--generations", type=int, default=GENERATIONS, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lattice", choices=["auto", "corner", "compact"], default="auto",
+    ap.add_argument("--lattice", choices=["auto", "corner", "compact", "packed"], default="auto",
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
@@ -176,7 +176,8 @@ def run_ours(args):
     genomes_h, Bmat_h = W.workload_mlp(P, seed=shards.shard_seed(1, rank))
     dims = np.tile(np.asarray(GRID, np.int32), (P, 1))
     stream = torch.cuda.current_stream()
-    lattice = {"auto": vs.LATTICE_AUTO, "corner": vs.LATTICE_CORNER, "compact": vs.LATTICE_COMPACT}[args.lattice]
+    lattice = {"auto": vs.LATTICE_AUTO, "corner": vs.LATTICE_CORNER, "compact": vs.LATTICE_COMPACT,
+               "packed": vs.LATTICE_PACKED}[args.lattice]
     sim = vs.Simulator(phys, device=local, stream=stream, lattice=lattice)
     seed_d = torch.from_numpy(genomes_h).cuda()          # the seeded population, device-resident
     g_a = torch.empty_like(seed_d)
