@@ -327,6 +327,24 @@ sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float*
  * stream.  Errors: SIM_ESTATE without a recorded run, SIM_EINVAL. */
 sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out);
 
+/* Impose the contact modes of robot `robot` on the steps that follow sim_set_population
+ * (analysis and testing: differentiating the step map along another run's contact decisions,
+ * such as those of an FP64 reference run, so that both sides follow the same piecewise-smooth
+ * map).  modes: host uint8 [n_steps][C] over the robot's C grid corners in the layout of
+ * sim_get_contact_modes (0 free, 1 stuck, 2 slipping, 3 saturated slip; corners without a mass
+ * are ignored).  At run step n < n_steps (counted from sim_set_population) every mass of the
+ * robot takes modes[n][corner] instead of deciding it from its state: free adds no ground force;
+ * the three contact modes add F_n = k_ground (-z) whatever the sign of z, then zero the
+ * horizontal force and velocity (stuck), remove mu_k F_n along F_h (slipping) or zero the
+ * horizontal force (saturated).  Later steps decide freely.  Every imposed robot covers the same
+ * n_steps; NULL modes clears every imposition; sim_set_population clears them too.  While modes
+ * are imposed, every robot of at most 768 corners steps on the per-corner lattice kernel, also in
+ * the replays of sim_backward and sim_get_contact_modes, which therefore follow the same modes.
+ * Errors: SIM_ESTATE without a population, SIM_EINVAL (robot out of range or larger than a
+ * lattice block, a mode above 3, another n_steps than the robots already imposed, damped
+ * physics, the streamed, plain or atomic organisation), SIM_ENOMEM. */
+sim_status sim_impose_contact_modes(voxsim_ctx* ctx, int32_t robot, const uint8_t* modes, int32_t n_steps);
+
 /* Population diversity (Fig. 3(b) plots a "diversity curve" without defining it; these are the
  * definitions used here), FP64 on the GPU:
  *   out[0] genome diversity: root mean square of the pairwise Euclidean distances between the P

@@ -81,6 +81,7 @@ def lib():
             L.orc_robot_get_state.argtypes = [vp, vp, vp]; L.orc_robot_get_state.restype = None
             L.orc_robot_set_state.argtypes = [vp, vp, vp, C.c_long]; L.orc_robot_set_state.restype = None
             L.orc_robot_simulate.argtypes = [vp, vp, i32]; L.orc_robot_simulate.restype = i32
+            L.orc_robot_simulate_modes.argtypes = [vp, vp, i32, vp]; L.orc_robot_simulate_modes.restype = i32
             L.orc_robot_fitness.argtypes = [vp, vp]; L.orc_robot_fitness.restype = d
             L.orc_run_population.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
             L.orc_run_population.restype = i32
@@ -196,6 +197,12 @@ class Robot:
 
     def simulate(self, nsteps: int) -> int:
         return lib().orc_robot_simulate(self._h, C.byref(self._params), int(nsteps))
+
+    def simulate_modes(self, force) -> int:
+        """Step once per row of force (uint8 [nsteps, M], mass order) with those contact modes
+        imposed."""
+        fm = np.ascontiguousarray(np.asarray(force, dtype=np.uint8).reshape(-1, self.M))
+        return lib().orc_robot_simulate_modes(self._h, C.byref(self._params), int(fm.shape[0]), _p(fm))
 
     def fitness(self) -> float:
         return lib().orc_robot_fitness(self._h, C.byref(self._params))

@@ -583,6 +583,18 @@ int orc_robot_simulate(orc_robot* R, const orc_params* p, int nsteps)
     return skipped;
 }
 
+/* Advance one robot by nsteps with the contact modes of every step imposed (force: nsteps x M in
+ * mass order, see orc_step).  Returns the number of zero-length spring skips. */
+int orc_robot_simulate_modes(orc_robot* R, const orc_params* p, int nsteps, const uint8_t* force)
+{
+    double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(R->M > 0 ? R->M : 1));
+    int skipped = 0;
+    for (int n = 0; n < nsteps; ++n)
+        skipped += orc_step(R, p, F, NULL, NULL, force + (size_t)n * (size_t)R->M);
+    free(F);
+    return skipped;
+}
+
 /* Fitness: displacement of the centroid along +x, final minus initial pose, equal masses.
  * The paper only names "fitness" (Section III); the centroid x-displacement is the reading taken.
  * An empty robot scores 0; a robot with a non-finite coordinate or one beyond dead_bound is dead

@@ -155,6 +155,22 @@ struct voxsim_ctx {
     int n_pitems = 0;
     size_t pitem_smem = 0;
     DevBuf<int4> d_pitems, d_pgroups;
+    // imposed contact modes (sim_impose_contact_modes): per robot the offset of its table in
+    // imp_table (-1: none), tables of imp_n steps x the robot's corners; device copies
+    bool imp_active = false;
+    int imp_n = 0;
+    std::vector<int64_t> imp_off;
+    std::vector<uint8_t> imp_table;
+    DevBuf<uint8_t> d_imp_modes;
+    DevBuf<int64_t> d_imp_off;
+    void imposed_args(LatticeArgs& a, int64_t step0) const
+    {
+        if (!imp_active) return;
+        a.imp_modes = d_imp_modes.p;
+        a.imp_off = d_imp_off.p;
+        a.imp_n = imp_n;
+        a.imp_step0 = step0;
+    }
     bool have_pack = false;   // the packed spring list exists for the current population
     int64_t max_big_spring_cap = 0;
     // per size class (by corner count): kind (0 lattice per corner, 1 atomic, 2 streamed,
@@ -480,6 +496,10 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
     }
     VX_CK(cudaMemsetAsync(ctx->d_status.p, 0, 4 * sizeof(int), s));
     ctx->host_genome_floats = 0;
+    ctx->imp_active = false;        // imposed contact modes belong to the previous population
+    ctx->imp_n = 0;
+    ctx->imp_off.clear();
+    ctx->imp_table.clear();
     const MatConst mc = ctx->matconst();
     // decode
     if (P > 0) {
@@ -683,10 +703,13 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
             else if (fits_sm && ctx->p.accumulate != SIM_ACC_GATHER) kind = kKindAtomic;
             else return fail(SIM_EINVAL, "robot %d (%d corners) does not fit the resident path", r, C);
         }
+        // while contact modes are imposed every robot that fits a lattice block runs on it
+        if (ctx->imp_active && C <= block && ctx->p.accumulate != SIM_ACC_ATOMIC) kind = kKindLattice;
         // a requested variant wins over the class choice; the direction-compacted one needs the list
         if (kind == kKindLattice && ctx->p.lattice == SIM_LATTICE_COMPACT) kind = kKindLatticeCompact;
         if (kind == kKindLatticeCompact &&
-            (ctx->p.lattice == SIM_LATTICE_CORNER || ctx->p.lattice == SIM_LATTICE_PACKED || !ctx->have_pack))
+            (ctx->p.lattice == SIM_LATTICE_CORNER || ctx->p.lattice == SIM_LATTICE_PACKED || !ctx->have_pack ||
+             ctx->imp_active))
             kind = kKindLattice;
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER)
             return fail(SIM_EINVAL, "bit-reproducible stepping supports robots of at most %d corners on the resident path", block);
@@ -818,7 +841,8 @@ static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vec
     size_t n = 0;
     for (const auto& v : lattice) n += v.size();
     const bool masses_known = (int)ctx->mass_count.size() == ctx->P;
-    if (n == 0 || !masses_known || ctx->p.lattice == SIM_LATTICE_CORNER || ctx->has_split) return SIM_OK;
+    if (n == 0 || !masses_known || ctx->p.lattice == SIM_LATTICE_CORNER || ctx->has_split || ctx->imp_active)
+        return SIM_OK;
     if (ctx->p.lattice != SIM_LATTICE_PACKED && n <= (size_t)ctx->num_sms) return SIM_OK;
     struct Grp { int T, C, r; };
     std::vector<Grp> gs;
@@ -917,6 +941,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
     a.n_items = ctx->n_items;
     a.queue = ctx->d_queue.p;
     a.has_split = ctx->has_split ? 1 : 0;
+    ctx->imposed_args(a, ctx->step);
     if (record) {                               // (buffers sized by sim_step_n)
         a.ckpt_u = ctx->d_ckpt_u.p;
         a.ckpt_v = ctx->d_ckpt_v.p;
@@ -1320,6 +1345,7 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     f.rec_u = ctx->d_srec_u.p;
     f.rec_f = ctx->d_srec_f.p;
     f.rec_stride = (int64_t)Mc;
+    ctx->imposed_args(f, ctx->rec_step0);
     AdjointArgs a{};
     a.pv = ctx->view();
     a.cflags = ctx->d_cflags.p;
@@ -1354,6 +1380,7 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
             f.v = ctx->d_rep_v0.p;
             f.sc = ctx->d_sc_rec.p + n0;
             f.nsteps = n1 - n0;
+            f.imp_step0 = ctx->rec_step0 + n0;
             VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
             VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, s));
         }
@@ -1504,6 +1531,7 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
             f.v = ctx->d_rep_v0.p;
             f.sc = ctx->d_sc_rec.p + n0;
             f.nsteps = n1 - n0;
+            ctx->imposed_args(f, ctx->rec_step0 + n0);
             const int threads = lattice_max_threads();
             VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
             VX_LAUNCH(ctx, launch_step_lattice(f, std::min(ctx->n_items, ctx->num_sms), threads,
@@ -1592,6 +1620,57 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
 
 // Per size class, time every admissible kernel on a sample of the class's robots (up to two per
 // SM) for n_steps steps from the current state, keep the fastest, restore the state.
+sim_status sim_impose_contact_modes(voxsim_ctx* ctx, int32_t robot, const uint8_t* modes, int32_t n_steps)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!ctx->have_pop) return fail(SIM_ESTATE, "no population set");
+    DeviceGuard g(ctx->device);
+    if (!modes) {
+        const bool was = ctx->imp_active;
+        ctx->imp_active = false;
+        ctx->imp_n = 0;
+        ctx->imp_off.clear();
+        ctx->imp_table.clear();
+        ctx->rec_valid = false;
+        if (was) return build_work_items(ctx);
+        return SIM_OK;
+    }
+    if (robot < 0 || robot >= ctx->P) return fail(SIM_EINVAL, "robot %d out of range", robot);
+    if (n_steps < 1) return fail(SIM_EINVAL, "n_steps must be >= 1");
+    if (ctx->imp_active && n_steps != ctx->imp_n)
+        return fail(SIM_EINVAL, "every imposed robot must cover the same %d steps", ctx->imp_n);
+    if (ctx->stepconst().damped || ctx->p.ground_zeta != 0.0)
+        return fail(SIM_EINVAL, "imposed contact modes need undamped springs and ground");
+    if (ctx->p.path == SIM_PATH_STREAMED || ctx->p.path == SIM_PATH_PLAIN || ctx->p.accumulate == SIM_ACC_ATOMIC)
+        return fail(SIM_EINVAL, "imposed contact modes run on the lattice kernel");
+    const int C = (ctx->dims[3 * robot] + 1) * (ctx->dims[3 * robot + 1] + 1) * (ctx->dims[3 * robot + 2] + 1);
+    if (C > lattice_max_threads())
+        return fail(SIM_EINVAL, "robot %d (%d corners) is not on the lattice kernel", robot, C);
+    const size_t len = (size_t)n_steps * C;
+    for (size_t i = 0; i < len; ++i)
+        if (modes[i] > 3) return fail(SIM_EINVAL, "contact mode %d out of range 0..3", (int)modes[i]);
+    if (ctx->imp_off.size() != (size_t)ctx->P) ctx->imp_off.assign(ctx->P, -1);
+    int64_t off = ctx->imp_off[robot];
+    if (off < 0) {
+        off = (int64_t)ctx->imp_table.size();
+        ctx->imp_table.resize(ctx->imp_table.size() + len);
+        ctx->imp_off[robot] = off;
+    }
+    std::memcpy(ctx->imp_table.data() + off, modes, len);
+    VX_CK(ctx->d_imp_modes.ensure(ctx->imp_table.size()));
+    VX_CK(ctx->d_imp_off.ensure(ctx->P));
+    cudaStream_t s = ctx->stream;
+    VX_CK(cudaMemcpyAsync(ctx->d_imp_modes.p, ctx->imp_table.data(), ctx->imp_table.size(), cudaMemcpyHostToDevice, s));
+    VX_CK(cudaMemcpyAsync(ctx->d_imp_off.p, ctx->imp_off.data(), sizeof(int64_t) * ctx->P, cudaMemcpyHostToDevice, s));
+    VX_CK(cudaStreamSynchronize(s));
+    const bool was = ctx->imp_active;
+    ctx->imp_active = true;
+    ctx->imp_n = n_steps;
+    ctx->rec_valid = false;
+    if (!was) return build_work_items(ctx);      // per-corner kernel only while modes are imposed
+    return SIM_OK;
+}
+
 sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out)
 {
     if (sim_status st = check_ctx(ctx)) return st;

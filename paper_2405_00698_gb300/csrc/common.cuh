@@ -168,6 +168,13 @@ struct LatticeArgs {
     float4* rec_u;
     float2* rec_f;
     int64_t rec_stride;
+    // imposed contact modes (NULL: none; sim_impose_contact_modes): robot r's table of imp_n
+    // steps x its C corners at imp_off[r] (-1: the robot decides its modes), indexed by the run
+    // step imp_step0 + n of this call's step n
+    const uint8_t* imp_modes;
+    const int64_t* imp_off;
+    int imp_n;
+    int64_t imp_step0;
 };
 
 // Streamed path (robots too large for one SM): one launch per step over all their corners.

@@ -208,4 +208,42 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
     return mode;
 }
 
+// mass_update with the contact mode given from outside (forced >= 0: one of kFree, kStick,
+// kSlip, kSlipHeld; forced < 0: decided from the state as in mass_update).  A given mode is
+// applied whatever the state: free adds no ground force; the three contact modes add
+// F_n = k_g (-z) whatever the sign of z, then zero the horizontal force and velocity (stick),
+// remove mu_k F_n along F_h (slip, no saturation) or zero the horizontal force (saturated slip).
+// This differentiates the step map along another run's contact decisions (those of the FP64
+// oracle).  Each mode's arithmetic is mass_update's, so imposing a run's own modes repeats it bit
+// for bit.
+__device__ __forceinline__ unsigned mass_update_imposed(float4& u, float4& v, float Fx, float Fy, float Fz,
+                                                        const StepConst& c, int forced)
+{
+    if (forced < 0) return mass_update(u, v, Fx, Fy, Fz, c);
+    Fz = __fsub_rn(Fz, c.weight);
+    if (forced != (int)kFree) {
+        const float z = __fadd_rn(u.w, u.z);
+        const float fn = __fmul_rn(c.k_ground, -z);
+        Fz = __fadd_rn(Fz, fn);
+        if (c.ground_c > 0.f) Fz = __fsub_rn(Fz, __fmul_rn(c.ground_c, v.z));
+        if (forced == (int)kStick) {
+            Fx = 0.f; Fy = 0.f; v.x = 0.f; v.y = 0.f;
+        } else if (forced == (int)kSlipHeld) {
+            Fx = 0.f; Fy = 0.f;
+        } else {
+            const float fh = __fsqrt_rn(__fmaf_rn(Fy, Fy, __fmul_rn(Fx, Fx)));
+            const float s = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(c.mu_k, fn), fh));
+            Fx = __fmul_rn(Fx, s);
+            Fy = __fmul_rn(Fy, s);
+        }
+    }
+    v.x = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fx, v.x));
+    v.y = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fy, v.y));
+    v.z = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fz, v.z));
+    u.x = __fmaf_rn(c.dt, v.x, u.x);
+    u.y = __fmaf_rn(c.dt, v.y, u.y);
+    u.z = __fmaf_rn(c.dt, v.z, u.z);
+    return (unsigned)forced;
+}
+
 }  // namespace vx

@@ -40,7 +40,8 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 // barrier the owner adds the helper's six plane entries in direction order before the backward
 // gather, so the sums are formed in the same order from the same values: the same bits as the
 // unsplit step, with the longest chain of spring evaluations per step cut from 13 to 7.
-template <bool DAMPED, bool RECORD, bool SPLIT>
+// IMPOSE: some robots take their contact modes from a table (sim_impose_contact_modes).
+template <bool DAMPED, bool RECORD, bool SPLIT, bool IMPOSE>
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
             float4 u = in ? a.u[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 v = in ? a.v[mo + cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
             const bool mass = ((fl >> 31) & 1u) && !hlp;
+            const int64_t imp = IMPOSE ? a.imp_off[r] : -1;
             if (in && !hlp) {
                 su[cidx] = u;
                 if (DAMPED) sv[cidx] = v;
@@ -159,12 +161,20 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
                 });
                 if (mass) {
+                    int forced = -1;
+                    if constexpr (IMPOSE) {
+                        const int64_t gstep = a.imp_step0 + n;
+                        if (imp >= 0 && gstep < a.imp_n) forced = a.imp_modes[imp + gstep * C + cidx];
+                    }
                     if constexpr (RECORD) {            // replay for the adjoint: the step's inputs
                         const float4 ub4 = u;
-                        const unsigned mode = mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                        const unsigned mode = IMPOSE ? mass_update_imposed(u, v, Fxy.x, Fxy.y, Fz, c, forced)
+                                                     : mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
                         const int64_t o = (int64_t)n * a.rec_stride + mo + cidx;
                         a.rec_u[o] = make_float4(ub4.x, ub4.y, ub4.z, __uint_as_float(mode));
                         a.rec_f[o] = Fxy;
+                    } else if constexpr (IMPOSE) {
+                        mass_update_imposed(u, v, Fxy.x, Fxy.y, Fz, c, forced);
                     } else {
                         mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
                     }
@@ -391,13 +401,14 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(L
             const int bar = 1 + group;
             float4* su = sm4 + gi.w;                 // displacements by corner, slot id in .w
             float4* sv = su + C;                     // velocities by corner (dashpots only)
-            float4* fb = DAMPED ? sv + C : su + C;   // plane d at fb + d * T, by the reader's slot
-            float4* junk = fb + 13 * T;              // absent springs' rows (never read)
+            float4* fb = DAMPED ? sv + C : su + C;   // plane d at fb + d * T, by the reader's slot;
+                                                     // then 32 rows for absent springs (never read)
             const int M = a.pv.n_mass[r];
             const bool in = lt < M;
             const int cidx = in ? a.corner_order[mo + lt] : 0;
             const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
             const float slot = __int_as_float(lt);
+            const int junk = 13 * T + (lt & 31);     // this lane's row for absent springs
             float pk[13], pa[13], pb[13];
             const float* prm = a.prm + 39 * mo;
             for_each_dir([&](auto t) {
@@ -441,8 +452,8 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(L
                         spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[d], c);
                     }
                     Fxy = __fadd2_rn(Fxy, make_float2(e.gx, e.gy)); Fz = __fadd_rn(Fz, e.gz);
-                    float4* dst = has ? fb + d * T + __float_as_int(ub.w) : junk + (lt & 31);
-                    *dst = make_float4(e.gx, e.gy, e.gz, 0.f);
+                    const int row = has ? d * T + __float_as_int(ub.w) : junk;
+                    fb[row] = make_float4(e.gx, e.gy, e.gz, 0.f);
                 });
                 group_sync(bar, T);
                 // phase B: backward springs (c - offset(d), c) from this slot's rows, then the update
@@ -486,10 +497,11 @@ cudaError_t launch_step_lattice_packed(const LatticeArgs& a, int grid, size_t sm
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
-    auto kernel = a.rec_u ? k_step_lattice<false, true, false>
+    auto kernel = a.imp_modes ? (a.rec_u ? k_step_lattice<false, true, false, true> : k_step_lattice<false, false, false, true>)
+                : a.rec_u ? k_step_lattice<false, true, false, false>
                 : a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
-                : a.c.damped ? (a.has_split ? k_step_lattice<true, false, true> : k_step_lattice<true, false, false>)
-                             : k_step_lattice<false, false, false>;
+                : a.c.damped ? (a.has_split ? k_step_lattice<true, false, true, false> : k_step_lattice<true, false, false, false>)
+                             : k_step_lattice<false, false, false, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<grid, threads, smem, s>>>(a);

@@ -26,7 +26,7 @@ GENOME_LEN = 20998
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
            "sim_set_trajectory_records", "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
-           "sim_get_timing", "sim_check_status_words")
+           "sim_get_timing", "sim_check_status_words", "sim_impose_contact_modes")
 
 
 class VoxsimError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
             "sim_get_topology": [vp, vp, vp, vp],
             "sim_get_timing": [vp, vp, vp],
             "sim_check_status_words": [vp],
+            "sim_impose_contact_modes": [vp, i32, vp, i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -292,6 +293,15 @@ class Simulator:
     def set_trajectory_records(self, on: bool):
         """Keep every step's record of the recorded run, so that backward needs no replay."""
         _check(lib().sim_set_trajectory_records(self._h, 1 if on else 0))
+
+    def impose_contact_modes(self, robot: int, modes):
+        """Impose contact modes on one robot's first steps (uint8 [n_steps, corners] in the
+        layout of contact_modes); None clears every imposition."""
+        if modes is None:
+            _check(lib().sim_impose_contact_modes(self._h, 0, None, 0))
+            return
+        m = np.ascontiguousarray(modes, dtype=np.uint8)
+        _check(lib().sim_impose_contact_modes(self._h, int(robot), m.ctypes.data, int(m.shape[0])))
 
     def contact_modes(self, robot: int, n_steps: int):
         """Contact mode (0 free, 1 stuck, 2 slipping, 3 slipping with the kinetic friction

@@ -593,3 +593,24 @@ def test_imposed_modes_make_every_parameter_differentiable(orc):
             fd = (fp - fm) / (2 * h)
             scale = max(abs(fd), 1e-3 * np.abs(grads[name]).max())
             assert abs(grads[name][v] - fd) <= 1e-5 * scale, (name, int(v), grads[name][v], fd)
+
+
+def test_simulate_with_imposed_modes_repeats_the_free_run(orc):
+    """Stepping with a run's own contact modes imposed reproduces it exactly; imposing all
+    contacts stuck keeps every contact corner's horizontal position while it is held."""
+    rng = np.random.default_rng(12)
+    g = W.uniform_materials(rng, (3, 3, 3))
+    free = orc.Robot(g, (3, 3, 3), PHYS)
+    _, modes, _ = orc.fitness_after_modes(g, (3, 3, 3), PHYS, 400)
+    assert (modes != 0).any()
+    free.simulate(400)
+    imp = orc.Robot(g, (3, 3, 3), PHYS)
+    imp.simulate_modes(modes)
+    assert np.array_equal(free.state()[0], imp.state()[0])
+    stuck = orc.Robot(g, (3, 3, 3), PHYS)
+    x0, _ = stuck.state()
+    hold = np.zeros((50, stuck.M), np.uint8)
+    hold[:, x0[:, 2] == 0.0] = 1
+    stuck.simulate_modes(hold)
+    x1, _ = stuck.state()
+    assert np.array_equal(x1[x0[:, 2] == 0.0, :2], x0[x0[:, 2] == 0.0, :2])
