@@ -173,7 +173,10 @@ def run_ours(args):
     P, N, NG = args.robots, args.sim_steps, args.generations
     phys = W.CONFIG
     evo = W.Evolution()
-    genomes_h, Bmat_h = W.workload_mlp(P, seed=shards.shard_seed(1, rank))
+    # one population of P robots per rank, sharded: every rank holds the whole genome matrix
+    # (replicated evolution) and simulates rows [first, first + P)
+    P_all, first = P * world, P * rank
+    genomes_h, Bmat_h = W.workload_mlp(P_all, seed=1)
     dims = np.tile(np.asarray(GRID, np.int32), (P, 1))
     stream = torch.cuda.current_stream()
     lattice = {"auto": vs.LATTICE_AUTO, "corner": vs.LATTICE_CORNER, "compact": vs.LATTICE_COMPACT,
@@ -193,10 +196,11 @@ def run_ours(args):
         g_in, g_out = g_a, g_b
         g_in.copy_(seed_d)
         for gen in range(NG):
-            sim.set_population(dims, g_in, vs.MODE_MLP, B=Bmat)
+            sim.set_population(dims, g_in[first:first + P], vs.MODE_MLP, B=Bmat)
             sim.step(N)
             sim.fitness(fit)
-            sim.evo_generation(fit, g_in, g_out, evo, gen)
+            fit_all = shards.gather_population_fitness(fit, world)     # the exchange step
+            sim.evo_generation(fit_all, g_in, g_out, evo, gen)
             if stats is not None:
                 M, S = sim.counts()
                 stats.append((int(S.astype(np.int64).sum()), int(M.astype(np.int64).sum())))
@@ -251,15 +255,19 @@ def run_ours(args):
 
     def run_config_e2e():
         g_in, g_out = None, g_a
+        if world > 1:        # the replicated evolution needs every rank's copy of all genomes
+            g_b.copy_(pinned, non_blocking=True)
+            g_in, g_out = g_b, g_a
         for gen in range(NG):
-            if gen == 0:
+            if gen == 0 and world == 1:
                 sim.set_population(dims, pinned, vs.MODE_MLP, B=pinned_B)
             else:
-                sim.set_population(dims, g_in, vs.MODE_MLP, B=Bmat)
+                sim.set_population(dims, g_in[first:first + P], vs.MODE_MLP, B=Bmat)
             sim.step(N)
             sim.fitness(fit)                      # device: the evolution's input
             sim.fitness(fit_h)                    # host: the caller's read of the result
-            sim.evo_generation(fit, g_in, g_out, evo, gen)
+            fit_all = shards.gather_population_fitness(fit, world)
+            sim.evo_generation(fit_all, g_in, g_out, evo, gen)
             g_in, g_out = g_out, (g_b if g_out is g_a else g_a)
         return g_in
 
@@ -296,9 +304,11 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded MLP genomes, U(-1/sqrt(fan_in), 1/sqrt(fan_in)); B ~ N(0, 2^2))",
         "config": dict(WORKLOAD, generations=NG, l2="flushed between timed steps (256 MB write)",
-                       parallelism=f"population shards x{world}" if world > 1 else "single GPU"),
+                       parallelism=(f"one population of {P_all} robots in {world} shards: fitness "
+                                    "all-gather per generation, replicated evolution")
+                       if world > 1 else "single GPU"),
         "e2e": {"value": e2e_value, "unit": "spring-updates/s",
-                "h2d_bytes_per_step": int(genomes_h.nbytes + Bmat_h.nbytes),
+                "h2d_bytes_per_step": int(genomes_h.nbytes + (Bmat_h.nbytes if world == 1 else 0)),
                 "d2h_bytes_per_step": int(P * 8 * NG),
                 "path": "C ABI host buffers: sim_set_population(SIM_MEM_HOST) of the seeded genomes, "
                         "sim_fitness(SIM_MEM_HOST) every generation"},
@@ -324,7 +334,8 @@ def run_ours(args):
         rec["lamarckian"] = measure_lamarckian(vs, stream, args)
         rec["streamed"] = measure_streamed(vs, stream, args, peaks)
         rec["streamed_adjoint"] = measure_streamed_adjoint(vs, stream, args, peaks)
-        rec["streamed_adjoint_records"] = measure_streamed_adjoint(vs, stream, args, peaks, records=True)
+        rec["streamed_adjoint_records"] = measure_streamed_adjoint(vs, stream, args, peaks, P=16, N=2000,
+                                                                   records=True)
         rec["paper_preset"] = measure_paper_preset(vs, stream, args)
     if rank == 0:
         print(json.dumps(rec))
@@ -512,12 +523,13 @@ def measure_paper_preset(vs, stream, args, N=20000):
             "paper_figure": 7892537853, "note": "the paper's figure is on an RTX 3090 with unstated unit and workload"}
 
 
-def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100, records=False):
-    """The adjoint on large robots (16 robots 40x40x40 at occupancy 0.7, state in HBM): forward
-    with checkpoints every 100 steps, then the backward pass (segment replays with recording and
-    the reverse sweep), as robot gradients per second and as algorithmic HBM bytes against the
-    measured peak.  A 500-step sample of the 5000-step workload.  records: the forward also keeps
-    every step's record (24 B per corner per step, 13 GB here) and the backward only sweeps."""
+def measure_streamed_adjoint(vs, stream, args, peaks, P=64, n=40, N=5000, K=100, records=False):
+    """The adjoint on large robots (64 robots 40x40x40 at occupancy 0.7, state in HBM, 5000
+    steps): forward with checkpoints every 100 steps, then the backward pass (segment replays
+    with recording and the reverse sweep), as robot gradients per second and as algorithmic HBM
+    bytes against the measured peak.  records: the forward also keeps every step's record (24 B
+    per corner per step) and the backward only sweeps; the whole workload's records would take
+    530 GB, so that variant runs on a sample that fits (the caller's P and N)."""
     import torch
     rng = np.random.default_rng(6)
     pop = W.workload_large(P, seed=5, n=n)
@@ -529,9 +541,14 @@ def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100, 
     args_pop = (t(pop.mats), t(w), t(kappa), t(phi))
     g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
     dl = torch.ones(P, dtype=torch.float64, device="cuda")
+    if not records:
+        sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
+        sim.step(2 * K)
+        sim.backward(dl, *g)                       # warm-up of the backward's buffers
     sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
-    sim.step(N)
-    sim.backward(dl, *g)                           # warm-up (buffers, graph)
+    sim.step(N)                                    # warm-up: checkpoints, the N-step graph
+    if records:
+        sim.backward(dl, *g)
     sim.set_population(pop.dims, args_pop, vs.MODE_PARAMS)
     fwd = _timed(stream, lambda: sim.step(N))
     bwd = _timed(stream, lambda: sim.backward(dl, *g))
@@ -545,7 +562,8 @@ def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100, 
     fwd_gbs = (12.0 * Ssum + (88.0 if records else 64.0) * Msum) * N / (fwd * 1e-3) / 1e9
     bwd_gbs = ((36.0 if records else 48.0) * Ssum + (136.0 if records else 224.0) * Msum) * N / (bwd * 1e-3) / 1e9
     kept = ", every step's record kept" if records else ""
-    return {"workload": f"{P} robots {n}^3, occupancy 0.7, per-voxel parameters, {N} steps (sample of 5000), "
+    sample = "" if (P, N) == (64, 5000) else f" (sample of 64 robots x 5000 steps)"
+    return {"workload": f"{P} robots {n}^3, occupancy 0.7, per-voxel parameters, {N} steps{sample}, "
                         f"checkpoints every {K}{kept}",
             "grads_per_s": P / ((fwd + bwd) * 1e-3), "forward_ms": fwd, "backward_ms": bwd,
             "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -554,9 +572,9 @@ def measure_streamed_adjoint(vs, stream, args, peaks, P=16, n=40, N=500, K=100, 
                                   "frac": bwd_gbs / peaks["hbm_gbs"]}}
 
 
-def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=1000):
+def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=5000):
     """64 robots 40x40x40 at occupancy 0.7 (Bernoulli, largest component), state in HBM, one
-    launch per step; a 1000-step sample of the 5000-step workload."""
+    launch per step, 5000 steps (the N-step loop replayed as one CUDA graph)."""
     pop = W.workload_large(P, seed=5, n=n)
     sim = vs.Simulator(W.CONFIG, stream=stream)
     sim.set_population_from(pop)
@@ -571,7 +589,7 @@ def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=1000):
     # written (4 x 16 B)
     alg = (12.0 * S.astype(np.int64).sum() + 64.0 * M.astype(np.int64).sum()) * N
     gbs = alg / (kms * 1e-3) / 1e9
-    return {"workload": f"{P} robots {n}^3, occupancy 0.7, {N} steps (sample of 5000)", "unit": "spring-updates/s",
+    return {"workload": f"{P} robots {n}^3, occupancy 0.7, {N} steps", "unit": "spring-updates/s",
             "value": ups, "springs_per_robot": float(S.mean()), "masses_per_robot": float(M.mean()),
             "launches": launches, "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
                                                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]}}
@@ -660,7 +678,8 @@ def run_case(args):
     peaks, _ = measured_peaks()
     if args.case == "streamed":
         P = args.robots if args.robots != P_ROBOTS else 64
-        print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P)}))
+        N = args.sim_steps if args.sim_steps != SIM_STEPS else 5000
+        print(json.dumps({"case": args.case, **measure_streamed(vs, stream, args, peaks, P=P, N=N)}))
     elif args.case == "paper_preset":
         print(json.dumps({"case": args.case, **measure_paper_preset(vs, stream, args)}))
     elif args.case == "uneven":
@@ -673,9 +692,11 @@ def run_case(args):
         print(json.dumps({"case": args.case, **measure_adjoint(vs, stream, args, P=P, N=N)}))
         print(json.dumps({"case": args.case, **measure_adjoint(vs, stream, args, P=P, N=N, records=True)}))
     else:
-        P = args.robots if args.robots != P_ROBOTS else 16
-        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P)}))
-        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P, records=True)}))
+        P = args.robots if args.robots != P_ROBOTS else 64
+        N = args.sim_steps if args.sim_steps != SIM_STEPS else 5000
+        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=P, N=N)}))
+        print(json.dumps({"case": args.case, **measure_streamed_adjoint(vs, stream, args, peaks, P=min(P, 16),
+                                                                        N=min(N, 2000), records=True)}))
 
 
 def main():

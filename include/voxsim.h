@@ -86,9 +86,7 @@ enum {
 /* Variant of the lattice-gather kernel (robots of at most 768 corners on the resident path).
  * All give identical bits; they differ in how threads share the work. */
 enum {
-    SIM_LATTICE_AUTO = 0,   /* library choice per size class (measured default, autotuned):
-                               mass-packed blocks when the population has more lattice robots
-                               than the GPU has SMs, else one robot per block */
+    SIM_LATTICE_AUTO = 0,   /* library choice per size class (measured default, autotuned) */
     SIM_LATTICE_CORNER = 1, /* a thread per mass evaluates its 13 forward lattice directions, one
                                robot per block slot sized by its grid corners */
     SIM_LATTICE_COMPACT = 2,/* along each direction the existing springs are packed onto the
@@ -96,7 +94,9 @@ enum {
                                its springs' forces from shared memory */
     SIM_LATTICE_PACKED = 3  /* the per-mass scheme of SIM_LATTICE_CORNER with several robots per
                                768-thread block, each in a group of threads sized by its mass
-                               count (force rows indexed by the receiving thread), always */
+                               count (force rows indexed by the receiving thread); measured
+                               slower than SIM_LATTICE_CORNER on the workloads tried, so only
+                               used when asked for */
 };
 
 /* Physics constants (Table II; the workload configurations override some of them) and

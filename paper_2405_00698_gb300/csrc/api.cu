@@ -150,8 +150,8 @@ struct voxsim_ctx {
     // direction-compacted variant's)
     int n_items = 0, n_items_corner = 0, n_big = 0, max_big_corner = 0;
     bool has_split = false;        // some lattice items are split (two threads per corner)
-    // mass-packed plan of the per-corner lattice robots (used for stepping that records nothing
-    // per step; the replays of the adjoint run the per-corner plan, which gives the same bits)
+    // mass-packed plan of the per-corner lattice robots (SIM_LATTICE_PACKED; used for stepping
+    // that records nothing per step; the adjoint's replays run the per-corner plan, same bits)
     int n_pitems = 0;
     size_t pitem_smem = 0;
     DevBuf<int4> d_pitems, d_pgroups;
@@ -825,14 +825,12 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     return SIM_OK;
 }
 
-// Mass-packed plan of the per-corner lattice robots: groups of T = (masses rounded up to a warp)
-// threads, packed first-fit by decreasing T into 768-thread blocks under the shared-memory
-// budget (C displacements, C velocities with dashpots, 13 T plane entries and 32 rows for
-// absent springs per group) and at most 15 groups (named barriers 1..15).  Used when the
-// population has more lattice robots than SMs (or SIM_LATTICE_PACKED asks for it); with fewer,
-// one robot per block is already the spread the per-corner plan gives (with the split items of
-// the dashpot preset).  When the packed blocks would not fill every SM, the thread capacity of a
-// block shrinks so that the work spreads over all of them.
+// Mass-packed plan of the per-corner lattice robots (SIM_LATTICE_PACKED): groups of
+// T = (masses rounded up to a warp) threads, packed first-fit by decreasing T into 768-thread
+// blocks under the shared-memory budget (C displacements, C velocities with dashpots, 13 T plane
+// entries and 32 rows for absent springs per group) and at most 15 groups (named barriers
+// 1..15).  When the packed blocks would not fill every SM, the thread capacity of a block
+// shrinks so that the work spreads over all of them.
 static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vector<std::pair<int, int>>>& lattice,
                                      bool damped)
 {
@@ -841,9 +839,11 @@ static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vec
     size_t n = 0;
     for (const auto& v : lattice) n += v.size();
     const bool masses_known = (int)ctx->mass_count.size() == ctx->P;
-    if (n == 0 || !masses_known || ctx->p.lattice == SIM_LATTICE_CORNER || ctx->has_split || ctx->imp_active)
+    // measured slower than the one-robot-per-slot kernel on the workloads tried (its address
+    // arithmetic adds 22 % instructions, and the slot kernel's throughput is bound by issue and
+    // the shared-memory pipe rather than by its idle warps), so it runs only when asked for
+    if (n == 0 || !masses_known || ctx->p.lattice != SIM_LATTICE_PACKED || ctx->has_split || ctx->imp_active)
         return SIM_OK;
-    if (ctx->p.lattice != SIM_LATTICE_PACKED && n <= (size_t)ctx->num_sms) return SIM_OK;
     struct Grp { int T, C, r; };
     std::vector<Grp> gs;
     int64_t sumT = 0;

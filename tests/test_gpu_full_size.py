@@ -3,9 +3,11 @@ robots the FP64 oracle recomputes one by one:
 
 * 1024 MLP genomes on 8x8x8 grids, decode + 10,000 steps in one call (one lattice launch);
 * 4096 uneven robots after the autotuner's choices, 5000 steps;
-* 64 robots of 40x40x40 on the streamed path (one graph-captured launch per step), a 300-step
-  sample of the 5000-step run;
-* the adjoint of 512 robots of 8x8x8 over 2000 steps with checkpoints every 100.
+* 64 robots of 40x40x40 on the streamed path (one graph-captured launch per step), the first
+  1000 steps of the 5000-step run;
+* the adjoint of 512 robots of 8x8x8 with checkpoints every 100, along the FP64 oracle's
+  contact modes (imposed on the sampled robots), at 500 steps (meets the bar) and at the stated
+  2000 steps (held to the stated bar, which it does not meet: expected failure, with numbers).
 
 Robots are sampled evenly over the spring-count order.  The simulation is compared from the
 GPU's own decoded grid and weights (the decode is checked separately on the same genomes).
@@ -106,7 +108,7 @@ def test_uneven_population_full_size(vs, orc):
 
 def test_large_robots_full_size_sample(vs, orc):
     pop = W.workload_large()
-    N = 300
+    N = 1000
     sim = vs.Simulator(PHYS)
     sim.set_population_from(pop)
     sim.step(N)
@@ -121,33 +123,6 @@ def test_large_robots_full_size_sample(vs, orc):
     xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
     offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick])])
     check_population(orc, sub, PHYS, N, f[pick], xs, offs, ref, K=2)
-
-
-def test_adjoint_full_size_sample(vs, orc):
-    import torch
-    rng = np.random.default_rng(3)
-    P, N, K = 512, 2000, 100
-    pop = W.population_uniform(P, (8, 8, 8), seed=3)
-    w, kappa, phi = W.voxel_params(rng, pop)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    sim = vs.Simulator(PHYS)
-    sim.set_checkpointing(K)
-    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
-    sim.step(N)
-    _, S = sim.counts()
-    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
-    sim.backward(t(np.ones(P)), *g)
-    torch.cuda.synchronize()
-    g = [a.cpu().numpy() for a in g]
-    sim.close()
-    bad = []
-    for r in W.stratified_subset(S, 3):
-        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
-        _, rw, rk, rp = orc.adjoint(pop.grid(r), (8, 8, 8), PHYS, N, 1.0, w[a:b], kappa[a:b], phi[a:b])
-        errs = [float(np.abs(x[a:b] - y).max() / max(np.abs(y).max(), 1e-30)) for x, y in zip(g, (rw, rk, rp))]
-        if max(errs) > 1e-3:
-            bad.append((r, errs))
-    assert len(bad) <= 1, bad
 
 
 def test_trajectory_records_full_size(vs):
@@ -179,142 +154,108 @@ def test_trajectory_records_full_size(vs):
         assert np.abs(y - x).max() <= 1e-5 * np.abs(x).max()
 
 
-def _fd_pair(args):
-    """FP64 oracle fitness at theta +- h for one parameter (run in a worker process)."""
-    from oracle import oracle as orc_mod
-    grid, dims, n, base, name, v, h = args
+def _oracle_run(args):
+    """The oracle's FP64 run of one robot: its contact modes (mass order), mass corners and adjoint."""
+    from oracle import oracle as o
+    grid, base, n = args
+    _, modes, _ = o.fitness_after_modes(grid, (8, 8, 8), PHYS, n, **base)
+    _, gw, gk, gp = o.adjoint(grid, (8, 8, 8), PHYS, n, **base)
+    mc = o.Robot(grid, (8, 8, 8), PHYS, **base).topology()["mass_corner"]
+    return modes, mc, {"w": gw, "kappa": gk, "phi": gp}
+
+
+def _fd_along(args):
+    """FP64 central difference of the fitness along imposed contact modes."""
+    from oracle import oracle as o
+    grid, base, name, v, h, modes, n = args
     ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
     am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
-    fp, hp = orc_mod.fitness_after(grid, dims, PHYS, n, **ap)
-    fm, hm = orc_mod.fitness_after(grid, dims, PHYS, n, **am)
-    return fp, fm, hp == hm
+    fp, _, _ = o.fitness_after_modes(grid, (8, 8, 8), PHYS, n, force=modes, **ap)
+    fm, _, _ = o.fitness_after_modes(grid, (8, 8, 8), PHYS, n, force=modes, **am)
+    return (fp - fm) / (2 * h)
 
 
-def test_adjoint_full_size_finite_differences(vs, orc):
-    """The gradient at full size (512 robots 8x8x8, 2000 steps, checkpoints every 100) against
-    FP64 central finite differences (h = 1e-6) of the oracle on 32 random parameters of each of
-    two sampled robots; parameter pairs whose +h and -h runs take different contact-mode
-    sequences are not differentiable there and are skipped (and counted).
-
-    The adjoint differentiates the float32 trajectory it ran, with that trajectory's contact
-    modes; over 2000 steps some stick/slip decisions of the float32 run differ from the FP64
-    run's, and the gradient follows them.  So at this size a majority of the parameters meets
-    1e-3 (the shorter runs of tests/test_gpu_adjoint.py meet it throughout) and every one stays
-    within 1e-1 (measured: 39 of 64 within 1e-3, the largest error 8.6e-2)."""
+def adjoint_along_oracle_modes(vs, orc, N, n_robots=8, n_params=32, K=100):
+    """The differentiation workload (512 robots 8x8x8, per-voxel w, kappa, phi, checkpoints every
+    K): the FP64 oracle runs n_robots robots sampled over the spring-count order, its contact
+    modes are imposed on those robots of the GPU run, and the GPU gradient is compared with
+    (a) FP64 central differences (h = 1e-6) along the same modes on n_params random parameters
+    per robot: |g - fd| / max(|fd|, 1e-3 max|g|) per sample, and (b) the oracle's FP64 adjoint:
+    max |g - g_ref| / max |g_ref| per robot and parameter kind.  Returns both error lists."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import torch
     rng = np.random.default_rng(3)
-    P, N, K = 512, 2000, 100
+    P = 512
     pop = W.population_uniform(P, (8, 8, 8), seed=3)
     w, kappa, phi = W.voxel_params(rng, pop)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    sim = vs.Simulator(PHYS)
-    sim.set_checkpointing(K)
-    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
-    sim.step(N)
-    _, S = sim.counts()
-    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
-    sim.backward(t(np.ones(P)), *g)
-    torch.cuda.synchronize()
-    g = dict(zip(("w", "kappa", "phi"), (a.cpu().numpy() for a in g)))
-    sim.close()
-    pick_rng = np.random.default_rng(44)
-    jobs, meta = [], []
-    for r in W.stratified_subset(S, 2):
-        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
-        kept = np.flatnonzero(orc.lcc(pop.grid(r), (8, 8, 8)) > 0)
-        base = {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
-                "phi": phi[a:b].astype(np.float64)}
-        for _ in range(32):
-            name = ("w", "kappa", "phi")[pick_rng.integers(3)]
-            v = int(pick_rng.choice(kept))
-            h = 1e-6 * max(1.0, abs(base[name][v]))
-            jobs.append((pop.grid(r), (8, 8, 8), N, base, name, v, h))
-            meta.append((r, a, name, v, h))
-    with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_fd_pair, jobs))
-    checked, failed, skipped = 0, [], 0
-    for (r, a, name, v, h), (fp, fm, same) in zip(meta, res):
-        if not same:
-            skipped += 1
-            continue
-        fd = (fp - fm) / (2 * h)
-        gr = g[name][a:a + 512]
-        scale = max(abs(fd), 1e-3 * np.abs(gr).max())
-        checked += 1
-        if abs(gr[v] - fd) > 1e-3 * scale:
-            failed.append((r, name, v, float(gr[v]), fd))
-    errs = sorted(abs(gg - fd) / max(abs(fd), 1e-3 * np.abs(g[name]).max()) for (_, name, _, gg, fd) in failed)
-    assert checked >= 16, (checked, skipped)
-    assert len(failed) <= checked // 2, errs
-    assert not errs or errs[-1] <= 1e-1, errs
-
-
-def _fd_pair_forced(args):
-    """FP64 oracle fitness at theta +- h along an imposed contact-mode sequence."""
-    from oracle import oracle as orc_mod
-    grid, dims, n, base, name, v, h, modes = args
-    ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
-    am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
-    fp, _, _ = orc_mod.fitness_after_modes(grid, dims, PHYS, n, force=modes, **ap)
-    fm, _, _ = orc_mod.fitness_after_modes(grid, dims, PHYS, n, force=modes, **am)
-    return fp, fm
-
-
-def test_adjoint_full_size_along_the_gpu_contact_modes(vs, orc):
-    """The same full-size gradient against FP64 central differences taken along the contact
-    modes the GPU run took (sim_get_contact_modes): with the stick/slip decisions shared, both
-    sides differentiate the same piecewise-smooth map.  What remains is the float32 trajectory
-    the gradient is linearised along, which after 2000 steps sits ~1e-4 away from the FP64 one:
-    measured 51 of 64 parameters within 1e-3, the rest within 4.3e-3 but one at 2.8e-2 (against
-    12 within 4e-3 ... 8.6e-2 without the shared modes)."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    import torch
-    rng = np.random.default_rng(3)
-    P, N, K = 512, 2000, 100
-    pop = W.population_uniform(P, (8, 8, 8), seed=3)
-    w, kappa, phi = W.voxel_params(rng, pop)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    sim = vs.Simulator(PHYS)
-    sim.set_checkpointing(K)
-    sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
-    sim.step(N)
-    _, S = sim.counts()
-    g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
-    sim.backward(t(np.ones(P)), *g)
-    torch.cuda.synchronize()
-    g = dict(zip(("w", "kappa", "phi"), (a.cpu().numpy() for a in g)))
-    picks = W.stratified_subset(S, 2)
-    corner_modes = {r: sim.contact_modes(r, N) for r in picks}
-    sim.close()
-    pick_rng = np.random.default_rng(45)
-    jobs, meta = [], []
+    S = np.array([orc.Robot(pop.grid(r), (8, 8, 8), PHYS).S for r in range(P)])
+    picks = W.stratified_subset(S, n_robots)
+    bases = {}
     for r in picks:
         a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
-        base = {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
-                "phi": phi[a:b].astype(np.float64)}
-        R = orc.Robot(pop.grid(r), (8, 8, 8), PHYS, **base)
-        mass_corner = R.topology()["mass_corner"]
-        modes = np.ascontiguousarray(corner_modes[r][:, mass_corner])
-        assert (modes != 0).any()
-        kept = np.flatnonzero(orc.lcc(pop.grid(r), (8, 8, 8)) > 0)
-        for _ in range(32):
-            name = ("w", "kappa", "phi")[pick_rng.integers(3)]
-            v = int(pick_rng.choice(kept))
-            h = 1e-6 * max(1.0, abs(base[name][v]))
-            jobs.append((pop.grid(r), (8, 8, 8), N, base, name, v, h, modes))
-            meta.append((r, a, name, v, h))
+        bases[r] = {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
+                    "phi": phi[a:b].astype(np.float64)}
     with cf.ProcessPoolExecutor(max_workers=16, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_fd_pair_forced, jobs))
-    failed = []
-    for (r, a, name, v, h), (fp, fm) in zip(meta, res):
-        fd = (fp - fm) / (2 * h)
+        runs = dict(zip(picks, ex.map(_oracle_run, [(pop.grid(r), bases[r], N) for r in picks])))
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        sim = vs.Simulator(PHYS)
+        sim.set_checkpointing(K)
+        sim.set_population(pop.dims, (t(pop.mats), t(w), t(kappa), t(phi)), vs.MODE_PARAMS)
+        for r in picks:
+            modes, mc, _ = runs[r]
+            corner_modes = np.zeros((N, 729), np.uint8)
+            corner_modes[:, mc] = modes
+            sim.impose_contact_modes(r, corner_modes)
+        sim.step(N)
+        g = [torch.empty(pop.mats.size, device="cuda") for _ in range(3)]
+        sim.backward(t(np.ones(P)), *g)
+        torch.cuda.synchronize()
+        g = dict(zip(("w", "kappa", "phi"), (a.cpu().numpy().astype(np.float64) for a in g)))
+        sim.close()
+        pick_rng = np.random.default_rng(44)
+        jobs, meta, adj_err = [], [], []
+        for r in picks:
+            a = pop.voxel_off[r]
+            modes, _, ref = runs[r]
+            for name in ("w", "kappa", "phi"):
+                gr = g[name][a:a + 512]
+                adj_err.append(float(np.abs(gr - ref[name]).max() / np.abs(ref[name]).max()))
+            kept = np.flatnonzero(orc.lcc(pop.grid(r), (8, 8, 8)) > 0)
+            for _ in range(n_params):
+                name = ("w", "kappa", "phi")[pick_rng.integers(3)]
+                v = int(pick_rng.choice(kept))
+                h = 1e-6 * max(1.0, abs(bases[r][name][v]))
+                jobs.append((pop.grid(r), bases[r], name, v, h, modes, N))
+                meta.append((a, name, v))
+        fds = list(ex.map(_fd_along, jobs))
+    fd_err = []
+    for (a, name, v), fd in zip(meta, fds):
         gr = g[name][a:a + 512]
-        scale = max(abs(fd), 1e-3 * np.abs(gr).max())
-        if abs(gr[v] - fd) > 1e-3 * scale:
-            failed.append((r, name, v, float(gr[v]), fd, abs(gr[v] - fd) / scale))
-    errs = sorted(float("%.3g" % e[-1]) for e in failed)
-    assert len(failed) <= len(res) // 4, f"{len(failed)} of {len(res)} beyond 1e-3, largest {errs[-3:]}"
-    assert not errs or errs[-1] <= 5e-2, errs[-3:]
+        fd_err.append(abs(gr[v] - fd) / max(abs(fd), 1e-3 * np.abs(gr).max()))
+    return np.asarray(fd_err), np.asarray(adj_err)
+
+
+def test_adjoint_full_population_500_steps(vs, orc):
+    """The whole differentiation population at a 500-step horizon, along the oracle's contact
+    modes: at least 95 % of 256 sampled parameters within 1e-3 of the FP64 differences, and every
+    sampled robot's gradient within 1e-3 of the oracle's adjoint (max norm per kind)."""
+    fd_err, adj_err = adjoint_along_oracle_modes(vs, orc, 500)
+    assert np.mean(fd_err <= 1e-3) >= 0.95, np.sort(fd_err)[-8:]
+    assert adj_err.max() <= 1e-3, adj_err
+
+
+@pytest.mark.xfail(strict=False, reason=(
+    "the stated bar (1e-3 against FP64 differences) is not met at the 2000-step horizon: along "
+    "the oracle's contact modes about 86 % of sampled parameters are within 1e-3 (median 8e-5, "
+    "95th percentile 5e-3); a float32-sized change of the inputs alone moves the FP64 gradient "
+    "by up to 3e-4 along fixed modes (tests/test_oracle_gradient_conditioning.py), and a float32 "
+    "run makes such roundings at every step"))
+def test_adjoint_full_size_meets_the_stated_bar(vs, orc):
+    """The differentiation workload as stated (512 robots 8x8x8, 2000 steps, checkpoints every
+    100), along the oracle's contact modes, held to the stated bar: at least 95 % of 256 sampled
+    parameters within 1e-3 of the FP64 differences."""
+    fd_err, adj_err = adjoint_along_oracle_modes(vs, orc, 2000)
+    print(f"within 1e-3: {np.mean(fd_err <= 1e-3):.3f} of {fd_err.size}; quantiles 50/90/95/100 %: "
+          f"{np.quantile(fd_err, [0.5, 0.9, 0.95, 1.0])}; adjoint max-norm errors {np.sort(adj_err)[-3:]}")
+    assert np.mean(fd_err <= 1e-3) >= 0.95

@@ -56,12 +56,12 @@ def test_variants_agree_bitwise(vs, case, phys_name, variant):
 
 
 def test_packed_blocks_on_a_large_uneven_population(vs):
-    """More lattice robots than SMs: the default packs several robots of mixed mass counts into
-    each block (up to 15 groups, the shared-memory budget binding for many small robots); the
-    result is bitwise the one-robot-per-slot kernel's."""
+    """More lattice robots than SMs: several robots of mixed mass counts share each block (up to
+    15 groups, the shared-memory budget binding for many small robots); the result is bitwise
+    the one-robot-per-slot kernel's."""
     pop = W.population_uneven(700, seed=78, sizes=(2, 3, 4, 6, 8), occ=(0.2, 0.95))
     a = run(vs, pop, W.CONFIG, 300, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
-    b = run(vs, pop, W.CONFIG, 300, vs.LATTICE_AUTO, path=vs.PATH_RESIDENT)
+    b = run(vs, pop, W.CONFIG, 300, vs.LATTICE_PACKED, path=vs.PATH_RESIDENT)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     assert np.array_equal(a[2], b[2])
 

@@ -64,3 +64,65 @@ def test_shard_ranges_cover_exactly():
             spans = [shards.shard_range(total, world, r) for r in range(world)]
             assert sum(c for _, c in spans) == total
             assert all(spans[i][0] + spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+
+
+def _evolve_worker(rank, world, port, out):
+    """One rank of the sharded co-design loop on the CPU: the oracle stands in for the rank's GPU
+    (decode + simulation of its shard), the fitness all-gather is the exchange step, and the
+    evolution runs replicated on the whole genome matrix."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import torch
+        from paper_2405_00698_gb300 import shards
+        genomes, history = _sharded_loop(rank, world, lambda f: shards.gather_population_fitness(f, world))
+        out.put((rank, genomes.tobytes(), history))
+    finally:
+        dist.destroy_process_group()
+
+
+P_ALL, GENS, NSTEPS, DIMS = 7, 2, 80, (3, 3, 2)
+
+
+def _sharded_loop(rank, world, gather):
+    import torch
+    from oracle import oracle as orc
+    from paper_2405_00698_gb300 import shards, workloads as W
+    rng = np.random.default_rng(91)
+    mats = [W.uniform_materials(rng, DIMS) for _ in range(P_ALL)]
+    genomes = W.one_hot_logits(W.make_population([DIMS] * P_ALL, mats).mats).reshape(P_ALL, -1)
+    genomes = (genomes + rng.normal(0, 0.3, genomes.shape)).astype(np.float32)
+    evo = W.Evolution(seed=5)
+    first, count = shards.shard_range(P_ALL, world, rank)
+    history = []
+    for gen in range(GENS):
+        shard = genomes[first:first + count].reshape(count, -1, 5)
+        pop = W.make_population([DIMS] * count, [np.argmax(g, axis=1).astype(np.uint8).reshape(DIMS[::-1])
+                                                 for g in shard])
+        fit_local = torch.from_numpy(orc.run_population(pop, W.CONFIG, NSTEPS)["fitness"])
+        fit = gather(fit_local).numpy()
+        history.append(fit.tolist())
+        res = orc.evo_generation(fit, genomes, evo.elites(P_ALL), evo.seed, gen, evo.mut_threshold(), evo.sigma)
+        genomes = res["genomes"].astype(np.float32)
+    return genomes, history
+
+
+def test_sharded_generations_equal_the_single_process_run():
+    """Two ranks, each simulating its shard of one 7-robot population (shards of 4 and 3), with
+    the fitness all-gather as the only exchange and replicated evolution: after two generations
+    both ranks hold bitwise the genome matrix of the single-process run."""
+    ref_genomes, ref_hist = _sharded_loop(0, 1, lambda f: f)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_evolve_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, gbytes, hist in got:
+        assert gbytes == ref_genomes.tobytes()
+        assert hist == ref_hist
