@@ -246,9 +246,10 @@ def test_adjoint_full_population_500_steps(vs, orc):
 
 
 @pytest.mark.xfail(strict=False, reason=(
-    "the stated bar (1e-3 against FP64 differences) is not met at the 2000-step horizon: along "
-    "the oracle's contact modes about 86 % of sampled parameters are within 1e-3 (median 8e-5, "
-    "95th percentile 5e-3); a float32-sized change of the inputs alone moves the FP64 gradient "
+    "the stated bar (95 % of sampled parameters within 1e-3 of FP64 differences) is not met at "
+    "the 2000-step horizon: along the oracle's contact modes 91 % of 256 sampled parameters are "
+    "within 1e-3 (median 5e-5, 95th percentile 1.7e-3, largest 0.13; against the oracle's adjoint "
+    "up to 3e-3 in max norm); a float32-sized change of the inputs alone moves the FP64 gradient "
     "by up to 3e-4 along fixed modes (tests/test_oracle_gradient_conditioning.py), and a float32 "
     "run makes such roundings at every step"))
 def test_adjoint_full_size_meets_the_stated_bar(vs, orc):
