@@ -445,50 +445,33 @@ def measure_adjoint(vs, stream, args, P=512, N=2000, K=100, records=False):
 
 def measure_lamarckian(vs, stream, args, P=512, N=2000, K=100):
     """Gradient-assisted co-design generation on 512 robots 8x8x8 (per-voxel parameter genome
-    rows, fixed morphology): forward with checkpoints, fitness, adjoint of the elites' fitness,
-    Lamarckian gradient step on the elites, genetic operators.  Generations per second."""
+    rows, fixed morphology): forward with checkpoints, fitness, the elites picked on the GPU as
+    adjoint weights, adjoint of the elites' summed fitness, Lamarckian gradient step, genetic
+    operators -- no host round trip.  Generations per second."""
     import torch
+    from paper_2405_00698_gb300 import codesign
     rng = np.random.default_rng(3)
     pop = W.population_uniform(P, (8, 8, 8), seed=3)
     w, kappa, phi = W.voxel_params(rng, pop)
     V = 512
     rows = np.concatenate([w.reshape(P, V), kappa.reshape(P, V), phi.reshape(P, V)], axis=1)
     g = torch.from_numpy(np.ascontiguousarray(rows, dtype=np.float32)).cuda()
-    g2 = torch.empty_like(g)
     mats = torch.from_numpy(np.ascontiguousarray(pop.mats)).cuda()
     sim = vs.Simulator(W.CONFIG, stream=stream)
-    sim.set_checkpointing(K)
     evo = W.Evolution()
-    E = evo.elites(P)
-    fit = torch.empty(P, dtype=torch.float64, device="cuda")
-    gw, gk, gp = (torch.empty(P * V, device="cuda") for _ in range(3))
-    inf = float("inf")
-    lo = torch.tensor([0.0] * V + [0.0] * V + [-inf] * V, device="cuda")
-    hi = torch.tensor([1.0] * V + [inf] * V + [inf] * V, device="cuda")
-    dl = torch.zeros(P, dtype=torch.float64, device="cuda")
-    state = {"gen": 0, "in": g, "out": g2}
+    state = {"gen": 0, "g": g}
 
     def generation():
-        sim.set_population(pop.dims, (mats, state["in"]), vs.MODE_PARAM_ROWS)
-        sim.step(N)
-        sim.fitness(fit)
-        f = fit.cpu().numpy()                         # the elite rows are chosen on the host
-        key = np.where(np.isnan(f), -np.inf, f)
-        elite = [int(r) for r in np.argsort(-key, kind="stable")[:E] if np.isfinite(f[r])]
-        dl_h = np.zeros(P)
-        dl_h[elite] = 1.0
-        dl.copy_(torch.from_numpy(dl_h))
-        sim.backward(dl, gw, gk, gp)
-        sim.evo_gradient_step(state["in"], gw, gk, gp, (0.02, 50.0, 0.1), rows=elite, lo=lo, hi=hi)
-        sim.evo_generation(fit, state["in"], state["out"], evo, state["gen"])
+        _, state["g"] = codesign.run_lamarckian(sim, mats, state["g"], (8, 8, 8), 1, N, evo,
+                                                eta=(0.02, 50.0, 0.1), checkpoint=K,
+                                                first_generation=state["gen"], log=False)
         state["gen"] += 1
-        state["in"], state["out"] = state["out"], state["in"]
     generation()                                      # warm-up
     ms = _timed(stream, generation)
     _, S = sim.counts()
     sim.close()
     return {"workload": f"{P} robots 8x8x8, parameter genome rows, {N} steps, checkpoints every {K}, "
-                        f"gradient step on the {E} elites", "ms_per_generation": ms,
+                        f"gradient step on the {evo.elites(P)} elites picked on the GPU", "ms_per_generation": ms,
             "generations_per_s": 1e3 / ms,
             "forward_spring_updates_per_s": float(S.astype(np.int64).sum()) * N / (ms * 1e-3)}
 

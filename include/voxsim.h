@@ -279,6 +279,15 @@ sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t
                              int32_t n_rows, float eta_w, float eta_kappa, float eta_phi,
                              const float* lo, const float* hi);
 
+/* The elites of a generation as adjoint weights, on the GPU (gradient-assisted variant, project
+ * extension): robots are ranked as evo_generation ranks them (fitness descending, ties by
+ * ascending index, NaN as -infinity) and weights[r] = 1 for the E best robots whose fitness is
+ * finite, 0 for every other robot.  Passed to sim_backward as dL_df it gives the gradient of the
+ * elites' summed fitness; no host round trip is needed to pick them.  fitness, weights: double
+ * [P], device memory; enqueued on the context's stream.  Errors: SIM_EINVAL (null pointers, P
+ * outside 1..65535, E outside 0..P), SIM_ENOMEM. */
+sim_status evo_elite_weights(voxsim_ctx* ctx, const double* fitness, int32_t P, int32_t E, double* weights);
+
 /* Turn state checkpointing on (every k_steps steps, k_steps >= 1) or off (0).  While on, each
  * sim_step_n call records the state at its start and every k_steps steps after, which
  * sim_backward replays (device memory: two float4 per grid corner per checkpoint, plus during

@@ -103,7 +103,8 @@ def rank_order(f: np.ndarray) -> np.ndarray:
 
 def run_lamarckian(sim: "vs.Simulator", mats, genomes, dims: Sequence[int], generations: int,
                    steps: int, evo: W.Evolution = W.Evolution(), eta=(0.0, 0.0, 0.0),
-                   checkpoint: int = 100, bounds=None, first_generation: int = 0) -> tuple:
+                   checkpoint: int = 100, bounds=None, first_generation: int = 0,
+                   log: bool = True) -> tuple:
     """Gradient-assisted co-design on per-voxel parameter genomes (a project extension beside the
     paper's purely genetic loop): the morphology `mats` (CUDA uint8 [P * V]) stays fixed and each
     genome row is [w | kappa | phi] (CUDA float32 [P, 3V], updated in place).  Every generation:
@@ -111,7 +112,9 @@ def run_lamarckian(sim: "vs.Simulator", mats, genomes, dims: Sequence[int], gene
     move the elites one gradient step uphill (evo_gradient_step, per-segment steps `eta`, box
     `bounds` = (lo, hi) or the default of param_bounds), then breed the next generation with the
     unchanged genetic operators from the improved elites (their Gaussian mutation is not held to
-    the box).  Returns (records, final genomes)."""
+    the box).  log=False skips the per-generation records (their host reads).  The elites are picked on the GPU (evo_elite_weights): the loop never waits for the
+    host between generations except for the records it logs.  Returns (records, final
+    genomes)."""
     import torch
     P, G = genomes.shape
     V = G // 3
@@ -129,24 +132,23 @@ def run_lamarckian(sim: "vs.Simulator", mats, genomes, dims: Sequence[int], gene
         sim.set_population(d, (mats, cur), vs.MODE_PARAM_ROWS)
         sim.step(steps)
         sim.fitness(fit)
-        f = fit.cpu().numpy()
-        alive = f[np.isfinite(f)]
-        E = evo.elites(P)
-        elite = [int(r) for r in rank_order(f)[:E] if np.isfinite(f[r])]
-        dl_h = np.zeros(P)
-        dl_h[elite] = 1.0
-        dl.copy_(torch.from_numpy(dl_h))
-        if elite:
-            sim.backward(dl, gw, gk, gp)
-            sim.evo_gradient_step(cur, gw, gk, gp, eta, rows=elite, lo=lo, hi=hi)
-        _, S = sim.counts()
-        records.append(GenerationRecord(
-            generation=gen, best=float(alive.max()) if alive.size else float("-inf"),
-            mean=float(alive.mean()) if alive.size else float("nan"),
-            median=float(np.median(alive)) if alive.size else float("nan"),
-            dead=int(P - alive.size), genome_diversity=sim.diversity(cur)[0],
-            morphology_diversity=float("nan"), spring_updates=int(S.astype(np.int64).sum()) * steps,
-            evolution=evo))
+        diversity = sim.diversity(cur)[0] if log else float("nan")
+        # the elites' summed fitness as the adjoint's loss; every row takes the step (the others'
+        # gradients are zero, and the generation below keeps only the elites' rows)
+        sim.evo_elite_weights(fit, evo.elites(P), dl)
+        sim.backward(dl, gw, gk, gp)
+        sim.evo_gradient_step(cur, gw, gk, gp, eta, rows=None, lo=lo, hi=hi)
+        if log:
+            f = fit.cpu().numpy()
+            alive = f[np.isfinite(f)]
+            _, S = sim.counts()
+            records.append(GenerationRecord(
+                generation=gen, best=float(alive.max()) if alive.size else float("-inf"),
+                mean=float(alive.mean()) if alive.size else float("nan"),
+                median=float(np.median(alive)) if alive.size else float("nan"),
+                dead=int(P - alive.size), genome_diversity=diversity,
+                morphology_diversity=float("nan"), spring_updates=int(S.astype(np.int64).sum()) * steps,
+                evolution=evo))
         sim.evo_generation(fit, cur, other, evo, gen)
         cur, other = other, cur
     return records, cur

@@ -1236,6 +1236,20 @@ sim_status evo_generation(voxsim_ctx* ctx, const double* fitness, const float* g
     return SIM_OK;
 }
 
+sim_status evo_elite_weights(voxsim_ctx* ctx, const double* fitness, int32_t P, int32_t E, double* weights)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!fitness || !weights) return fail(SIM_EINVAL, "null argument");
+    if (P < 1 || P > 65535) return fail(SIM_EINVAL, "P must be in 1..65535");
+    if (E < 0 || E > P) return fail(SIM_EINVAL, "E must be in 0..P");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    VX_CK(ctx->d_order.ensure(P));
+    VX_LAUNCH(ctx, launch_evo_rank(fitness, P, ctx->d_order.p, s));
+    VX_LAUNCH(ctx, launch_elite_weights(ctx->d_order.p, fitness, P, E, weights, s));
+    return SIM_OK;
+}
+
 // Lamarckian gradient step on genome rows [w | kappa | phi] of the current population.
 sim_status evo_gradient_step(voxsim_ctx* ctx, float* genomes, int32_t P, int32_t G, const float* g_w,
                              const float* g_kappa, const float* g_phi, const int32_t* rows,

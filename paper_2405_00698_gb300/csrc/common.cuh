@@ -298,6 +298,8 @@ cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, 
                            float dead_bound, double* out, cudaStream_t s);
 
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s);
+cudaError_t launch_elite_weights(const int* order, const double* fitness, int P, int E, double* w,
+                                 cudaStream_t s);
 cudaError_t launch_evo_children(const float* gin, float* gout, const int* order, int P, int G,
                                 int E, uint64_t seed, uint64_t gen, uint32_t thresh, float sigma,
                                 uint32_t keep, int* parents, uint8_t* mask, cudaStream_t s);

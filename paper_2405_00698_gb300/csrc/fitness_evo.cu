@@ -193,6 +193,27 @@ cudaError_t launch_fitness(PopView pv, const int* mass_corner, const float4* u, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// dL/df weights of the E best robots in rank order (1 for the j-th ranked robot when j < E and
+// its fitness is finite, 0 for every other robot).
+__global__ void k_elite_weights(const int* __restrict__ order, const double* __restrict__ f, int P, int E,
+                                double* __restrict__ w)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const int r = order[j];
+    w[r] = (j < E && isfinite(f[r])) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_elite_weights(const int* order, const double* fitness, int P, int E, double* w, cudaStream_t s)
+{
+    k_elite_weights<<<(P + 255) / 256, 256, 0, s>>>(order, fitness, P, E, w);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s)
 {
     const int T = 256;

@@ -26,7 +26,7 @@ GENOME_LEN = 20998
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
            "sim_set_trajectory_records", "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
-           "sim_get_timing", "sim_check_status_words", "sim_impose_contact_modes")
+           "sim_get_timing", "sim_check_status_words", "sim_impose_contact_modes", "evo_elite_weights")
 
 
 class VoxsimError(RuntimeError):
@@ -109,6 +109,7 @@ def lib():
             "sim_get_timing": [vp, vp, vp],
             "sim_check_status_words": [vp],
             "sim_impose_contact_modes": [vp, i32, vp, i32],
+            "evo_elite_weights": [vp, vp, i32, i32, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -330,6 +331,14 @@ class Simulator:
                                     _ptr(genomes_out)[0], int(P), int(G), C.byref(e),
                                     int(generation), _ptr(parents)[0], _ptr(mask)[0]))
 
+
+    def evo_elite_weights(self, fitness, E: int, out):
+        """out[r] = 1 for the E best robots with finite fitness (evo_generation's rank order), else
+        0 (device f64 tensors [P]); the adjoint weights of the elites' summed fitness."""
+        P = fitness.shape[0]
+        self._sync_inputs(MEM_DEVICE)
+        _check(lib().evo_elite_weights(self._h, _ptr(fitness)[0], int(P), int(E), _ptr(out)[0]))
+        return out
 
     def evo_gradient_step(self, genomes, g_w, g_kappa, g_phi, eta, rows=None, lo=None, hi=None):
         """Lamarckian step on MODE_PARAM_ROWS genome rows (device f32 [P, 3V]) along sim_backward's

@@ -282,3 +282,27 @@ def test_backward_can_be_repeated_on_one_recorded_run(vs, path):
     sim.close()
     for g1, g3 in zip(*out):       # float32 sums: linear up to rounding, relative to the largest entry
         assert np.abs(g3 - 3.0 * g1).max() <= 1e-5 * np.abs(g3).max()
+
+
+def test_adjoint_through_saturated_slip(vs, orc):
+    """Table II's friction order (mu_s = 0.6 < mu_k = 1.0) without dashpots: contact corners pass
+    through saturated slip (the kinetic friction cancels the horizontal force), on the GPU as in
+    the oracle; the gradient along the oracle's modes matches the oracle's adjoint."""
+    phys = dataclasses.replace(PHYS, mu_s=0.6, mu_k=1.0)
+    rng = np.random.default_rng(69)
+    dims, nsteps = (4, 4, 4), 500
+    pop = W.population_uniform(4, dims, seed=69)
+    w, kappa, phi = W.voxel_params(rng, pop, phys)
+    impose, saturated = {}, False
+    for r in range(pop.P):
+        modes = oracle_corner_modes(orc, pop.grid(r), dims, nsteps, robot_params(pop, r, w, kappa, phi), phys)
+        saturated |= bool((modes == 3).any())
+        impose[r] = modes
+    assert saturated, "the runs must pass through saturated slip"
+    f, gw, gk, gp = gpu_grads(vs, pop, w, kappa, phi, nsteps, 100, phys=phys, impose=impose)
+    for r in range(pop.P):
+        a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+        fr, rw, rk, rp = orc.adjoint(pop.grid(r), dims, phys, nsteps, 1.0, w[a:b], kappa[a:b], phi[a:b])
+        errs = (rel_grad_err(gw[a:b], rw), rel_grad_err(gk[a:b], rk), rel_grad_err(gp[a:b], rp))
+        assert max(errs) <= GRAD_TOL, (r, errs)
+        assert abs(f[r] - fr) <= 1e-3 * max(abs(fr), 1e-3 * phys.edge), (r, f[r], fr)

@@ -163,3 +163,29 @@ def test_lamarckian_loop(vs):
     # (the box holds right after the gradient step; the children's Gaussian mutation may leave it)
     out = final.cpu().numpy()
     assert np.all(np.isfinite(out)) and not np.array_equal(out, rows)
+
+
+def test_elite_weights_follow_the_rank_order(vs):
+    """evo_elite_weights marks the E best robots with finite fitness in evo_generation's order:
+    fitness descending, ties by ascending index, NaN and -inf last (never elites)."""
+    import torch
+    from paper_2405_00698_gb300 import codesign
+    rng = np.random.default_rng(86)
+    f = np.round(rng.standard_normal(300), 1)
+    f[[3, 17, 40]] = np.nan
+    f[[5, 6]] = -np.inf
+    f[[7]] = np.inf
+    sim = vs.Simulator(PHYS)
+    for E in (0, 1, 75, 298, 300):
+        out = torch.full((300,), 7.0, dtype=torch.float64, device="cuda")
+        sim.evo_elite_weights(torch.from_numpy(f).cuda(), E, out)
+        torch.cuda.synchronize()
+        want = np.zeros(300)
+        for r in codesign.rank_order(f)[:E]:
+            if np.isfinite(f[r]):
+                want[r] = 1.0
+        assert np.array_equal(out.cpu().numpy(), want), E
+    with pytest.raises(vs.VoxsimError):
+        sim.evo_elite_weights(torch.zeros(4, dtype=torch.float64, device="cuda"), 5,
+                              torch.zeros(4, dtype=torch.float64, device="cuda"))
+    sim.close()

@@ -614,3 +614,33 @@ def test_simulate_with_imposed_modes_repeats_the_free_run(orc):
     stuck.simulate_modes(hold)
     x1, _ = stuck.state()
     assert np.array_equal(x1[x0[:, 2] == 0.0, :2], x0[x0[:, 2] == 0.0, :2])
+
+
+def test_adjoint_through_saturated_slip_matches_fd(orc):
+    """With Table II's friction order (mu_s = 0.6 < mu_k = 1.0, no dashpots) contact corners pass
+    through the saturated-slip mode (kinetic friction cancelling the horizontal force); along the
+    run's fixed modes FP64 central differences match the oracle's adjoint there too."""
+    phys = dataclasses.replace(PHYS, mu_s=0.6, mu_k=1.0)
+    rng = np.random.default_rng(23)
+    dims, n = (3, 3, 3), 600
+    mat = W.uniform_materials(rng, dims)
+    mat[0, :, :] = np.maximum(mat[0, :, :], 1)
+    V = mat.size
+    w = rng.uniform(0.5, 1.0, V); kappa = np.asarray(phys.k_mat)[mat.reshape(-1)].astype(float)
+    phi = np.asarray(phys.phase_mat)[mat.reshape(-1)] + rng.uniform(-0.5, 0.5, V)
+    _, modes, _ = orc.fitness_after_modes(mat, dims, phys, n, w, kappa, phi)
+    assert (modes == 3).any(), "the run must pass through saturated slip"
+    _, gw, gk, gp = orc.adjoint(mat, dims, phys, n, 1.0, w, kappa, phi)
+    grads = {"w": gw, "kappa": gk, "phi": gp}
+    base = {"w": w, "kappa": kappa, "phi": phi}
+    occ = np.flatnonzero(orc.lcc(mat, dims) > 0)
+    for name in ("w", "kappa", "phi"):
+        for v in rng.choice(occ, 5, replace=False):
+            h = 1e-6 * max(1.0, abs(base[name][v]))
+            ap = dict(base); ap[name] = base[name].copy(); ap[name][v] += h
+            am = dict(base); am[name] = base[name].copy(); am[name][v] -= h
+            fp, _, _ = orc.fitness_after_modes(mat, dims, phys, n, force=modes, **ap)
+            fm, _, _ = orc.fitness_after_modes(mat, dims, phys, n, force=modes, **am)
+            fd = (fp - fm) / (2 * h)
+            scale = max(abs(fd), 1e-3 * np.abs(grads[name]).max())
+            assert abs(grads[name][v] - fd) <= 1e-5 * scale, (name, int(v), grads[name][v], fd)
