@@ -80,3 +80,24 @@ def check_population(orc, pop, phys, nsteps, f_gpu, x_gpu, off, ref, w=None, kap
     assert len(sensitive) <= max(1, int(max_sensitive_frac * pop.P)), \
         f"too many robots only within the perturbation envelope: {sensitive}"
     return sensitive
+
+
+def oracle_corner_modes(orc, grid, dims, nsteps, base, phys=None):
+    """The contact modes of the oracle's FP64 run of one robot, laid out [nsteps][grid corners]
+    (0 where no mass) as sim_impose_contact_modes takes them."""
+    if phys is None:
+        from paper_2405_00698_gb300 import workloads
+        phys = workloads.CONFIG
+    _, modes, _ = orc.fitness_after_modes(grid, dims, phys, nsteps, **base)
+    mc = orc.Robot(grid, dims, phys, **base).topology()["mass_corner"]
+    C = int(np.prod(np.asarray(dims) + 1))
+    out = np.zeros((nsteps, C), np.uint8)
+    out[:, mc] = modes
+    return out
+
+
+def robot_params(pop, r, w, kappa, phi):
+    """Robot r's per-voxel (w, kappa, phi) as FP64 arrays for the oracle."""
+    a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
+    return {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
+            "phi": phi[a:b].astype(np.float64)}

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 from paper_2405_00698_gb300 import workloads as W
+from tests.parity import oracle_corner_modes, robot_params
 
 pytestmark = pytest.mark.gpu
 PHYS = W.CONFIG
@@ -29,22 +30,6 @@ def vs():
     from paper_2405_00698_gb300 import build, voxsim
     build.build()
     return voxsim
-
-
-def oracle_corner_modes(orc, grid, dims, nsteps, base, phys=PHYS):
-    """The contact modes of the oracle's FP64 run, [nsteps][grid corners] (0 where no mass)."""
-    _, modes, _ = orc.fitness_after_modes(grid, dims, phys, nsteps, **base)
-    mc = orc.Robot(grid, dims, phys, **base).topology()["mass_corner"]
-    C = int(np.prod(np.asarray(dims) + 1))
-    out = np.zeros((nsteps, C), np.uint8)
-    out[:, mc] = modes
-    return out
-
-
-def robot_params(pop, r, w, kappa, phi):
-    a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
-    return {"w": w[a:b].astype(np.float64), "kappa": kappa[a:b].astype(np.float64),
-            "phi": phi[a:b].astype(np.float64)}
 
 
 def gpu_grads(vs, pop, w, kappa, phi, nsteps, K, dL=None, phys=PHYS, impose=None):

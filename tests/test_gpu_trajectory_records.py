@@ -31,12 +31,14 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def run(vs, pop, w, kappa, phi, nsteps, K, records, modes_of=(), dL=None, repeat=1, **kw):
+def run(vs, pop, w, kappa, phi, nsteps, K, records, modes_of=(), dL=None, repeat=1, impose=None, **kw):
     import torch
     sim = vs.Simulator(PHYS, **kw)
     sim.set_checkpointing(K)
     sim.set_trajectory_records(records)
     sim.set_population(pop.dims, (_t(pop.mats), _t(w), _t(kappa), _t(phi)), vs.MODE_PARAMS)
+    for r, m in (impose or {}).items():
+        sim.impose_contact_modes(r, m)
     sim.step(nsteps)
     f = sim.fitness()
     modes = [sim.contact_modes(r, nsteps) for r in modes_of]
@@ -71,19 +73,21 @@ def test_records_equal_checkpointed_replay(vs, dims, nsteps, K):
 
 
 def test_records_match_oracle_adjoint(vs, orc):
+    """The replay-free sweep over kept records, along the oracle run's contact modes, against
+    the oracle's FP64 adjoint: every robot within the bar."""
+    from tests.parity import oracle_corner_modes, robot_params
     rng = np.random.default_rng(121)
     dims, nsteps = (4, 4, 4), 350
     pop = W.population_uniform(4, dims, seed=121)
     w, kappa, phi = W.voxel_params(rng, pop)
-    _, g, _ = run(vs, pop, w, kappa, phi, nsteps, 100, True)
-    bad = []
+    impose = {r: oracle_corner_modes(orc, pop.grid(r), dims, nsteps, robot_params(pop, r, w, kappa, phi))
+              for r in range(pop.P)}
+    _, g, _ = run(vs, pop, w, kappa, phi, nsteps, 100, True, impose=impose)
     for r in range(pop.P):
         a, b = pop.voxel_off[r], pop.voxel_off[r + 1]
         _, rw, rk, rp = orc.adjoint(pop.grid(r), dims, PHYS, nsteps, 1.0, w[a:b], kappa[a:b], phi[a:b])
         errs = [np.abs(x[a:b] - y).max() / max(np.abs(y).max(), 1e-30) for x, y in zip(g[0], (rw, rk, rp))]
-        if max(errs) > GRAD_TOL:
-            bad.append((r, errs))
-    assert len(bad) <= 1, bad
+        assert max(errs) <= GRAD_TOL, (r, errs)
 
 
 def test_records_repeatable_and_mixed_with_streamed_robots(vs):
