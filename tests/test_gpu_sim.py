@@ -235,3 +235,28 @@ def test_gather_mode_keeps_large_robots_deterministic(vs):
         out.append(sim.state()[0])
         sim.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_maximum_and_ragged_grids(vs, orc):
+    """Grids at the largest extent per axis (64): a sparse 64x64x64 robot (its largest component
+    on the streamed path), a 64-voxel rod along each axis, and a 1x64x2 sheet, in one population
+    with a small robot; 30 steps against the oracle."""
+    rng = np.random.default_rng(31)
+    dims = [(64, 64, 64), (64, 1, 1), (1, 64, 1), (1, 1, 64), (1, 64, 2), (3, 2, 2)]
+    grids = [W.bernoulli_grid(rng, dims[0], 0.35)] + [np.full(d[::-1], 4, np.uint8) for d in dims[1:]]
+    pop = W.make_population(dims, grids)
+    g, ref = run_both(vs, orc, pop, PHYS, 30)
+    assert np.array_equal(g["M"], ref["M"]) and np.array_equal(g["S"], ref["S"])
+    assert g["M"][0] > 20000
+    check_population(orc, pop, PHYS, 30, g["f"], g["x"], g["off"], ref)
+
+
+def test_empty_population(vs):
+    """A population of no robots: every call succeeds and does nothing."""
+    sim = vs.Simulator(PHYS)
+    sim.set_population(np.zeros((0, 3), np.int32), np.zeros(0, np.uint8))
+    sim.step(100)
+    assert sim.fitness().size == 0
+    M, S = sim.counts()
+    assert M.size == 0 and S.size == 0
+    sim.close()
