@@ -399,7 +399,8 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
             "batched_roofline": {"bound": "smem", "achieved": batched_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                                  "frac": batched_gbs / SMEM_PEAK_GBS},
             "autotune": {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
-                         "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted, 4 lattice cluster)": kinds.tolist(),
+                         "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted, 4 lattice cluster, "
+                         "5 lattice in mass-sized groups)": kinds.tolist(),
                          "atomic_threads": threads.tolist(), "seconds": tune_s},
             "plain": res["plain"], "batched_on_plain_sample": res["batched_same_sample"],
             "plain_roofline": {"bound": "hbm", "achieved": res["plain_gbs"], "peak": peaks["hbm_gbs"],

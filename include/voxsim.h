@@ -94,9 +94,10 @@ enum {
                                its springs' forces from shared memory */
     SIM_LATTICE_PACKED = 3  /* the per-mass scheme of SIM_LATTICE_CORNER with several robots per
                                768-thread block, each in a group of threads sized by its mass
-                               count (force rows indexed by the receiving thread); measured
-                               slower than SIM_LATTICE_CORNER on the workloads tried, so only
-                               used when asked for */
+                               count (force rows indexed by the receiving thread), also for
+                               robots of more than 768 corners but at most 768 masses; measured
+                               slower than SIM_LATTICE_CORNER on robots of up to 768 corners
+                               (the autotuner may still choose it for the larger ones) */
 };
 
 /* Physics constants (Table II; the workload configurations override some of them) and
@@ -368,7 +369,9 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
  * Robots are grouped by grid-corner count into 10 classes (up to 64, 128, 192, 256, 384, 768,
  * 1536, 2560, 5120 corners, and more).  For every class present in the population, each
  * admissible kernel (the lattice-gather kernel in its two variants, the cluster lattice kernel,
- * the atomic resident kernel at three block sizes, the streamed path) is timed on up to two robots per SM of that class for n_steps steps from
+ * the atomic resident kernel at three block sizes, the lattice kernel in mass-sized thread groups
+ * for sparse robots of more than 768 corners, the streamed path) is timed on up to two robots
+ * per SM of that class for n_steps steps from
  * the current state (CUDA events), and the fastest is kept for that class.  The state is
  * restored afterwards; the choices persist for later populations of this context.  The trial
  * runs record nothing: a recorded run (sim_step_n with checkpointing on) stays available to
@@ -377,7 +380,9 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
  * kernels.  kind_out / threads_out: int32 [10] host arrays (either may be NULL) receiving per
  * class 0 = lattice (per corner), 1 = atomic resident, 2 = streamed, 3 = lattice
  * (direction-compacted), 4 = cluster of lattice blocks (robots cut into slabs of whole corner
- * layers, one block each), and the atomic kernel's block size.
+ * layers, one block each), 5 = lattice in thread groups sized by mass count (robots of more than
+ * 768 corners but at most 768 masses; larger ones of the class take the atomic kernel, or the
+ * cluster when bit-reproducibility is required), and the atomic kernel's block size.
  * Synchronises the stream.  Errors: SIM_ESTATE without a population, SIM_EINVAL. */
 sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int32_t* threads_out);
 

@@ -118,7 +118,8 @@ int64_t full_springs(int nx, int ny, int nz)
 // Size classes by grid-corner count: the six lattice slot sizes, then larger bands.
 constexpr int kNumClasses = 10;
 constexpr int kClassCorners[kNumClasses] = {64, 128, 192, 256, 384, 768, 1536, 2560, 5120, 1 << 30};
-enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2, kKindLatticeCompact = 3, kKindCluster = 4 };
+enum { kKindLattice = 0, kKindAtomic = 1, kKindStreamed = 2, kKindLatticeCompact = 3, kKindCluster = 4,
+       kKindMassGroups = 5 };
 
 static int class_of(int corners)
 {
@@ -153,6 +154,7 @@ struct voxsim_ctx {
     // mass-packed plan of the per-corner lattice robots (SIM_LATTICE_PACKED; used for stepping
     // that records nothing per step; the adjoint's replays run the per-corner plan, same bits)
     int n_pitems = 0;
+    bool pitems_cover_corner = false;   // the per-corner robots are in the packed plan too
     size_t pitem_smem = 0;
     DevBuf<int4> d_pitems, d_pgroups;
     // imposed contact modes (sim_impose_contact_modes): per robot the offset of its table in
@@ -310,7 +312,7 @@ struct voxsim_ctx {
 extern "C" {
 static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subset = nullptr);
 static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vector<std::pair<int, int>>>& lattice,
-                                     bool damped);
+                                     const std::vector<int>& mass_groups, bool damped);
 }
 
 namespace {
@@ -676,6 +678,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     std::vector<std::pair<int, std::pair<int, int>>> atomic;   // (threads, (-corners, robot))
     std::vector<int> streamed;
     std::vector<std::pair<int, int>> clustered;                  // (q, robot)
+    std::vector<int> mass_groups;                                // larger robots in mass-sized groups
     ctx->max_stream_corner = 0;
     const int nrob = subset ? (int)subset->size() : ctx->P;
     for (int ri = 0; ri < nrob; ++ri) {
@@ -686,6 +689,25 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         const bool fits_sm = C <= kResidentMaxCorner && resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget;
         const int q = cluster_q(nx, ny, nz);            // >= 2: the cluster lattice kernel can take it
         int kind = ctx->class_kind[k];
+        // SIM_LATTICE_PACKED asks for mass-sized groups wherever a robot fits them
+        if (ctx->p.lattice == SIM_LATTICE_PACKED && C > block) kind = kKindMassGroups;
+        // robots of more than a block's corners but at most a block's masses can run on the
+        // lattice kernel in mass-sized thread groups (deterministic); else the class's atomic
+        // alternative
+        if (kind == kKindMassGroups) {
+            const bool known = (int)ctx->mass_count.size() == ctx->P;
+            const int M = known ? ctx->mass_count[r] : 0;
+            const int T = (M + 31) / 32 * 32;
+            const size_t need = sizeof(float4) * ((damped ? 2 : 1) * (size_t)C + 13 * (size_t)T + 32);
+            if (C <= block) kind = lattice_default(ctx);
+            else if (known && M >= 1 && T <= block && need <= budget && ctx->ckpt_every == 0 &&
+                     ctx->p.accumulate != SIM_ACC_ATOMIC && ctx->p.path != SIM_PATH_STREAMED && !ctx->imp_active) {
+                mass_groups.push_back(r);
+                continue;
+            } else {
+                kind = ctx->p.accumulate == SIM_ACC_GATHER ? kKindCluster : kKindAtomic;
+            }
+        }
         if (ctx->p.path == SIM_PATH_STREAMED) kind = kKindStreamed;
         else if (ctx->p.accumulate == SIM_ACC_ATOMIC && (is_lattice(kind) || kind == kKindCluster)) kind = kKindAtomic;
         else if (ctx->p.accumulate == SIM_ACC_GATHER && kind == kKindAtomic) kind = k < 6 ? lattice_default(ctx) : kKindCluster;
@@ -763,7 +785,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
             if (split && !v.empty()) ctx->has_split = true;
         }
     }
-    if (sim_status st = build_packed_items(ctx, lattice, damped)) return st;
+    if (sim_status st = build_packed_items(ctx, lattice, mass_groups, damped)) return st;
     std::sort(atomic.begin(), atomic.end());
     std::vector<int> big;
     for (size_t i = 0; i < atomic.size();) {
@@ -832,33 +854,38 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
 // 1..15).  When the packed blocks would not fill every SM, the thread capacity of a block
 // shrinks so that the work spreads over all of them.
 static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vector<std::pair<int, int>>>& lattice,
-                                     bool damped)
+                                     const std::vector<int>& mass_groups, bool damped)
 {
     ctx->n_pitems = 0;
+    ctx->pitems_cover_corner = false;
     ctx->pitem_smem = 0;
-    size_t n = 0;
-    for (const auto& v : lattice) n += v.size();
     const bool masses_known = (int)ctx->mass_count.size() == ctx->P;
-    // measured slower than the one-robot-per-slot kernel on the workloads tried (its address
-    // arithmetic adds 22 % instructions, and the slot kernel's throughput is bound by issue and
-    // the shared-memory pipe rather than by its idle warps), so it runs only when asked for
-    if (n == 0 || !masses_known || ctx->p.lattice != SIM_LATTICE_PACKED || ctx->has_split || ctx->imp_active)
-        return SIM_OK;
+    // the per-corner robots join the packed plan only when asked for: measured slower than the
+    // one-robot-per-slot kernel on the workloads tried (its address arithmetic adds 22 %
+    // instructions, and the slot kernel's throughput is bound by issue and the shared-memory
+    // pipe rather than by its idle warps); robots of more than a block's corners come here when
+    // their size class chose mass-sized groups
+    const bool corner_too = masses_known && ctx->p.lattice == SIM_LATTICE_PACKED && !ctx->has_split &&
+                            !ctx->imp_active;
     struct Grp { int T, C, r; };
     std::vector<Grp> gs;
     int64_t sumT = 0;
     int maxT = 32;
-    for (const auto& v : lattice)
-        for (const auto& e : v) {
-            const int r = e.second, M = ctx->mass_count[r];
-            if (M <= 0) continue;                       // nothing to step
-            const int C = (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
-            const int T = (M + 31) / 32 * 32;
-            gs.push_back({T, C, r});
-            sumT += T;
-            maxT = std::max(maxT, T);
-        }
-    if (gs.empty()) return SIM_OK;
+    auto add = [&](int r) {
+        const int M = ctx->mass_count[r];
+        if (M <= 0) return;                             // nothing to step
+        const int C = (ctx->dims[3 * r] + 1) * (ctx->dims[3 * r + 1] + 1) * (ctx->dims[3 * r + 2] + 1);
+        const int T = (M + 31) / 32 * 32;
+        gs.push_back({T, C, r});
+        sumT += T;
+        maxT = std::max(maxT, T);
+    };
+    if (corner_too)
+        for (const auto& v : lattice)
+            for (const auto& e : v) add(e.second);
+    for (int r : mass_groups) add(r);
+    ctx->pitems_cover_corner = corner_too;
+    if (gs.empty()) { ctx->pitems_cover_corner = false; return SIM_OK; }
     std::sort(gs.begin(), gs.end(), [](const Grp& a, const Grp& b) {
         return a.T != b.T ? a.T > b.T : (a.C != b.C ? a.C > b.C : a.r < b.r);
     });
@@ -925,7 +952,7 @@ static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
 // records when they are kept, are written; every other caller steps without recording).
 static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
 {
-    if (ctx->n_items == 0) return SIM_OK;
+    if (ctx->n_items == 0 && ctx->n_pitems == 0) return SIM_OK;
     LatticeArgs a{};
     a.pv = ctx->view();
     a.corner_order = ctx->d_mass_corner.p;
@@ -958,15 +985,20 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
     VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, 2 * sizeof(int), ctx->stream));
     // per-corner variant: items [0, n_items_corner); direction-compacted variant: the rest
     const int n_corner = ctx->n_items_corner, n_spring = ctx->n_items - ctx->n_items_corner;
-    if (n_corner > 0 && ctx->n_pitems > 0 && !a.rec_u) {
-        // the same robots in mass-packed groups (identical bits; checkpoints written alike)
+    const bool packed = ctx->n_pitems > 0 && !a.rec_u;
+    if (packed) {
+        // mass-sized groups: robots of more than a block's corners, and the per-corner robots
+        // when the plan covers them (identical bits; checkpoints written alike)
         LatticeArgs b = a;
         b.items = ctx->d_pitems.p;
         b.groups = ctx->d_pgroups.p;
         b.n_items = ctx->n_pitems;
+        b.queue = ctx->d_queue.p + 1;
+        VX_CK(cudaMemsetAsync(b.queue, 0, sizeof(int), ctx->stream));
         VX_LAUNCH(ctx, launch_step_lattice_packed(b, std::min(ctx->n_pitems, ctx->num_sms), ctx->pitem_smem,
                                                   ctx->stream));
-    } else if (n_corner > 0) {
+    }
+    if (n_corner > 0 && !(packed && ctx->pitems_cover_corner)) {
         a.n_items = n_corner;
         VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_corner, ctx->num_sms), threads, smem, ctx->stream));
     }
@@ -974,6 +1006,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
         a.items = ctx->d_items.p + n_corner;
         a.n_items = n_spring;
         a.queue = ctx->d_queue.p + 1;
+        if (packed) VX_CK(cudaMemsetAsync(a.queue, 0, sizeof(int), ctx->stream));   // reused after the packed launch
         a.spack = ctx->d_spack.p;
         VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_spring, ctx->num_sms), threads, smem, ctx->stream));
     }
@@ -1734,6 +1767,9 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
         if (k >= 6 && ctx->p.path != SIM_PATH_STREAMED && cluster_q(ctx->dims[3 * sample[0]], ctx->dims[3 * sample[0] + 1],
                                                                    ctx->dims[3 * sample[0] + 2]) >= 2)
             cands.push_back({kKindCluster, 0});
+        if (k >= 6 && k < kNumClasses - 1 && ctx->p.accumulate != SIM_ACC_ATOMIC && ctx->ckpt_every == 0 &&
+            ctx->p.path != SIM_PATH_STREAMED)
+            cands.push_back({kKindMassGroups, 0});
         if (k >= 6 && ctx->p.path != SIM_PATH_RESIDENT) cands.push_back({kKindStreamed, 0});
         if (cands.size() < 2) continue;
         float best_ms = 1e30f;

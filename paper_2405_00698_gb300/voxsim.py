@@ -236,7 +236,8 @@ class Simulator:
     def autotune(self, n_steps: int = 50):
         """Time the admissible stepping kernels per size class and keep the fastest; returns
         (kind [10], threads [10]) with kind 0 lattice per corner, 1 atomic resident, 2 streamed,
-        3 lattice direction-compacted, 4 cluster of lattice blocks."""
+        3 lattice direction-compacted, 4 cluster of lattice blocks, 5 lattice in mass-sized
+        thread groups (sparse robots of more than 768 corners)."""
         kind = np.zeros(10, np.int32); threads = np.zeros(10, np.int32)
         _check(lib().sim_autotune(self._h, int(n_steps), kind.ctypes.data, threads.ctypes.data))
         return kind, threads

@@ -127,3 +127,40 @@ def test_autotune_reports_the_variant(vs):
     kinds, _ = sim.autotune(20)
     sim.close()
     assert set(int(k) for k in kinds[:6]) <= {0}
+
+
+def test_mass_groups_for_large_sparse_robots(vs, orc):
+    """Robots of more than 768 corners but at most 768 masses run on the lattice kernel in
+    mass-sized thread groups (SIM_LATTICE_PACKED asks for it; the autotuner may choose it): the
+    same bits as the other deterministic kernels for such robots (the cluster of lattice blocks
+    under bit-reproducible accumulation), and the oracle's trajectory."""
+    rng = np.random.default_rng(79)
+    dims = [(10, 10, 10), (12, 12, 8), (9, 11, 10), (12, 12, 12)]
+    grids = [W.connected_growth(rng, d, occ) for d, occ in zip(dims, (0.3, 0.25, 0.35, 0.2))]
+    pop = W.make_population(dims, grids)
+    sim = vs.Simulator(W.CONFIG)
+    sim.set_population_from(pop)
+    M, _ = sim.counts()
+    sim.close()
+    C = np.array([(a + 1) * (b + 1) * (c + 1) for a, b, c in dims])
+    assert np.all(C > 768) and np.all(M <= 768), (C, M)
+    a = run(vs, pop, W.CONFIG, 500, vs.LATTICE_PACKED, accumulate=vs.ACC_GATHER)
+    b = run(vs, pop, W.CONFIG, 500, vs.LATTICE_CORNER, accumulate=vs.ACC_GATHER)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    ref = orc.run_population(pop, W.CONFIG, 500, want_x=True)
+    check_population(orc, pop, W.CONFIG, 500, a[2], a[0], a[3], ref)
+
+
+def test_autotuner_may_choose_mass_groups(vs):
+    """On a population of large sparse robots the autotuner's candidates for their size classes
+    include the mass-sized groups (kind 5); whatever it picks, the run stays within the classes'
+    admissible kinds and keeps the fitness finite."""
+    pop = W.population_uneven(400, seed=80, sizes=(10, 12), occ=(0.2, 0.35))
+    sim = vs.Simulator(W.CONFIG)
+    sim.set_population_from(pop)
+    kinds, _ = sim.autotune(20)
+    sim.step(100)
+    f = sim.fitness()
+    sim.close()
+    assert set(int(k) for k in kinds[6:9]) <= {1, 2, 4, 5}
+    assert np.all(np.isfinite(f))
