@@ -370,7 +370,7 @@ sim_status sim_diversity(voxsim_ctx* ctx, const float* genomes, int32_t P, int32
  * 1536, 2560, 5120 corners, and more).  For every class present in the population, each
  * admissible kernel (the lattice-gather kernel in its two variants, the cluster lattice kernel,
  * the atomic resident kernel at three block sizes, the lattice kernel in mass-sized thread groups
- * for sparse robots of more than 768 corners, the streamed path) is timed on up to two robots
+ * for sparse robots of more than 768 corners, the streamed path) is timed on up to six robots
  * per SM of that class for n_steps steps from
  * the current state (CUDA events), and the fastest is kept for that class.  The state is
  * restored afterwards; the choices persist for later populations of this context.  The trial

@@ -636,12 +636,16 @@ static void default_choices(voxsim_ctx* ctx)
     for (int k = 0; k < kNumClasses; ++k) {
         const int C = std::min(kClassCorners[k], kResidentMaxCorner);
         const bool fits = resident_smem_bytes(C, 0, SIM_ACC_ATOMIC) <= budget && kClassCorners[k] <= kResidentMaxCorner;
-        // robots of up to 768 corners: one lattice block; larger: the atomic kernel when it fits
-        // (measured ahead of the cluster of lattice blocks, 47 against 63 ms on the uneven
-        // population's large robots), else streamed.  Bit-reproducible stepping takes the
-        // cluster of lattice blocks (ahead of the streamed path: 63 against 80 ms).
-        int kind = k < 6 ? lattice_default(ctx) : (fits ? kKindAtomic : kKindStreamed);
+        // robots of up to 768 corners: one lattice block; larger: the lattice kernel in
+        // mass-sized thread groups for those of at most 768 masses (measured 1.87x the atomic
+        // kernel's rate on the uneven population's 824 such robots: 9.1 against 17.0 ms for 500
+        // steps), the atomic kernel for the others while it fits (measured ahead of the cluster
+        // of lattice blocks, 47 against 63 ms on the uneven population's large robots), else
+        // streamed.  Bit-reproducible stepping takes the cluster of lattice blocks for robots of
+        // more than 768 masses (ahead of the streamed path: 63 against 80 ms).
+        int kind = k < 6 ? lattice_default(ctx) : (fits ? kKindMassGroups : kKindStreamed);
         if (kind == kKindAtomic && ctx->p.accumulate == SIM_ACC_GATHER) kind = kKindCluster;
+        if (kind == kKindMassGroups && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
         if (is_lattice(kind) && ctx->p.accumulate == SIM_ACC_ATOMIC) kind = kKindAtomic;
         ctx->class_kind[k] = kind;
         ctx->class_threads[k] = 0;
@@ -1751,7 +1755,9 @@ sim_status sim_autotune(voxsim_ctx* ctx, int32_t n_steps, int32_t* kind_out, int
         if (members[k].empty()) continue;
         std::sort(members[k].begin(), members[k].end());
         std::vector<int> sample;
-        for (size_t i = 0; i < members[k].size() && (int)i < 2 * ctx->num_sms; ++i) sample.push_back(members[k][i].second);
+        // up to six robots per SM of the class: enough waves that the tail of a launch, which a
+        // candidate splitting the class over two launches pays twice, does not decide the choice
+        for (size_t i = 0; i < members[k].size() && (int)i < 6 * ctx->num_sms; ++i) sample.push_back(members[k][i].second);
         const int Cmax = -members[k].front().first;
         const bool fits = Cmax <= kResidentMaxCorner && resident_smem_bytes(Cmax, 0, SIM_ACC_ATOMIC) <= budget;
         std::vector<std::pair<int, int>> cands;
