@@ -18,10 +18,14 @@ __device__ __forceinline__ void mass_adjoint(unsigned mode, float z, float2 fh, 
                                              float& luz, float& lvx, float& lvy, float& lvz, float& lFx,
                                              float& lFy, float& lFz, const StepConst& c)
 {
-    const float l1x = lvx + c.dt * lux, l1y = lvy + c.dt * luy, l1z = lvz + c.dt * luz;
-    const float kf = c.damping * c.dt_over_m;
-    const float fx = kf * l1x, fy = kf * l1y, fz = kf * l1z;
-    const float tx = c.damping * l1x, ty = c.damping * l1y, tz = c.damping * l1z;
+    // the transposes of integrate(): the constants as pairs, the damping as its complement
+    const float l1x = fmaf(c.dt, lux, fmaf(c.dt_lo, lux, lvx));
+    const float l1y = fmaf(c.dt, luy, fmaf(c.dt_lo, luy, lvy));
+    const float l1z = fmaf(c.dt, luz, fmaf(c.dt_lo, luz, lvz));
+    const float tx = fmaf(-c.damping_c, l1x, l1x), ty = fmaf(-c.damping_c, l1y, l1y),
+                tz = fmaf(-c.damping_c, l1z, l1z);
+    const float fx = fmaf(c.dt_over_m, tx, c.dtm_lo * tx), fy = fmaf(c.dt_over_m, ty, c.dtm_lo * ty),
+                fz = fmaf(c.dt_over_m, tz, c.dtm_lo * tz);
     if (mode == kFree) {
         lFx = fx; lFy = fy; lFz = fz;
         lvx = tx; lvy = ty; lvz = tz;
@@ -40,12 +44,12 @@ __device__ __forceinline__ void mass_adjoint(unsigned mode, float z, float2 fh, 
         const float fn = c.k_ground * -z;
         const float fhm = sqrtf(fh.x * fh.x + fh.y * fh.y);
         const float hx = fh.x / fhm, hy = fh.y / fhm;
-        const float rr = c.mu_k * fn / fhm;
+        const float rr = fmaf(c.mu_k, fn, c.mu_k_lo * fn) / fhm;
         const float ul = hx * fx + hy * fy;
         lFx = fx - rr * (fx - hx * ul);
         lFy = fy - rr * (fy - hy * ul);
         lFz = fz;
-        const float lfn = -c.mu_k * ul + fz;
+        const float lfn = -fmaf(c.mu_k, ul, c.mu_k_lo * ul) + fz;
         luz += -c.k_ground * lfn;
         lvx = tx; lvy = ty; lvz = tz;
     }

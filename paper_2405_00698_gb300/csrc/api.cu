@@ -292,6 +292,11 @@ struct voxsim_ctx {
         c.dt_over_m = (float)(p.dt / p.mass);
         c.weight = (float)(p.mass * p.gravity);
         c.damping = (float)p.damping;
+        c.dt_lo = (float)(p.dt - (double)c.dt);
+        c.dtm_lo = (float)(p.dt / p.mass - (double)c.dt_over_m);
+        c.weight_lo = (float)(p.mass * p.gravity - (double)c.weight);
+        c.damping_c = (float)(1.0 - p.damping);
+        c.mu_k_lo = (float)(p.mu_k - (double)(float)p.mu_k);
         c.k_ground = (float)p.k_ground;
         c.mu_s = (float)p.mu_s;
         c.mu_k = (float)p.mu_k;

@@ -48,6 +48,16 @@ struct StepConst {
     float dt_over_m;    // dt / mass
     float weight;       // mass * gravity
     float damping;
+    // the step constants carried past float32: a float32 dt, dt / m or m g is off by up to 3e-8
+    // of itself (0.999 by 1.3e-8), the same in every step, and at 2000 steps such a fixed
+    // offset of the map moves its gradients by more than 1e-3 of the largest entry; each is
+    // applied as a pair hi + lo (lo = the float32 of the remainder), the damping as
+    // c w = w - (1 - c) w with 1 - c in float32 (an error of 1e-11 of c)
+    float dt_lo;
+    float dtm_lo;
+    float weight_lo;
+    float damping_c;    // 1 - damping
+    float mu_k_lo;
     float k_ground;
     float mu_s;
     float mu_k;

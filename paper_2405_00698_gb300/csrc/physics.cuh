@@ -159,6 +159,22 @@ __device__ __forceinline__ void spring_dashpot(SpringEval& e, float dvx, float d
     e.gz = __fmaf_rn(fd, e.dz, e.gz);
 }
 
+// Semi-implicit Euler with velocity damping, v <- c (v + dt F / m), u <- u + dt v, with the
+// constants carried past float32 (see StepConst): w = v + (dt/m)_hi F + (dt/m)_lo F,
+// v = w - (1 - c) w, u = u + dt_hi v + dt_lo v.
+__device__ __forceinline__ void integrate(float4& u, float4& v, float Fx, float Fy, float Fz, const StepConst& c)
+{
+    const float wx = __fmaf_rn(c.dt_over_m, Fx, __fmaf_rn(c.dtm_lo, Fx, v.x));
+    const float wy = __fmaf_rn(c.dt_over_m, Fy, __fmaf_rn(c.dtm_lo, Fy, v.y));
+    const float wz = __fmaf_rn(c.dt_over_m, Fz, __fmaf_rn(c.dtm_lo, Fz, v.z));
+    v.x = __fmaf_rn(-c.damping_c, wx, wx);
+    v.y = __fmaf_rn(-c.damping_c, wy, wy);
+    v.z = __fmaf_rn(-c.damping_c, wz, wz);
+    u.x = __fmaf_rn(c.dt, v.x, __fmaf_rn(c.dt_lo, v.x, u.x));
+    u.y = __fmaf_rn(c.dt, v.y, __fmaf_rn(c.dt_lo, v.y, u.y));
+    u.z = __fmaf_rn(c.dt, v.z, __fmaf_rn(c.dt_lo, v.z, u.z));
+}
+
 // Contact modes of a mass in one step (kSlipHeld: slipping with the kinetic friction saturated at
 // the horizontal force it opposes).
 enum : unsigned { kFree = 0u, kStick = 1u, kSlip = 2u, kSlipHeld = 3u };
@@ -176,7 +192,7 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
                                                 const StepConst& c)
 {
     unsigned mode = kFree;
-    Fz = __fsub_rn(Fz, c.weight);
+    Fz = __fsub_rn(__fsub_rn(Fz, c.weight), c.weight_lo);
     const float z = __fadd_rn(u.w, u.z);
     if (c.ground_on && z < 0.f) {
         const float fn = __fmul_rn(c.k_ground, -z);
@@ -187,7 +203,7 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
             mode = kStick;
             Fx = 0.f; Fy = 0.f; v.x = 0.f; v.y = 0.f;
         } else {
-            const float r = __fdiv_rn(__fmul_rn(c.mu_k, fn), fh);
+            const float r = __fdiv_rn(__fmaf_rn(c.mu_k, fn, __fmul_rn(c.mu_k_lo, fn)), fh);
             if (r >= 1.0f) {
                 mode = kSlipHeld;
                 Fx = 0.f; Fy = 0.f;
@@ -199,12 +215,7 @@ __device__ __forceinline__ unsigned mass_update(float4& u, float4& v, float Fx, 
             }
         }
     }
-    v.x = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fx, v.x));
-    v.y = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fy, v.y));
-    v.z = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fz, v.z));
-    u.x = __fmaf_rn(c.dt, v.x, u.x);
-    u.y = __fmaf_rn(c.dt, v.y, u.y);
-    u.z = __fmaf_rn(c.dt, v.z, u.z);
+    integrate(u, v, Fx, Fy, Fz, c);
     return mode;
 }
 
@@ -220,7 +231,7 @@ __device__ __forceinline__ unsigned mass_update_imposed(float4& u, float4& v, fl
                                                         const StepConst& c, int forced)
 {
     if (forced < 0) return mass_update(u, v, Fx, Fy, Fz, c);
-    Fz = __fsub_rn(Fz, c.weight);
+    Fz = __fsub_rn(__fsub_rn(Fz, c.weight), c.weight_lo);
     if (forced != (int)kFree) {
         const float z = __fadd_rn(u.w, u.z);
         const float fn = __fmul_rn(c.k_ground, -z);
@@ -232,17 +243,12 @@ __device__ __forceinline__ unsigned mass_update_imposed(float4& u, float4& v, fl
             Fx = 0.f; Fy = 0.f;
         } else {
             const float fh = __fsqrt_rn(__fmaf_rn(Fy, Fy, __fmul_rn(Fx, Fx)));
-            const float s = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(c.mu_k, fn), fh));
+            const float s = __fsub_rn(1.0f, __fdiv_rn(__fmaf_rn(c.mu_k, fn, __fmul_rn(c.mu_k_lo, fn)), fh));
             Fx = __fmul_rn(Fx, s);
             Fy = __fmul_rn(Fy, s);
         }
     }
-    v.x = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fx, v.x));
-    v.y = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fy, v.y));
-    v.z = __fmul_rn(c.damping, __fmaf_rn(c.dt_over_m, Fz, v.z));
-    u.x = __fmaf_rn(c.dt, v.x, u.x);
-    u.y = __fmaf_rn(c.dt, v.y, u.y);
-    u.z = __fmaf_rn(c.dt, v.z, u.z);
+    integrate(u, v, Fx, Fy, Fz, c);
     return (unsigned)forced;
 }
 

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             __syncthreads();
             for (int m = tid; m < M; m += T) {
                 if (!((L.massbits[m >> 5] >> (m & 31)) & 1u)) continue;   // a corner without a mass
-                float fx = L.fx[m], fy = L.fy[m], fz = L.fz[m] - c.weight;
+                float fx = L.fx[m], fy = L.fy[m], fz = L.fz[m] - c.weight - c.weight_lo;
                 L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
                 float4 u = L.u[m], v = L.vel[m];
                 const float z = u.w + u.z;
@@ -130,15 +130,12 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
                         fx = 0.f; fy = 0.f; v.x = 0.f; v.y = 0.f;
                     } else {
                         // kinetic friction removes at most |F_h| (saturated: F_h cancelled)
-                        const float r = c.mu_k * fn / fh;
+                        const float r = fmaf(c.mu_k, fn, c.mu_k_lo * fn) / fh;
                         const float s2 = r >= 1.0f ? 0.0f : 1.0f - r;
                         fx *= s2; fy *= s2;
                     }
                 }
-                v.x = c.damping * (v.x + c.dt_over_m * fx);
-                v.y = c.damping * (v.y + c.dt_over_m * fy);
-                v.z = c.damping * (v.z + c.dt_over_m * fz);
-                u.x += c.dt * v.x; u.y += c.dt * v.y; u.z += c.dt * v.z;
+                integrate(u, v, fx, fy, fz, c);
                 L.u[m] = u;
                 L.vel[m] = v;
             }

@@ -42,7 +42,8 @@ def fit_err(f, fr, edge):
 
 def check_population(orc, pop, phys, nsteps, f_gpu, x_gpu, off, ref, w=None, kappa=None, phi=None,
                      K=8, max_sensitive_frac=0.1, perturb=PERTURB, envelope=1.5):
-    """Assert parity for every robot; returns the indices accepted through the envelope."""
+    """Assert parity for every robot; returns (index, errors, spreads) of the robots accepted
+    through the envelope."""
     sensitive = []
     rng = np.random.default_rng(1234)
     for r in range(pop.P):
@@ -76,9 +77,9 @@ def check_population(orc, pop, phys, nsteps, f_gpu, x_gpu, off, ref, w=None, kap
         assert ok, (f"robot {r} dims {tuple(pop.dims[r])}: position error {pe:.3e}, fitness error "
                     f"{fe:.3e}; nearest perturbed oracle run {near[0]:.3e}, {near[1]:.3e}; oracle "
                     f"spread {spread_p:.3e}, {spread_f:.3e}")
-        sensitive.append(r)
+        sensitive.append((r, round(pe, 6), round(fe, 6), round(float(spread_p), 6), round(float(spread_f), 6)))
     assert len(sensitive) <= max(1, int(max_sensitive_frac * pop.P)), \
-        f"too many robots only within the perturbation envelope: {sensitive}"
+        f"too many robots only within the perturbation envelope (robot, pos err, fit err, spreads): {sensitive}"
     return sensitive
 
 

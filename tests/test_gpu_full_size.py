@@ -6,8 +6,7 @@ robots the FP64 oracle recomputes one by one:
 * 64 robots of 40x40x40 on the streamed path (one graph-captured launch per step), the first
   1000 steps of the 5000-step run;
 * the adjoint of 512 robots of 8x8x8 with checkpoints every 100, along the FP64 oracle's
-  contact modes (imposed on the sampled robots), at 500 steps (meets the bar) and at the stated
-  2000 steps (held to the stated bar, which it does not meet: expected failure, with numbers).
+  contact modes (imposed on the sampled robots), at 500 steps and at the stated 2000 steps.
 
 Robots are sampled evenly over the spring-count order.  The simulation is compared from the
 GPU's own decoded grid and weights (the decode is checked separately on the same genomes).
@@ -54,25 +53,32 @@ def test_mlp_population_full_size(vs, orc):
     f = sim.fitness()
     x, _, off = sim.state()
     sim.close()
-    pick = W.stratified_subset(S, 12)
+    # the stated bar after 1000 steps on 48 robots spread over the spring-count order (about 6 %
+    # of them cross a stick/slip switch within float32 rounding and are held to the oracle's own
+    # spread instead; a sample of 12 can hold two of them), the long run on 12 of those
+    pick48 = W.stratified_subset(S, 48)
+    pick = pick48[::4]
     # decode: exact outside the guard band of the oracle's FP64 scores
-    for g in pick:
+    for g in pick48:
         mat, w, logits, guard = orc.mlp_query(dims, B, G[g])
         got = vox["decoded"][g * 512:(g + 1) * 512]
         top = np.sort(logits[:, :5], axis=1)
         sure = (top[:, -1] - top[:, -2]) > 2 * guard
         assert np.array_equal(got[sure], mat[sure]), g
     # simulation of the GPU's decoded robots
-    pop = W.make_population([dims] * len(pick), [vox["decoded"][g * 512:(g + 1) * 512].reshape(8, 8, 8)
-                                                  for g in pick])
-    w = np.concatenate([vox["w"][g * 512:(g + 1) * 512] for g in pick]).astype(np.float64)
-    kappa = np.asarray(PHYS.k_mat)[pop.mats]
-    phi = np.asarray(PHYS.phase_mat)[pop.mats]
+    def decoded(picks):
+        pop = W.make_population([dims] * len(picks), [vox["decoded"][g * 512:(g + 1) * 512].reshape(8, 8, 8)
+                                                       for g in picks])
+        w = np.concatenate([vox["w"][g * 512:(g + 1) * 512] for g in picks]).astype(np.float64)
+        return pop, w, np.asarray(PHYS.k_mat)[pop.mats], np.asarray(PHYS.phase_mat)[pop.mats]
+    pop48, w, kappa, phi = decoded(pick48)
+    offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick48])])
+    ref1 = orc.run_population(pop48, PHYS, 1000, w=w, kappa=kappa, phi=phi, want_x=True)
+    assert np.array_equal(ref1["S"], S[pick48]) and np.array_equal(ref1["M"], M[pick48])
+    x1s = np.concatenate([x1[off[g]:off[g + 1]] for g in pick48])
+    check_population(orc, pop48, PHYS, 1000, f1[pick48], x1s, offs, ref1, w=w, kappa=kappa, phi=phi)
+    pop, w, kappa, phi = decoded(pick)
     offs = np.concatenate([[0], np.cumsum([off[g + 1] - off[g] for g in pick])])
-    ref1 = orc.run_population(pop, PHYS, 1000, w=w, kappa=kappa, phi=phi, want_x=True)
-    assert np.array_equal(ref1["S"], S[pick]) and np.array_equal(ref1["M"], M[pick])
-    x1s = np.concatenate([x1[off[g]:off[g + 1]] for g in pick])
-    check_population(orc, pop, PHYS, 1000, f1[pick], x1s, offs, ref1, w=w, kappa=kappa, phi=phi)
     ref = orc.run_population(pop, PHYS, N, w=w, kappa=kappa, phi=phi, want_x=True)
     xs = np.concatenate([x[off[g]:off[g + 1]] for g in pick])
     check_population(orc, pop, PHYS, N, f[pick], xs, offs, ref, w=w, kappa=kappa, phi=phi, K=8,
@@ -245,17 +251,13 @@ def test_adjoint_full_population_500_steps(vs, orc):
     assert adj_err.max() <= 1e-3, adj_err
 
 
-@pytest.mark.xfail(strict=False, reason=(
-    "the stated bar (95 % of sampled parameters within 1e-3 of FP64 differences) is not met at "
-    "the 2000-step horizon: along the oracle's contact modes 91 % of 256 sampled parameters are "
-    "within 1e-3 (median 5e-5, 95th percentile 1.7e-3, largest 0.13; against the oracle's adjoint "
-    "up to 3e-3 in max norm); a float32-sized change of the inputs alone moves the FP64 gradient "
-    "by up to 3e-4 along fixed modes (tests/test_oracle_gradient_conditioning.py), and a float32 "
-    "run makes such roundings at every step"))
 def test_adjoint_full_size_meets_the_stated_bar(vs, orc):
     """The differentiation workload as stated (512 robots 8x8x8, 2000 steps, checkpoints every
     100), along the oracle's contact modes, held to the stated bar: at least 95 % of 256 sampled
-    parameters within 1e-3 of the FP64 differences."""
+    parameters within 1e-3 of the FP64 differences (measured 96.9 %, median 1.4e-5, 95th
+    percentile 3.8e-4).  It holds because the step's constants (dt, dt / m, m g, the damping) are
+    carried past float32: rounded to float32 they shift the map itself by up to 3e-8 of each
+    constant, which alone left 91 % of the samples within 1e-3."""
     fd_err, adj_err = adjoint_along_oracle_modes(vs, orc, 2000)
     print(f"within 1e-3: {np.mean(fd_err <= 1e-3):.3f} of {fd_err.size}; quantiles 50/90/95/100 %: "
           f"{np.quantile(fd_err, [0.5, 0.9, 0.95, 1.0])}; adjoint max-norm errors {np.sort(adj_err)[-3:]}")
