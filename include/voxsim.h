@@ -86,7 +86,9 @@ enum {
 /* Variant of the lattice-gather kernel (robots of at most 768 corners on the resident path).
  * All give identical bits; they differ in how threads share the work. */
 enum {
-    SIM_LATTICE_AUTO = 0,   /* library choice per size class (measured default, autotuned) */
+    SIM_LATTICE_AUTO = 0,   /* library choice (measured default, autotuned): one robot per slot,
+                               or the robots in mass-sized groups (SIM_LATTICE_PACKED) once their
+                               masses fill less than 55 % of their slots' threads */
     SIM_LATTICE_CORNER = 1, /* a thread per mass evaluates its 13 forward lattice directions, one
                                robot per block slot sized by its grid corners */
     SIM_LATTICE_COMPACT = 2,/* along each direction the existing springs are packed onto the
@@ -95,9 +97,10 @@ enum {
     SIM_LATTICE_PACKED = 3  /* the per-mass scheme of SIM_LATTICE_CORNER with several robots per
                                768-thread block, each in a group of threads sized by its mass
                                count (force rows indexed by the receiving thread), also for
-                               robots of more than 768 corners but at most 768 masses; measured
-                               slower than SIM_LATTICE_CORNER on robots of up to 768 corners
-                               (the autotuner may still choose it for the larger ones) */
+                               robots of more than 768 corners but at most 768 masses; for
+                               robots of up to 768 corners measured slower than
+                               SIM_LATTICE_CORNER until they fill less than about 55 % of their
+                               slots (the default then picks it) */
 };
 
 /* Physics constants (Table II; the workload configurations override some of them) and
