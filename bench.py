@@ -44,8 +44,9 @@ SMEM_PEAK_GBS = 152 * 128 * 2.07
 # 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
 # stays in shared memory, so traffic grows with the robots, not with the steps.
 LATTICE_DRAM_BYTES_PER_ROBOT = 18.91e6 / 152
-LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of k_step_lattice (152 robots, 1000 steps) scaled by robots; "
-                        "independent of the step count")
+LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of one k_step_lattice launch (152 robots, 1000 steps) scaled by "
+                        "robots; independent of the step count (the packed kernel reads 0.127 MB per "
+                        "robot, 2 % more)")
 
 
 def parse():
@@ -315,7 +316,9 @@ def run_ours(args):
         "springs_per_generation": [sp for sp, _ in stats],
         "gpu_launches": launches,
         "spring_plus_mass_updates_per_s": sm_value,
-        "roofline": {"bound": "smem", "kernel": "k_step_lattice",
+        "roofline": {"bound": "smem",
+                     "kernel": "k_step_lattice (k_step_lattice_packed once the robots fill less than 55 % "
+                               "of their slots: generations 8 and 9)",
                      "achieved": achieved_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                      "frac": achieved_gbs / SMEM_PEAK_GBS, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
                      "traffic_source": LATTICE_TRAFFIC_NOTE,
