@@ -1092,8 +1092,18 @@ static sim_status step_resident(voxsim_ctx* ctx, int n)
         while (per_sm < 8 && need * (per_sm + 1) <= ctx->smem_optin && threads * (per_sm + 1) <= 2048)
             ++per_sm;
         if (per_sm > 1) spr_fit = sc;
+        // a block with an SM to itself keeps its threads' first springs in tensor memory (the
+        // 512 columns split over the warps of each lane quarter, 4 columns per spring)
+        int tm_rec = 0, tm_cols = 0;
+        if (per_sm == 1) {
+            const int per_quarter = (threads / 32 + 3) / 4;
+            tm_cols = (512 / per_quarter) & ~3;
+            tm_rec = (int)std::min<int64_t>(tm_cols / 4, (sc + threads - 1) / threads);
+        }
+        a.tm_rec = tm_rec;
+        a.tm_cols = tm_cols;
         a.max_mass = g.max_corner;
-        a.max_spring_smem = (int)std::min<int64_t>(sc, spr_fit);
+        a.max_spring_smem = (int)std::min<int64_t>(std::max<int64_t>(0, sc - (int64_t)tm_rec * threads), spr_fit);
         const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
         int grid = (int)std::min<int64_t>(g.count, (int64_t)ctx->num_sms * per_sm);
         if (grid < 1) grid = 1;

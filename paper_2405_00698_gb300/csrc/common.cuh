@@ -135,7 +135,9 @@ struct ResidentArgs {
     int n_robots;            // entries of order
     int* queue;              // work counter (zeroed by the launcher) or NULL for static split
     int max_mass;            // smem layout: masses per robot slot
-    int max_spring_smem;     // springs cached in shared memory per robot
+    int max_spring_smem;     // springs cached in shared memory per robot (after those in tensor memory)
+    int tm_rec;              // springs per thread held in tensor memory (0: none, nothing allocated)
+    int tm_cols;             // tensor-memory columns per warp (of the block's 512)
     int accumulate;          // SIM_ACC_ATOMIC or SIM_ACC_GATHER
     // gather path
     const int* inc_off;      // [moff-based] per-mass incidence start (length M+1 per robot)

@@ -5,9 +5,13 @@
 //                       rest height z0 (corners without a mass are carried along unchanged)
 //   v       float4[C]   velocity
 //   F       float[3][C] accumulated by the spring phase, consumed and cleared by the mass phase
-//   springs float4[S]   as many as fit, the rest read from device memory (L2) every step:
-//                       (k, alpha L0, beta L0, a | b << 14 | direction << 28), ordered by
-//                       direction then a, so a warp's atomic updates hit distinct masses.
+//   springs float4[S]   (k, alpha L0, beta L0, a | b << 14 | direction << 28), ordered by
+//                       direction then a, so a warp's atomic updates hit distinct masses:
+//                       thread t's springs t, t + T, t + 2T, ... the first tm_rec of them in
+//                       tensor memory (when the block has an SM to itself: 16 springs per thread
+//                       at 1024 threads), then as many as fit in shared memory, the rest read
+//                       from device memory (L2) every step.  A spring read from tensor memory
+//                       takes no shared-memory bandwidth, which bounds this kernel.
 // Keeping the displacement instead of the position keeps float32 precise: a spring vector is
 // d = d0 + (u_b - u_a) with d0 the exact lattice offset, and the extension is formed without
 // cancellation as l - L0 = (2 d0.du + du.du) / (l + L0).
@@ -15,6 +19,7 @@
 // order, so an uneven population runs in one launch.
 #include "common.cuh"
 #include "physics.cuh"
+#include "tmem.cuh"
 
 namespace vx {
 namespace {
@@ -48,9 +53,19 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sh_robot;
     __shared__ float4 sh_d0[13];   // lattice offset of each direction, rest length in .w
+    __shared__ uint32_t sh_tmem;
     const SmemLayout L = carve(smem_raw, a.max_mass, a.max_spring_smem);
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5;
     const StepConst c = a.c;
+    const int tm_rec = a.tm_rec;
+    if (tm_rec > 0) {
+        if (warp == 0) tmem_alloc_warp(&sh_tmem);
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+    }
+    // this thread's cells: lane quarter warp % 4, a_tm_cols-column block per warp of the quarter
+    const uint32_t tmb = tm_rec > 0 ? sh_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(a.tm_cols * (warp >> 2)) : 0u;
     if (tid < 13) {
         const int ix = lattice_dir(tid, 0), iy = lattice_dir(tid, 1), iz = lattice_dir(tid, 2);
         const float dx = c.edge * ix, dy = c.edge * iy, dz = c.edge * iz;
@@ -76,11 +91,21 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             L.vel[m] = a.v[mo + m];
             L.fx[m] = 0.f; L.fy[m] = 0.f; L.fz[m] = 0.f;
         }
-        // as many springs as fit stay in shared memory (the first ones of the direction-major
-        // list); the rest are read from device memory (L2) every step
-        const int nsm = min(S, a.max_spring_smem);
+        // thread t's first springs t + j T (j < jt) in tensor memory, the next ones of the
+        // direction-major list in shared memory as far as they fit, the rest read from device
+        // memory (L2) every step
         const float4* __restrict__ spr_g = a.spr_pack + so;
-        for (int s = tid; s < nsm; s += T) L.spr[s] = spr_g[s];
+        const int jt = min(tm_rec, (S + T - 1) / T);      // uniform over the block
+        const int base = jt * T;
+        const int nsm = max(0, min(S - base, a.max_spring_smem));
+        for (int s = tid; s < nsm; s += T) L.spr[s] = spr_g[base + s];
+        for (int j = 0; j < jt; ++j) {
+            const int s = tid + j * T;
+            const float4 q = s < S ? spr_g[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            tmem_st4(tmb + 4 * j, __float_as_uint(q.x), __float_as_uint(q.y), __float_as_uint(q.z), __float_as_uint(q.w));
+        }
+        if (jt > 0) tmem_wait_st();
         // which corners carry a mass, one bit each
         for (int w = tid; w < (M + 31) / 32; w += T) {
             uint32_t bits = 0u;
@@ -91,8 +116,7 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
         __syncthreads();
         for (int n = 0; n < a.nsteps; ++n) {
             const float2 sc = a.sc[n];
-            for (int s = tid; s < S; s += T) {
-                const float4 q = s < nsm ? L.spr[s] : spr_g[s];
+            auto spring = [&](const float4 q) {
                 const unsigned bits = __float_as_uint(q.w);
                 const int ia = bits & 0x3fffu, ib = (bits >> 14) & 0x3fffu, dir = bits >> 28;
                 const float4 ua = L.u[ia], ub = L.u[ib], d0 = sh_d0[dir];
@@ -113,7 +137,17 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
                 const float gx = f * dx, gy = f * dy, gz = f * dz;
                 atomicAdd(&L.fx[ia], gx); atomicAdd(&L.fy[ia], gy); atomicAdd(&L.fz[ia], gz);
                 atomicAdd(&L.fx[ib], -gx); atomicAdd(&L.fy[ib], -gy); atomicAdd(&L.fz[ib], -gz);
+            };
+            for (int j = 0; j < jt; ++j) {
+                uint32_t r[4];
+                __syncwarp();                             // converged for the collective load
+                tmem_ld4(tmb + 4 * j, r[0], r[1], r[2], r[3]);
+                tmem_wait_ld4(r);
+                if (tid + j * T < S)
+                    spring(make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
+                                       __uint_as_float(r[3])));
             }
+            for (int s = base + tid; s < S; s += T) spring(s - base < nsm ? L.spr[s - base] : spr_g[s]);
             __syncthreads();
             for (int m = tid; m < M; m += T) {
                 if (!((L.massbits[m >> 5] >> (m & 31)) & 1u)) continue;   // a corner without a mass
@@ -146,6 +180,12 @@ __global__ void __launch_bounds__(1024, 1) k_step_resident_atomic(ResidentArgs a
             a.v[mo + m] = L.vel[m];
         }
         __syncthreads();
+    }
+    if (tm_rec > 0) {                              // every thread has waited for its own accesses
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (warp == 0) tmem_dealloc_warp(sh_tmem);
     }
 }
 

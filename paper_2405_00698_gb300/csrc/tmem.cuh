@@ -79,6 +79,11 @@ __device__ __forceinline__ void tmem_wait_ld6(uint32_t (&r)[6])
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 }  // namespace vx
