@@ -223,6 +223,20 @@ def test_atomic_path_matches_oracle(vs, orc):
     check_population(orc, pop, PHYS, 500, g["f"], g["x"], g["off"], ref)
 
 
+def test_atomic_kernel_spring_tiers(vs, orc):
+    """Full robots on the atomic kernel whose springs span its three stores: each thread's first
+    16 springs in tensor memory (1024 threads), the next ones in shared memory as far as they fit
+    beside the state, the rest read from device memory every step (12 x 12 x 13: 26,197 springs,
+    16,384 in tensor memory, about 7,900 in shared memory, about 1,900 from L2)."""
+    rng = np.random.default_rng(27)
+    dims = [(12, 12, 13), (12, 12, 12), (7, 9, 11)]
+    grids = [W.bernoulli_grid(rng, d, 1.0) for d in dims]
+    pop = W.make_population(dims, grids)
+    g, ref = run_both(vs, orc, pop, PHYS, 300, accumulate=vs.ACC_ATOMIC)
+    assert np.array_equal(g["S"], ref["S"]) and int(g["S"][0]) > 16384 + 8192
+    check_population(orc, pop, PHYS, 300, g["f"], g["x"], g["off"], ref)
+
+
 def test_gather_mode_keeps_large_robots_deterministic(vs):
     """Under bit-reproducible stepping a robot larger than a lattice block runs on a kernel with
     the same fixed summation order (a cluster of lattice blocks), and two runs agree bitwise."""
