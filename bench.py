@@ -63,6 +63,8 @@ def parse():
                     help="variant of the lattice-gather kernel")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven-population, adjoint and large-robot measurements")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="uneven population: keep the default per-class routing (reproducible under a profiler)")
     ap.add_argument("--case", choices=["streamed", "streamed_adjoint", "paper_preset", "adjoint", "uneven"], default=None,
                     help="run one extra measurement alone (for profiling; --robots sets its robots)")
     return ap.parse_args()
@@ -369,7 +371,10 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
     sim.set_population_from(pop)
     M, S = sim.counts()
     t0 = time.perf_counter()
-    kinds, threads = sim.autotune(20)           # per-size-class kernel choice, state restored
+    if getattr(args, "no_autotune", False):     # the default routing of every size class
+        kinds, threads = np.full(10, -1), np.zeros(10, np.int64)
+    else:
+        kinds, threads = sim.autotune(20)       # per-size-class kernel choice, state restored
     tune_s = time.perf_counter() - t0
     sim.step(50)                                # warm-up
     sim.timing()
@@ -401,7 +406,8 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
             "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
             "batched_roofline": {"bound": "smem", "achieved": batched_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
                                  "frac": batched_gbs / SMEM_PEAK_GBS},
-            "autotune": {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
+            "autotune": {"skipped": "default routing of every size class"} if getattr(args, "no_autotune", False) else
+                        {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
                          "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted, 4 lattice cluster, "
                          "5 lattice in mass-sized groups)": kinds.tolist(),
                          "atomic_threads": threads.tolist(), "seconds": tune_s},
