@@ -40,6 +40,9 @@ WORKLOAD = dict(workload="mlp-encoded population: 1024 genomes, 8x8x8 grid, 10 g
 P_ROBOTS, GRID, SIM_STEPS, GENERATIONS = 1024, (8, 8, 8), 10000, 10
 SMEM_PEAK_NOTE = "152 SMs x 128 B/clk x 2.07 GHz (unit counts and maximum SM clock)"
 SMEM_PEAK_GBS = 152 * 128 * 2.07
+SMEM_PEAK_MEASURED_NOTE = ("measured: sim_measure_smem_bandwidth, two 1024-thread blocks per SM streaming "
+                           "conflict-free 16-byte shared loads for 5 ms, best of 3 (peak_nominal: "
+                           + SMEM_PEAK_NOTE + ")")
 # DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
 # 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
 # stays in shared memory, so traffic grows with the robots, not with the steps.
@@ -155,6 +158,15 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # the GPU arm
 # ------------------------------------------------------------------------------------------
+
+def measured_smem_peak(sim):
+    """Shared-memory bandwidth of this GPU from the library's probe (best of three runs of about
+    5 ms each), else the nominal figure from unit counts and the maximum clock."""
+    try:
+        return max(sim.measure_smem_bandwidth() for _ in range(3)), SMEM_PEAK_MEASURED_NOTE
+    except Exception as exc:                    # noqa: BLE001 - reported in the line
+        return SMEM_PEAK_GBS, f"{SMEM_PEAK_NOTE} (probe failed: {exc})"
+
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -289,8 +301,11 @@ def run_ours(args):
     e2e_value, _, _ = shards.job_throughput(float(springs_per_step * args.steps), e2e_ms * 1e-3, "cuda")
 
     peaks, peak_src = measured_peaks()
+    smem_peak, smem_src = measured_smem_peak(sim)
+    peaks["smem_gbs"] = smem_peak
     # dominant kernel: the resident step kernel; algorithmic shared-memory bytes per step
-    # 48 B per spring update (two position reads, two atomic force updates) + 36 B per mass
+    # 48 B per spring update (the far end's position read, the force-plane write and its read by
+    # the far end) + 36 B per mass
     alg_bytes = 48.0 * updates + 36.0 * masses
     achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else 0.0
     rec = {
@@ -321,10 +336,10 @@ def run_ours(args):
         "roofline": {"bound": "smem",
                      "kernel": "k_step_lattice (k_step_lattice_packed once the robots fill less than 55 % "
                                "of their slots: generations 8 and 9)",
-                     "achieved": achieved_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
-                     "frac": achieved_gbs / SMEM_PEAK_GBS, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
+                     "achieved": achieved_gbs, "peak": smem_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / smem_peak, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
                      "traffic_source": LATTICE_TRAFFIC_NOTE,
-                     "peak_source": SMEM_PEAK_NOTE,
+                     "peak_source": smem_src, "peak_nominal": SMEM_PEAK_GBS,
                      "kernel_ms_per_step": kernel_ms / args.steps},
         "clocks": clk,
         "peaks_source": peak_src,
@@ -384,6 +399,10 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
     # algorithmic shared-memory bytes of the resident kernels (48 B per spring update, 36 B per
     # mass update) against the shared-memory peak
     batched_gbs = (48.0 * S.astype(np.int64).sum() + 36.0 * M.astype(np.int64).sum()) * N / (ms * 1e-3) / 1e9
+    if "smem_gbs" in peaks:
+        smem_peak, smem_src = peaks["smem_gbs"], SMEM_PEAK_MEASURED_NOTE
+    else:
+        smem_peak, smem_src = measured_smem_peak(sim)
     sim.close()
     sub = pop.subset(W.stratified_subset(S, plain_robots))
     res = {}
@@ -404,8 +423,8 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
     return {"workload": f"{P} robots, axes from {{4,6,8,10,12}}, occupancy U[0.3,0.9], connected, "
                         f"{N} steps", "unit": "spring-updates/s", "batched": batched,
             "batched_ms": ms, "batched_launches": launches, "springs": int(S.sum()),
-            "batched_roofline": {"bound": "smem", "achieved": batched_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
-                                 "frac": batched_gbs / SMEM_PEAK_GBS},
+            "batched_roofline": {"bound": "smem", "achieved": batched_gbs, "peak": smem_peak, "unit": "GB/s",
+                                 "frac": batched_gbs / smem_peak, "peak_source": smem_src},
             "autotune": {"skipped": "default routing of every size class"} if getattr(args, "no_autotune", False) else
                         {"classes_max_corners": [64, 128, 192, 256, 384, 768, 1536, 2560, 5120, "more"],
                          "kind (0 lattice per corner, 1 atomic, 2 streamed, 3 lattice compacted, 4 lattice cluster, "

@@ -421,6 +421,14 @@ sim_status sim_get_topology(voxsim_ctx* ctx, int32_t* mass_corner, int32_t* spri
  * Errors: SIM_EINVAL for a NULL context, SIM_ECUDA. */
 sim_status sim_get_timing(voxsim_ctx* ctx, double* step_ms, int64_t* launches);
 
+/* Measured shared-memory bandwidth of the context's device (GB/s, all SMs): two 1024-thread
+ * blocks per SM stream conflict-free 16-byte loads from their shared memory for about 5 ms
+ * (after a warm-up launch), timed with CUDA events on the context's stream.  The resident
+ * stepping kernels keep their state in shared memory, so this, not HBM, is the roofline they
+ * are measured against.  Synchronises the stream; allocates and frees a scratch array of 8 B
+ * per SM.  Errors: SIM_EINVAL for a NULL context or output, SIM_ECUDA. */
+sim_status sim_measure_smem_bandwidth(voxsim_ctx* ctx, double* gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1104,7 +1104,11 @@ static sim_status step_resident(voxsim_ctx* ctx, int n)
         a.tm_cols = tm_cols;
         a.max_mass = g.max_corner;
         a.max_spring_smem = (int)std::min<int64_t>(std::max<int64_t>(0, sc - (int64_t)tm_rec * threads), spr_fit);
-        const size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
+        size_t smem = resident_smem_bytes(a.max_mass, a.max_spring_smem, a.accumulate);
+        // a block that allocates the whole tensor memory must have its SM to itself: with the
+        // springs moved out of shared memory it could otherwise share one with a second block,
+        // which would wait for the first one's allocation until that block has drained the queue
+        if (tm_rec > 0) smem = std::max(smem, (size_t)ctx->smem_optin / 2 + 4096);
         int grid = (int)std::min<int64_t>(g.count, (int64_t)ctx->num_sms * per_sm);
         if (grid < 1) grid = 1;
         VX_CK(cudaMemsetAsync(a.queue, 0, sizeof(int), s));
@@ -1968,6 +1972,36 @@ sim_status sim_get_timing(voxsim_ctx* ctx, double* step_ms, int64_t* launches)
     if (launches) *launches = ctx->launches;
     ctx->ev_used = 0;
     ctx->launches = 0;
+    return SIM_OK;
+}
+
+sim_status sim_measure_smem_bandwidth(voxsim_ctx* ctx, double* gbs)
+{
+    if (sim_status st = check_ctx(ctx)) return st;
+    if (!gbs) return fail(SIM_EINVAL, "null output");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int grid = 2 * ctx->num_sms;            // two 1024-thread blocks per SM
+    const int iters = 4000;                       // about 5 ms at the nominal rate
+    float* sink = nullptr;
+    VX_CK(cudaMallocAsync((void**)&sink, sizeof(float) * grid, s));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = launch_probe_smem(grid, iters / 4, sink, s);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = launch_probe_smem(grid, iters, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ctx->launches += 2;
+    cudaFreeAsync(sink, s);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(e, "shared-memory probe");
+    if (!(ms > 0.f)) return fail(SIM_ECUDA, "shared-memory probe: no elapsed time");
+    *gbs = (double)probe_smem_bytes_per_iter(grid) * iters / (ms * 1e-3) / 1e9;
     return SIM_OK;
 }
 

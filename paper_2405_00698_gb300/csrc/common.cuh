@@ -299,6 +299,9 @@ cudaError_t launch_adjoint_voxels(const uint8_t* mat, const float* w, const floa
                                   const float* g_b, int64_t n, float* g_w, float* g_kappa,
                                   float* g_phi, cudaStream_t s);
 int lattice_max_threads();
+// Shared-memory bandwidth probe: grid blocks of 1024 threads, iters rounds of 8 16-byte loads.
+cudaError_t launch_probe_smem(int grid, int iters, float* sink, cudaStream_t s);
+size_t probe_smem_bytes_per_iter(int grid);
 constexpr int kLatticeSlotVec4 = 15;     // shared float4 per corner slot: u, v, 13 force planes
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s);

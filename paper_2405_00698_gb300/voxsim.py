@@ -26,7 +26,8 @@ GENOME_LEN = 20998
 EXPORTS = ("sim_create", "sim_destroy", "sim_last_error", "sim_set_population", "sim_step_n",
            "sim_fitness", "evo_generation", "evo_generation_static", "evo_gradient_step", "sim_set_checkpointing",
            "sim_set_trajectory_records", "sim_backward", "sim_get_contact_modes", "sim_autotune", "sim_diversity", "sim_get_counts", "sim_get_state", "sim_get_voxels", "sim_get_topology",
-           "sim_get_timing", "sim_check_status_words", "sim_impose_contact_modes", "evo_elite_weights")
+           "sim_get_timing", "sim_check_status_words", "sim_impose_contact_modes", "evo_elite_weights",
+           "sim_measure_smem_bandwidth")
 
 
 class VoxsimError(RuntimeError):
@@ -110,6 +111,7 @@ def lib():
             "sim_check_status_words": [vp],
             "sim_impose_contact_modes": [vp, i32, vp, i32],
             "evo_elite_weights": [vp, vp, i32, i32, vp],
+            "sim_measure_smem_bandwidth": [vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -282,6 +284,12 @@ class Simulator:
         sp = np.empty((int(S.sum()), 4), np.float32)
         _check(lib().sim_get_topology(self._h, mc.ctypes.data, ab.ctypes.data, sp.ctypes.data))
         return dict(M=M, S=S, mass_corner=mc, ab=ab, params=sp)
+
+    def measure_smem_bandwidth(self) -> float:
+        """Measured shared-memory bandwidth of the device, GB/s over all SMs."""
+        g = C.c_double()
+        _check(lib().sim_measure_smem_bandwidth(self._h, C.byref(g)))
+        return g.value
 
     def timing(self):
         ms = C.c_double(); n = C.c_int64()

@@ -237,6 +237,17 @@ def test_atomic_kernel_spring_tiers(vs, orc):
     check_population(orc, pop, PHYS, 300, g["f"], g["x"], g["off"], ref)
 
 
+def test_shared_memory_probe(vs):
+    """The shared-memory bandwidth probe (the resident kernels' roofline denominator) returns a
+    rate between 30 % and 110 % of 128 B per clock per SM at the 2.07 GHz maximum clock."""
+    import torch
+    sim = vs.Simulator(PHYS)
+    g = sim.measure_smem_bandwidth()
+    sim.close()
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2.07
+    assert 0.3 * nominal < g < 1.1 * nominal, (g, nominal)
+
+
 def test_gather_mode_keeps_large_robots_deterministic(vs):
     """Under bit-reproducible stepping a robot larger than a lattice block runs on a kernel with
     the same fixed summation order (a cluster of lattice blocks), and two runs agree bitwise."""
