@@ -75,27 +75,35 @@ __device__ __forceinline__ uint32_t draw32(uint64_t seed, uint64_t gen, uint32_t
 }
 
 // Rank by counting: the rank of robot i is the number of robots ordered before it
-// (larger fitness, or equal fitness and smaller index; NaN counts as -infinity).
+// (larger fitness, or equal fitness and smaller index; NaN counts as -infinity).  The fitness
+// values are compared as order-preserving 64-bit integer keys (the same order and the same ties
+// as the floating-point comparison; -0 and +0 share a key), which runs on the integer pipes
+// instead of the few FP64 units.
+__device__ __forceinline__ unsigned long long rank_key(double x)
+{
+    if (isnan(x)) x = -INFINITY;
+    if (x == 0.0) x = 0.0;                               // -0 and +0 compare equal
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 __global__ void k_rank(const double* __restrict__ f, int P, int* __restrict__ order)
 {
-    extern __shared__ double tile[];
+    extern __shared__ unsigned long long tile[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double fi = -INFINITY;
-    if (i < P) { fi = f[i]; if (isnan(fi)) fi = -INFINITY; }
+    const unsigned long long ki = i < P ? rank_key(f[i]) : 0ull;
     int rank = 0;
     for (int base = 0; base < P; base += blockDim.x) {
         __syncthreads();
         const int j = base + threadIdx.x;
-        double fj = -INFINITY;
-        if (j < P) { fj = f[j]; if (isnan(fj)) fj = -INFINITY; }
-        tile[threadIdx.x] = fj;
+        tile[threadIdx.x] = j < P ? rank_key(f[j]) : 0ull;
         __syncthreads();
         const int n = min((int)blockDim.x, P - base);
         if (i < P)
             for (int t = 0; t < n; ++t) {
-                const double g = tile[t];
+                const unsigned long long kg = tile[t];
                 const int jj = base + t;
-                rank += (g > fi) || (g == fi && jj < i);
+                rank += (kg > ki) || (kg == ki && jj < i);
             }
     }
     if (i < P) order[rank] = i;
@@ -217,7 +225,7 @@ cudaError_t launch_elite_weights(const int* order, const double* fitness, int P,
 cudaError_t launch_evo_rank(const double* fitness, int P, int* order, cudaStream_t s)
 {
     const int T = 256;
-    k_rank<<<(P + T - 1) / T, T, T * sizeof(double), s>>>(fitness, P, order);
+    k_rank<<<(P + T - 1) / T, T, T * sizeof(unsigned long long), s>>>(fitness, P, order);
     return cudaGetLastError();
 }
 
