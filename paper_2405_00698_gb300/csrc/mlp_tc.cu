@@ -9,18 +9,19 @@
 //
 // One CTA (4 warps) per genome at a time, persistent over genomes, two CTAs per SM (one CTA's
 // weight conversion and epilogues overlap the other's tensor work; measured 1.6x over one CTA
-// per SM with a double-buffered gamma tile).  Operands are bfloat16 in shared memory in the
-// 128-byte-swizzled K-major layout the tensor core reads directly:
-//   * gamma tiles of 128 queries arrive by TMA into one buffer, which after layer 1 holds the
-//     hidden activations (so a CTA needs 107 KB of shared memory);
-//   * W1, W2, W3 are converted from the float32 genome by the CTA's threads into the same
-//     layout (W3 padded to 16 rows);
+// per SM with a double-buffered gamma tile).  Shared-memory operands are bfloat16 in the
+// 128-byte-swizzled K-major layout the tensor core reads directly (107 KB per CTA):
+//   * gamma tiles of 128 queries arrive by TMA into one buffer; the next tile's copy is issued
+//     as soon as layer 1 has read the current one, so it overlaps the rest of the tile;
+//   * W1, W2, W3 are converted from the float32 genome by the CTA's threads into that layout
+//     (W3 padded to 16 rows);
 //   * the three layers are tcgen05.mma kind::f16 (M = 128; N = 64, 64, 16) accumulating in
 //     TMEM; one thread issues them; completion is signalled on an mbarrier by tcgen05.commit;
 //   * each epilogue reads its accumulator rows with tcgen05.ld (warp w owns TMEM lanes
 //     32w..32w+31 = queries of the tile), adds the bias, applies ReLU, rounds to bfloat16 and
-//     writes the next layer's A operand back to shared memory; the last epilogue computes the
-//     heads and writes material, weight, stiffness and phase per voxel.
+//     stores the hidden activations in TMEM with tcgen05.st (row i in lane i, two units per
+//     column), where layers 2 and 3 read their A operand; the last epilogue computes the heads
+//     and writes material, weight, stiffness and phase per voxel.
 // Every mbarrier wait is bounded: on timeout the kernel raises a status bit, abandons the
 // remaining work and still releases its TMEM.
 #include <cuda.h>
@@ -154,6 +155,18 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a_desc, uint64_t 
         ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
+// The same with the A operand (M x 16 bfloat16, row i in lane i, two elements per column) read
+// from tensor memory at column address a_tmem.
+__device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -181,6 +194,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive 32-bit columns of this thread's lane from 32 registers, then wait for them.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+          "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+          "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
@@ -190,7 +218,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 // Convert a float32 [rows][K] weight block (8-byte aligned) into the swizzled bf16 layout.
 // Each thread takes kUnroll chunks of 8 values per round and issues all their loads before
 // converting any, so several global loads per thread are in flight.
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 8;
 __device__ __forceinline__ void load_weights(const float* __restrict__ src, int rows, int K,
                                              int valid_rows, unsigned char* dst)
 {
@@ -220,21 +248,22 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ src, int 
     }
 }
 
-// Bias + ReLU of a 64-wide accumulator row block, rounded to bfloat16 into the A operand
-// of the next layer (row = query of the tile).
-__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bias, unsigned char* h, int row)
+// Bias + ReLU of a 64-wide accumulator row block, rounded to bfloat16 and stored as the next
+// layer's A operand in tensor memory (this thread's lane = query row of the tile; column j holds
+// hidden units 2j and 2j + 1, the lower index in the low half).
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bias, uint32_t th)
 {
+    uint32_t p[32];
 #pragma unroll
     for (int c0 = 0; c0 < kHidden; c0 += 16) {
         float v[16];
         tmem_ld16(taddr + c0, v);
-        uint32_t p[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            p[i] = pack_bf16(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f), fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
-        *reinterpret_cast<uint4*>(h + sw128_offset(row, c0, kTileM)) = make_uint4(p[0], p[1], p[2], p[3]);
-        *reinterpret_cast<uint4*>(h + sw128_offset(row, c0 + 8, kTileM)) = make_uint4(p[4], p[5], p[6], p[7]);
+            p[c0 / 2 + i] = pack_bf16(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f),
+                                      fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
     }
+    tmem_st32(th, p);
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
@@ -261,10 +290,12 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s.tmem_base;
-    const uint32_t t_d1 = tmem, t_d2 = tmem + 64, t_d3 = tmem + 128;
+    // accumulators of the three layers, then the hidden activations (bf16 pairs), which are the
+    // A operand of layers 2 and 3
+    const uint32_t t_d1 = tmem, t_d2 = tmem + 64, t_d3 = tmem + 128, t_h = tmem + 160;
     const uint32_t lane_sel = (uint32_t)(warp * 32) << 16;    // this warp's TMEM lane quarter
     const int ntiles = (Q + kTileM - 1) / kTileM;
-    uint32_t tma_phase[2] = {0, 0}, mma_phase = 0;
+    uint32_t tma_phase = 0, mma_phase = 0;
     constexpr uint32_t id_h = idesc_bf16(kTileM, kHidden);
     constexpr uint32_t id_o = idesc_bf16(kTileM, kW3Rows);
     // issuing thread only: the TMA batch and the MMA commit whose completion it has not yet
@@ -272,6 +303,16 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
     bool tma_out = false, mma_out = false;
     uint32_t tma_out_phase = 0, mma_out_phase = 0;
     bool stop = false;
+    // the gamma tile of the next layer-1 MMA, copied as soon as the buffer is free (right after
+    // the previous tile's layer 1), so the copy overlaps that tile's epilogues and layers 2, 3
+    auto issue_gamma = [&](int tile) {
+        mbar_expect_tx(&s.tma_bar[0], kABytes);
+        for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
+            tma_load_2d(s.a[0] + kb * kTileM * 128, &pe_map, &s.tma_bar[0], kb * kKBlock, tile * kTileM);
+        tma_out = true;
+        tma_out_phase = tma_phase;
+    };
+    if (tid == 0 && (int)blockIdx.x < P) issue_gamma(0);
 
     for (int g = blockIdx.x; g < P && !stop; g += gridDim.x) {
         const float* G = genomes + (size_t)g * kGenome;
@@ -286,20 +327,13 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
         proxy_fence();
         __syncthreads();
         for (int t = 0; t < ntiles; ++t) {
-            const int cur = 0;
-            if (tid == 0 && !s.abort) {                     // this tile's gamma rows
-                mbar_expect_tx(&s.tma_bar[0], kABytes);
-                for (int kb = 0; kb < kPeDim / kKBlock; ++kb)
-                    tma_load_2d(s.a[0] + kb * kTileM * 128, &pe_map, &s.tma_bar[0], kb * kKBlock, t * kTileM);
-                tma_out = true;
-                tma_out_phase = tma_phase[0];
-            }
             // layer 1: D1 = gamma_tile . W1^T  (K = 256: 4 swizzle blocks x 4 steps of 16)
-            if (tid == 0 && tma_out) {
-                if (mbar_wait(&s.tma_bar[cur], tma_phase[cur], s, status)) {
+            if (tid == 0 && tma_out && !s.abort) {
+                if (mbar_wait(&s.tma_bar[0], tma_phase, s, status)) {
                     tma_out = false;
+                    tma_phase ^= 1;
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(s.a[cur]), b0 = smem_u32(s.w1);
+                    const uint32_t a0 = smem_u32(s.a[0]), b0 = smem_u32(s.w1);
 #pragma unroll
                     for (int k = 0; k < kPeDim / 16; ++k) {
                         const uint32_t ao = (k / 4) * (kTileM * 128) + (k % 4) * 32;
@@ -311,23 +345,24 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
                     mma_out_phase = mma_phase;
                 }
             }
-            tma_phase[cur] ^= 1;
             const int row = warp * 32 + lane;
-            // epilogue 1 -> H
             if (mbar_wait(&s.mma_bar, mma_phase, s, status) && tid == 0) mma_out = false;
             mma_phase ^= 1;
+            // the gamma buffer is free again: the next tile's copy (or the next genome's first)
+            if (tid == 0 && !s.abort && (t + 1 < ntiles || g + (int)gridDim.x < P))
+                issue_gamma(t + 1 < ntiles ? t + 1 : 0);
+            // epilogue 1 -> H (tensor memory)
             tc_fence_after();
-            if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, s.a[0], row);
-            proxy_fence();
+            if (!s.abort) epilogue_hidden(t_d1 + lane_sel, s.b1, t_h + lane_sel);
             tc_fence_before();
             __syncthreads();
-            // layer 2: D2 = H . W2^T
+            // layer 2: D2 = H . W2^T, H read from tensor memory (8 columns per step of K = 16)
             if (tid == 0 && !s.abort) {
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(s.a[0]), b0 = smem_u32(s.w2);
+                const uint32_t b0 = smem_u32(s.w2);
 #pragma unroll
                 for (int k = 0; k < kHidden / 16; ++k)
-                    umma(t_d2, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_h, k > 0);
+                    umma_ts(t_d2, t_h + k * 8, sw128_desc(b0 + k * 32), id_h, k > 0);
                 umma_commit(&s.mma_bar);
                 mma_out = true;
                 mma_out_phase = mma_phase;
@@ -335,17 +370,16 @@ k_mlp_tc(const __grid_constant__ CUtensorMap pe_map, int P, int Q, const float* 
             if (mbar_wait(&s.mma_bar, mma_phase, s, status) && tid == 0) mma_out = false;
             mma_phase ^= 1;
             tc_fence_after();
-            if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, s.a[0], row);
-            proxy_fence();
+            if (!s.abort) epilogue_hidden(t_d2 + lane_sel, s.b2, t_h + lane_sel);
             tc_fence_before();
             __syncthreads();
             // layer 3: D3 = H . W3^T (N = 16, rows 6..15 of W3 are zero)
             if (tid == 0 && !s.abort) {
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(s.a[0]), b0 = smem_u32(s.w3);
+                const uint32_t b0 = smem_u32(s.w3);
 #pragma unroll
                 for (int k = 0; k < kHidden / 16; ++k)
-                    umma(t_d3, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), id_o, k > 0);
+                    umma_ts(t_d3, t_h + k * 8, sw128_desc(b0 + k * 32), id_o, k > 0);
                 umma_commit(&s.mma_bar);
                 mma_out = true;
                 mma_out_phase = mma_phase;
