@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         float ldx, ldy, ldz, dk, da, db;
                         spring_adjoint(e, k, lFx - gb.x, lFy - gb.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz, dk, da, db);
                         lux -= ldx; luy -= ldy; luz -= ldz;
-                        sl[d * Ss + cidx] = make_float4(ldx, ldy, ldz, 0.f);
+                        sl[d * Ss + cidx] = make_float4(ldx, ldy, ldz, e.ext);
                         __syncwarp();
                         tmem_st4(tm + cells_s<d>(), cur[2], __float_as_uint(__uint_as_float(cur[3]) + dk),
                                  __float_as_uint(__uint_as_float(cur[4]) + da),

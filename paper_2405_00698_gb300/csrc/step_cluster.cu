@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_step_cluster(ClusterArgs
             if constexpr (DAMPED)
                 spring_dashpot(e, __fsub_rn(vb.x, v.x), __fsub_rn(vb.y, v.y), __fsub_rn(vb.z, v.z), pk[d], a.c);
             Fxy = __fadd2_rn(Fxy, make_float2(e.gx, e.gy)); Fz = __fadd_rn(Fz, e.gz);
-            fb[d * S + t] = make_float4(e.gx, e.gy, e.gz, 0.f);
+            fb[d * S + t] = make_float4(e.gx, e.gy, e.gz, e.ext);
         });
         cl.sync();
         // phase B: backward springs (c - offset(d), c), then the mass update
