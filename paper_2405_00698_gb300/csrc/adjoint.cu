@@ -202,8 +202,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                         const int nb = has ? cidx + lattice_offset<d>(Xs, XYs) : cidx;
                         const float4 ub = su[nb], gb = sg[nb];
                         const float k = __uint_as_float(cur[0]);
-                        const SpringEval e = spring_eval_dir<d>(
-                            __fsub_rn(ub.x, un.x), __fsub_rn(ub.y, un.y), __fsub_rn(ub.z, un.z), c.edge,
+                        const SpringEval e = spring_eval_ends<d>(ub, un, c.edge,
                             lattice_rest<d>(c), lattice_rest_sq<d>(c), k, __uint_as_float(cur[1]),
                             __uint_as_float(cur[2]), sc.x, sc.y);
                         float ldx, ldy, ldz, dk, da, db;

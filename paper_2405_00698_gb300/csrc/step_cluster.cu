@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_step_cluster(ClusterArgs
                     if (DAMPED) vb = sv[nb - c0];
                 }
             }
-            SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y), __fsub_rn(ub.z, u.z), a.c.edge,
+            SpringEval e = spring_eval_ends<d>(ub, u, a.c.edge,
                                               lattice_rest<d>(a.c), lattice_rest_sq<d>(a.c), pk[d], pa[d], pb[d],
                                               sc.x, sc.y);
             if constexpr (DAMPED)
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_step_cluster(ClusterArgs
             if (!((fl >> (16 + d)) & 1u)) return;
             const int na = cidx - lattice_offset<d>(X, XY);
             const float4 g = (lattice_dir(d, 2) == 1 && bottom) ? fb_prev[d * S + (na - cprev)] : fb[d * S + (na - c0)];
-            Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
+            Fxy = __ffma2_rn(make_float2(g.x, g.y), kMinusOne2, Fxy); Fz = __fsub_rn(Fz, g.z);
         });
         if (mass) {
             mass_update(u, v, Fxy.x, Fxy.y, Fz, a.c);

@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     }
                     float4 ub = u;
                     if (has) ub = su[cidx + lattice_offset<d>(X, XY)];
-                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
-                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
+                    SpringEval e = spring_eval_ends<d>(ub, u, c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
                                                       pk[d], pa[d], pb[d], sc.x, sc.y);
                     if constexpr (DAMPED) {
                         const float4 vb = sv[has ? cidx + lattice_offset<d>(X, XY) : cidx];
@@ -160,7 +159,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
                     constexpr int d = decltype(t)::value;
                     if (!((fl >> (16 + d)) & 1u)) return;
                     const float4 g = fb[d * S + cidx - lattice_offset<d>(X, XY)];   // force on a
-                    Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
+                    Fxy = __ffma2_rn(make_float2(g.x, g.y), kMinusOne2, Fxy); Fz = __fsub_rn(Fz, g.z);
                 });
                 if (mass) {
                     int forced = -1;
@@ -303,8 +302,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_compact(
                     const int cb = ca + lattice_offset<d>(X, XY);
                     const float4 ua = su[ca];
                     const float4 ub = su[cb];
-                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, ua.x), __fsub_rn(ub.y, ua.y),
-                                                      __fsub_rn(ub.z, ua.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
+                    SpringEval e = spring_eval_ends<d>(ub, ua, c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
                                                       pk[d], pa[d], pb[d], sc.x, sc.y);
                     if constexpr (DAMPED) {
                         const float4 va = sv[ca];
@@ -446,8 +444,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(L
                     }
                     float4 ub = u;
                     if (has) ub = su[cidx + lattice_offset<d>(X, XY)];
-                    SpringEval e = spring_eval_dir<d>(__fsub_rn(ub.x, u.x), __fsub_rn(ub.y, u.y),
-                                                      __fsub_rn(ub.z, u.z), c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
+                    SpringEval e = spring_eval_ends<d>(ub, u, c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
                                                       pk[d], pa[d], pb[d], sc.x, sc.y);
                     if constexpr (DAMPED) {
                         const float4 vb = sv[cidx + lattice_offset<d>(X, XY)];
@@ -464,7 +461,7 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(L
                         constexpr int d = decltype(t)::value;
                         if (!((fl >> (16 + d)) & 1u)) return;
                         const float4 g = fb[d * T + lt];   // force on the spring's first end
-                        Fxy = __fadd2_rn(Fxy, make_float2(-g.x, -g.y)); Fz = __fsub_rn(Fz, g.z);
+                        Fxy = __ffma2_rn(make_float2(g.x, g.y), kMinusOne2, Fxy); Fz = __fsub_rn(Fz, g.z);
                     });
                     if ((fl >> 31) & 1u) {
                         mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
