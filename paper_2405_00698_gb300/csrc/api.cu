@@ -190,6 +190,7 @@ struct voxsim_ctx {
     int n_cluster = 0;
     DevBuf<int> d_cluster;
     int n_stream = 0, max_stream_corner = 0;
+    bool corner_cube8 = false;   // every per-corner lattice item is one 8 x 8 x 8 robot (768 threads)
     std::vector<int> stream_robots;
     DevBuf<int> d_stream;
     // CUDA graph of the streamed N-step loop, cached by step count (captured on a private
@@ -794,6 +795,15 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
             if (split && !v.empty()) ctx->has_split = true;
         }
     }
+    // the per-corner kernel's compile-time 8 x 8 x 8 instantiation applies when every one of its
+    // items is a single robot of that grid in a 768-thread slot
+    ctx->corner_cube8 = ctx->n_items_corner > 0;
+    for (int i = 0; i < ctx->n_items_corner && ctx->corner_cube8; ++i) {
+        const int4 it = items[i];
+        const int r = robots[it.x];
+        ctx->corner_cube8 = it.y == 1 && it.z == 768 && it.w == 0 && ctx->dims[3 * r] == 8 &&
+                            ctx->dims[3 * r + 1] == 8 && ctx->dims[3 * r + 2] == 8;
+    }
     if (sim_status st = build_packed_items(ctx, lattice, mass_groups, damped)) return st;
     std::sort(atomic.begin(), atomic.end());
     std::vector<int> big;
@@ -994,6 +1004,7 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
     a.n_items = ctx->n_items;
     a.queue = ctx->d_queue.p;
     a.has_split = ctx->has_split ? 1 : 0;
+    a.cube8 = ctx->corner_cube8 ? 1 : 0;
     ctx->imposed_args(a, ctx->step);
     if (record) {                               // (buffers sized by sim_step_n)
         a.ckpt_u = ctx->d_ckpt_u.p;
@@ -1428,6 +1439,7 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     f.items = ctx->d_items.p;
     f.item_robots = ctx->d_item_robots.p;
     f.n_items = ctx->n_items;
+    f.cube8 = ctx->corner_cube8 && ctx->n_items == ctx->n_items_corner ? 1 : 0;
     f.queue = ctx->d_queue.p;
     f.rec_u = ctx->d_srec_u.p;
     f.rec_f = ctx->d_srec_f.p;
@@ -1606,6 +1618,7 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
             f.items = ctx->d_items.p;
             f.item_robots = ctx->d_item_robots.p;
             f.n_items = ctx->n_items;
+            f.cube8 = ctx->corner_cube8 && ctx->n_items == ctx->n_items_corner ? 1 : 0;
             f.queue = ctx->d_queue.p;
             f.rec_u = ctx->d_srec_u.p;
             f.rec_f = ctx->d_srec_f.p;

@@ -168,6 +168,7 @@ struct LatticeArgs {
                              // shared-memory offset in float4)
     int n_items;
     int has_split;           // the items include split ones (run by the split instantiation)
+    int cube8;               // every per-corner item is one 8 x 8 x 8 robot in a 768-thread slot
     int* queue;              // work counter, zeroed before the launch
     // checkpoints for the adjoint (NULL when off): state at steps 0, K, 2K, ... of the call
     float4* ckpt_u;

@@ -41,7 +41,10 @@ __device__ __forceinline__ void group_sync(int id, int nthreads)
 // gather, so the sums are formed in the same order from the same values: the same bits as the
 // unsplit step, with the longest chain of spring evaluations per step cut from 13 to 7.
 // IMPOSE: some robots take their contact modes from a table (sim_impose_contact_modes).
-template <bool DAMPED, bool RECORD, bool SPLIT, bool IMPOSE>
+// CUBE8: every item of the launch is one 8 x 8 x 8 robot in a 768-thread slot (the MLP
+// population's fixed grid); the strides and the plane stride become compile-time constants, so
+// the shared-memory addresses of the 13 directions are immediate offsets.
+template <bool DAMPED, bool RECORD, bool SPLIT, bool IMPOSE, bool CUBE8 = false>
 __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -65,17 +68,17 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice(LatticeA
         // split groups only in the SPLIT instantiation (launched when the plan has some); the
         // other instantiations run a split item as one unsplit group of 2 S threads
         const bool split = SPLIT && sh_item[4] == 2;
-        const int group = tid / gthreads, lt = tid % gthreads;
+        const int group = CUBE8 ? 0 : tid / gthreads, lt = CUBE8 ? tid : tid % gthreads;
         __syncthreads();   // everyone has read the item before thread 0 may overwrite it
         if (group < count) {
             const int r = a.item_robots[first + group];
             const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
-            const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
+            const int X = CUBE8 ? 9 : nx + 1, XY = CUBE8 ? 81 : (nx + 1) * (ny + 1), C = CUBE8 ? 729 : XY * (nz + 1);
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
             // shared-memory slot of this group (S corners): u, then 13 force planes; a split
             // group has 2 S threads, owners [0, S) and helpers [S, 2 S) (whole warps each)
-            const int S = split ? gthreads / 2 : gthreads;
+            const int S = CUBE8 ? kMaxLatticeThreads : (split ? gthreads / 2 : gthreads);
             const bool hlp = split && lt >= S;
             const int li = hlp ? lt - S : lt;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
@@ -496,8 +499,10 @@ cudaError_t launch_step_lattice_packed(const LatticeArgs& a, int grid, size_t sm
 cudaError_t launch_step_lattice(const LatticeArgs& a, int grid, int threads, size_t smem,
                                 cudaStream_t s)
 {
+    const bool cube8 = a.cube8 && !a.c.damped;
     auto kernel = a.imp_modes ? (a.rec_u ? k_step_lattice<false, true, false, true> : k_step_lattice<false, false, false, true>)
-                : a.rec_u ? k_step_lattice<false, true, false, false>
+                : a.rec_u ? (cube8 ? k_step_lattice<false, true, false, false, true> : k_step_lattice<false, true, false, false>)
+                : (cube8 && !a.spack) ? k_step_lattice<false, false, false, false, true>
                 : a.spack ? (a.c.damped ? k_step_lattice_compact<true> : k_step_lattice_compact<false>)
                 : a.c.damped ? (a.has_split ? k_step_lattice<true, false, true, false> : k_step_lattice<true, false, false, false>)
                              : k_step_lattice<false, false, false, false>;

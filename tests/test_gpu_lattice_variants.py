@@ -164,3 +164,18 @@ def test_autotuner_may_choose_mass_groups(vs):
     sim.close()
     assert set(int(k) for k in kinds[6:9]) <= {1, 2, 4, 5}
     assert np.all(np.isfinite(f))
+
+
+def test_eight_cube_instantiation_equals_the_generic_kernel(vs):
+    """A population of 8 x 8 x 8 robots only runs the per-corner kernel's compile-time 8-cube
+    instantiation; adding one robot of another grid sends the same robots through the generic
+    one.  Their states and fitness agree bit for bit."""
+    pop = W.population_bernoulli(24, (8, 8, 8), 0.8, seed=73)
+    other = W.population_bernoulli(1, (5, 7, 6), 0.8, seed=74)
+    both = W.make_population([tuple(d) for d in pop.dims] + [tuple(other.dims[0])],
+                             [pop.grid(r) for r in range(pop.P)] + [other.grid(0)])
+    a = run(vs, pop, W.CONFIG, 600, vs.LATTICE_CORNER)
+    b = run(vs, both, W.CONFIG, 600, vs.LATTICE_CORNER)
+    n = int(a[3][-1])
+    assert np.array_equal(a[0], b[0][:n]) and np.array_equal(a[1], b[1][:n])
+    assert np.array_equal(a[2], b[2][:pop.P])
