@@ -70,6 +70,9 @@ __device__ __forceinline__ void cells_load(uint32_t tm, uint32_t (&v)[6])
 // transpose and one 4-column store of the updated sums after it.  Held in registers next to the
 // sweep's other state they spilled to local memory, which misses L1 beside 221 KB of shared
 // memory: 1.5x the time of this version.
+// CUBE8: every item is one 8 x 8 x 8 robot in a 768-thread slot; strides and plane stride are
+// compile-time constants (immediate shared-memory offsets), as in the forward kernel.
+template <bool CUBE8>
 __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
 {
     extern __shared__ __align__(16) float4 sm4[];
@@ -95,15 +98,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
         __syncthreads();
         if (!sh_item[3]) break;
         const int first = sh_item[0], count = sh_item[1], gthreads = sh_item[2];
-        const int group = tid / gthreads, lt = tid % gthreads;
+        const int group = CUBE8 ? 0 : tid / gthreads, lt = CUBE8 ? tid : tid % gthreads;
         __syncthreads();
         if (group < count) {                              // whole warps (slots are multiples of 32)
             const int r = a.item_robots[first + group];
             const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
-            const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
+            const int X = CUBE8 ? 9 : nx + 1, XY = CUBE8 ? 81 : (nx + 1) * (ny + 1), C = CUBE8 ? 729 : XY * (nz + 1);
             const int64_t mo = a.pv.moff[r];
             const int bar = 1 + group;
-            const int S = gthreads;
+            const int S = CUBE8 ? kBlock : gthreads;
             float4* su = sm4 + (size_t)group * kLatticeSlotVec4 * S;
             float4* sg = su + S;
             float4* sl = sg + S;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
             for (int n = a.n1 - 1; n >= a.n0; --n) {
                 // the lattice offsets are recomputed every step rather than hoisted out of the
                 // loop and spilled: an opaque copy of the strides hides their invariance
-                asm volatile("" : "+r"(Xs), "+r"(XYs), "+r"(Ss));
+                if constexpr (!CUBE8) asm volatile("" : "+r"(Xs), "+r"(XYs), "+r"(Ss));
                 // direction 0's cells, read while the mass part runs
                 uint32_t cur[6];
                 if (warp_in) {
@@ -285,9 +288,10 @@ __global__ void k_adjoint_voxels(const uint8_t* __restrict__ mat, const float* _
 
 cudaError_t launch_adjoint_lattice(const AdjointArgs& a, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint_lattice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kernel = a.cube8 ? k_adjoint_lattice<true> : k_adjoint_lattice<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_adjoint_lattice<<<grid, threads, smem, s>>>(a);
+    kernel<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

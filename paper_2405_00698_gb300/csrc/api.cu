@@ -1463,6 +1463,7 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     a.items = ctx->d_items.p;
     a.item_robots = ctx->d_item_robots.p;
     a.n_items = ctx->n_items;
+    a.cube8 = f.cube8;
     a.queue = ctx->d_queue.p;
     a.g_k = ctx->d_gk.p;
     a.g_a = ctx->d_ga.p;

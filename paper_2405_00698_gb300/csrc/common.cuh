@@ -288,6 +288,7 @@ struct AdjointArgs {
     const int4* items;
     const int* item_robots;
     int n_items;
+    int cube8;               // every item is one 8 x 8 x 8 robot in a 768-thread slot
     int* queue;
     float* g_k;              // per voxel: dL/dk_v, dL/d(alpha_v), dL/d(beta_v) accumulators
     float* g_a;
