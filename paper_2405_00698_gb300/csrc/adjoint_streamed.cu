@@ -27,13 +27,15 @@ struct CornerRef {
     uint32_t fl;
 };
 
+// NC > 0: every streamed robot is NC x NC x NC (compile-time strides, as in the forward step).
+template <int NC = 0>
 __device__ __forceinline__ bool corner_ref(const StreamAdjArgs& a, CornerRef& q)
 {
     q.r = a.robots[blockIdx.y];
     const int nx = a.pv.dims[3 * q.r], ny = a.pv.dims[3 * q.r + 1], nz = a.pv.dims[3 * q.r + 2];
-    q.X = nx + 1;
-    q.XY = (nx + 1) * (ny + 1);
-    q.C = q.XY * (nz + 1);
+    q.X = NC ? NC + 1 : nx + 1;
+    q.XY = NC ? (NC + 1) * (NC + 1) : (nx + 1) * (ny + 1);
+    q.C = NC ? (NC + 1) * (NC + 1) * (NC + 1) : q.XY * (nz + 1);
     q.cidx = blockIdx.x * blockDim.x + threadIdx.x;
     if (q.cidx >= q.C) return false;
     q.mo = a.pv.moff[q.r];
@@ -54,10 +56,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_sadj_init(StreamAdjArgs a)
     for (int k = 0; k < 39; ++k) acc[k * q.C + q.cidx] = 0.f;
 }
 
+template <int NC>
 __global__ void __launch_bounds__(kAdjThreads, 4) k_sadj_step(StreamAdjArgs a)
 {
     CornerRef q;
-    if (!corner_ref(a, q)) return;
+    if (!corner_ref<NC>(a, q)) return;
     const int64_t o = q.mo + q.cidx;
     const int X = q.X, XY = q.XY, C = q.C, cidx = q.cidx;
     const uint32_t fl = q.fl;
@@ -185,7 +188,8 @@ cudaError_t launch_stream_adj_init(const StreamAdjArgs& a, int max_corners, cuda
 cudaError_t launch_stream_adj_step(const StreamAdjArgs& a, int max_corners, cudaStream_t s)
 {
     if (a.n_robots == 0) return cudaSuccess;
-    k_sadj_step<<<grid_of(a, max_corners), kAdjThreads, 0, s>>>(a);
+    if (a.cube40) k_sadj_step<40><<<grid_of(a, max_corners), kAdjThreads, 0, s>>>(a);
+    else k_sadj_step<0><<<grid_of(a, max_corners), kAdjThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

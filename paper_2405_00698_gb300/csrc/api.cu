@@ -190,6 +190,7 @@ struct voxsim_ctx {
     int n_cluster = 0;
     DevBuf<int> d_cluster;
     int n_stream = 0, max_stream_corner = 0;
+    bool stream_cube40 = false;  // every streamed robot is 40 x 40 x 40
     bool corner_cube8 = false;   // every per-corner lattice item is one 8 x 8 x 8 robot (768 threads)
     std::vector<int> stream_robots;
     DevBuf<int> d_stream;
@@ -835,6 +836,10 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
     ctx->n_big = (int)big.size();
     ctx->n_stream = (int)streamed.size();
     ctx->stream_robots = streamed;
+    ctx->stream_cube40 = !streamed.empty();
+    for (int r : streamed)
+        ctx->stream_cube40 = ctx->stream_cube40 && ctx->dims[3 * r] == 40 && ctx->dims[3 * r + 1] == 40 &&
+                             ctx->dims[3 * r + 2] == 40;
     cudaStream_t s = ctx->stream;
     VX_CK(ctx->d_queue.ensure(2 + ctx->atomic_groups.size()));
     if (!streamed.empty()) {
@@ -1158,6 +1163,7 @@ static sim_status enqueue_streamed(voxsim_ctx* ctx, int n, cudaStream_t s, bool 
     a.c = ctx->stepconst();
     a.robots = ctx->d_stream.p;
     a.n_robots = ctx->n_stream;
+    a.cube40 = ctx->stream_cube40 ? 1 : 0;
     const int K = record ? ctx->ckpt_every : 0;
     const bool keep = record && ctx->keep_records;
     for (int i = 0; i < n; ++i) {
@@ -1528,6 +1534,7 @@ static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
     b.dL_df = dL_df;
     b.c = ctx->stepconst();
     b.robots = ctx->d_stream.p;
+    b.cube40 = ctx->stream_cube40 ? 1 : 0;
     b.n_robots = ctx->n_stream;
     b.g_k = ctx->d_gk.p;
     b.g_a = ctx->d_ga.p;
@@ -1545,6 +1552,7 @@ static sim_status backward_streamed(voxsim_ctx* ctx, const double* dL_df)
     f.c = ctx->stepconst();
     f.robots = ctx->d_stream.p;
     f.n_robots = ctx->n_stream;
+    f.cube40 = ctx->stream_cube40 ? 1 : 0;
     const int nseg = (N + K - 1) / K;
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
@@ -1646,6 +1654,7 @@ sim_status sim_get_contact_modes(voxsim_ctx* ctx, int32_t robot, uint8_t* out)
             f.c = ctx->stepconst();
             f.robots = ctx->d_stream.p;
             f.n_robots = ctx->n_stream;
+            f.cube40 = ctx->stream_cube40 ? 1 : 0;
             float4* ru[2] = {ctx->d_rep_u0.p, ctx->d_rep_u1.p};
             float4* rv[2] = {ctx->d_rep_v0.p, ctx->d_rep_v1.p};
             for (int i = 0; i < n1 - n0; ++i) {

@@ -203,6 +203,7 @@ struct StreamArgs {
     StepConst c;
     const int* robots;       // streamed robots (grid.y)
     int n_robots;
+    int cube40;              // every streamed robot is 40 x 40 x 40 (compile-time strides)
     // checkpoint of the state at the start of this step (NULL: none), per corner
     float4* ckpt_u;
     float4* ckpt_v;
@@ -236,6 +237,7 @@ struct StreamAdjArgs {
     StepConst c;
     const int* robots;       // streamed robots (grid.y)
     int n_robots;
+    int cube40;              // every streamed robot is 40 x 40 x 40 (compile-time strides)
     float* g_k;              // per voxel accumulators
     float* g_a;
     float* g_b;

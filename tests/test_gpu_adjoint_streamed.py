@@ -104,3 +104,22 @@ def test_checkpointing_routes_atomic_robots_to_the_streamed_path(vs):
     _, launches_back = sim.timing()
     assert launches_back < 40
     sim.close()
+
+
+def test_forty_cube_adjoint_equals_the_generic_kernel(vs):
+    """The streamed adjoint's compile-time 40 x 40 x 40 instantiation against the generic kernel
+    (one robot of another grid added): the forward runs agree bitwise, the gradients up to the
+    order of the per-voxel atomic sums."""
+    rng = np.random.default_rng(91)
+    dims = [(40, 40, 40)]
+    g40 = [W.bernoulli_grid(rng, dims[0], 0.7)]
+    extra = W.bernoulli_grid(rng, (26, 22, 24), 0.7)
+    pop = W.make_population(dims, g40)
+    both = W.make_population(dims + [(26, 22, 24)], g40 + [extra])
+    w, kappa, phi = W.voxel_params(rng, both)
+    n = pop.mats.size
+    fa, ga = grads(vs, pop, w[:n], kappa[:n], phi[:n], 120, 50, path=vs.PATH_STREAMED)
+    fb, gb = grads(vs, both, w, kappa, phi, 120, 50, path=vs.PATH_STREAMED)
+    assert np.array_equal(fa, fb[:1])
+    for x, y in zip(ga, gb):
+        assert rel(y[:n], x) < 1e-5

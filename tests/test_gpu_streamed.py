@@ -39,6 +39,24 @@ def test_streamed_equals_resident_lattice_bitwise(vs, nsteps):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
 
 
+def test_forty_cube_instantiation_equals_the_generic_kernel(vs):
+    """Streamed robots that are all 40 x 40 x 40 run the compile-time instantiation of that
+    grid; one robot of another grid added sends the same robots through the generic kernel.
+    States and fitness agree bit for bit (an odd step count leaves the newest state in the
+    alternate buffer)."""
+    rng = np.random.default_rng(76)
+    dims = [(40, 40, 40), (40, 40, 40)]
+    grids = [W.bernoulli_grid(rng, d, 0.7) for d in dims]
+    extra = W.bernoulli_grid(rng, (30, 20, 25), 0.7)
+    pop = W.make_population(dims, grids)
+    both = W.make_population(dims + [(30, 20, 25)], grids + [extra])
+    a = run(vs, pop, 151, path=vs.PATH_STREAMED)
+    b = run(vs, both, 151, path=vs.PATH_STREAMED)
+    n = int(a[2][-1])
+    assert np.array_equal(a[0], b[0][:n]) and np.array_equal(a[1], b[1][:n])
+    assert np.array_equal(a[3], b[3][:2])
+
+
 def test_large_robots_match_oracle(vs, orc):
     """Bernoulli(0.7) grids of 16^3 and 20x18x22 voxels (more corners than one SM holds)."""
     grids = [W.bernoulli_grid(np.random.default_rng(71), (16, 16, 16), 0.7),
