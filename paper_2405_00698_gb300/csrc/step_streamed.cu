@@ -60,7 +60,9 @@ k_step_streamed(StreamArgs a, int n)
     // them) and its evaluation takes no branch (another 5 %): du = 0 and k = 0 make its force an
     // exact zero that leaves the sums' bits unchanged.  The sums keep the fixed order (forward by
     // direction, then backward by direction).
-    constexpr int kBatch = kStreamBatch;
+    // the 40^3 instantiation, with its addresses constant, has the registers for batches of five
+    // directions (1.098x over three; six spill)
+    constexpr int kBatch = NC ? 5 : kStreamBatch;
     for_each_batch<kBatch>([&](auto t0) {      // forward springs (c, c + offset(d))
         constexpr int d0 = decltype(t0)::value;
         constexpr int nb = d0 + kBatch <= 13 ? kBatch : 13 - d0;
