@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_adjoint_lattice(AdjointArgs a)
                             lattice_rest<d>(c), lattice_rest_sq<d>(c), k, __uint_as_float(cur[1]),
                             __uint_as_float(cur[2]), sc.x, sc.y);
                         float ldx, ldy, ldz, dk, da, db;
-                        spring_adjoint(e, k, lFx - gb.x, lFy - gb.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz, dk, da, db);
+                        // lambda_F_a - lambda_F_b, x and y as one paired fused multiply-add
+                        const float2 lf = __ffma2_rn(make_float2(gb.x, gb.y), kMinusOne2, make_float2(lFx, lFy));
+                        spring_adjoint(e, k, lf.x, lf.y, lFz - gb.z, sc.x, sc.y, ldx, ldy, ldz, dk, da, db);
                         lux -= ldx; luy -= ldy; luz -= ldz;
                         sl[d * Ss + cidx] = make_float4(ldx, ldy, ldz, e.ext);
                         __syncwarp();
