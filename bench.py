@@ -606,7 +606,7 @@ def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=5000):
             "launches": launches, "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
                                                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                                                "note": "the algorithmic bound; measured, the kernel is bound by "
-                                                       "instruction issue and load latency (60 % of issue slots, "
+                                                       "instruction issue and load latency (65 % of issue slots, "
                                                        "every spring evaluated by both ends), not by HBM: "
                                                        "populations that fit L2 run no faster"}}
 
