@@ -622,7 +622,7 @@ def oracle_generation(genomes, Bmat, N, nthreads=0):
 
     from oracle import oracle as O
     P = genomes.shape[0]
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+    with ThreadPoolExecutor(max_workers=nthreads if nthreads > 0 else (os.cpu_count() or 4)) as ex:
         dec = list(ex.map(lambda g: O.mlp_query(GRID, Bmat, g), genomes))
     mats = [d[0].reshape(GRID[::-1]) for d in dec]
     w = np.concatenate([d[1] for d in dec])
@@ -650,9 +650,15 @@ def cpu_baseline(genomes, Bmat, N, budget_s=12.0):
         dt += time.perf_counter() - t1
         upd += u2
         n += more
+    # the same pass on one host thread, over two genomes (about a second)
+    t2 = time.perf_counter()
+    u1, _ = oracle_generation(genomes[:2], Bmat, N, nthreads=1)
+    dt1 = time.perf_counter() - t2
     return {"value": upd / dt, "unit": "spring-updates/s", "cores": th, "kind": "oracle",
             "sample": f"{n} of the 1024 genomes, full {N}-step generation (decode, simulate, "
-                      f"fitness, evolve), OpenMP over robots; {dt:.1f} s"}
+                      f"fitness, evolve), OpenMP over robots; {dt:.1f} s",
+            "single_thread": {"value": u1 / dt1, "unit": "spring-updates/s", "cores": 1,
+                              "sample": f"2 of the 1024 genomes, full {N}-step generation; {dt1:.1f} s"}}
 
 
 def run_reference(args):
