@@ -405,6 +405,10 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
         smem_peak, smem_src = measured_smem_peak(sim)
     sim.close()
     sub = pop.subset(W.stratified_subset(S, plain_robots))
+    cpu = None
+    if not getattr(args, "no_cpu_baseline", False):
+        cpu = cpu_baseline_population(pop.subset(range(plain_robots)), 500,
+                                      f"the first {plain_robots} of the {P} robots, 500 steps")
     res = {}
     for name, path in (("plain", vs.PATH_PLAIN), ("batched_same_sample", vs.PATH_AUTO)):
         s2 = vs.Simulator(W.CONFIG, stream=stream, path=path)
@@ -435,7 +439,8 @@ def measure_uneven(vs, stream, args, peaks, P=4096, N=5000, plain_robots=64, pla
                                "unit": "GB/s", "frac": res["plain_gbs"] / peaks["hbm_gbs"],
                                "note": "launch bound: two launches per robot and step"},
             "plain_sample": f"{plain_robots} robots stratified by spring count, {plain_steps} steps",
-            "speedup_vs_plain": batched / res["plain"]}
+            "speedup_vs_plain": batched / res["plain"],
+            **({"cpu_baseline": cpu} if cpu else {})}
 
 
 def measure_adjoint(vs, stream, args, P=512, N=2000, K=100, records=False):
@@ -601,6 +606,10 @@ def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=5000):
     # written (4 x 16 B)
     alg = (12.0 * S.astype(np.int64).sum() + 64.0 * M.astype(np.int64).sum()) * N
     gbs = alg / (kms * 1e-3) / 1e9
+    cpu = None
+    if not getattr(args, "no_cpu_baseline", False):
+        ncpu = min(P, 16)
+        cpu = cpu_baseline_population(pop.subset(range(ncpu)), 50, f"{ncpu} of the {P} robots, 50 steps")
     return {"workload": f"{P} robots {n}^3, occupancy 0.7, {N} steps", "unit": "spring-updates/s",
             "value": ups, "springs_per_robot": float(S.mean()), "masses_per_robot": float(M.mean()),
             "launches": launches, "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
@@ -608,7 +617,8 @@ def measure_streamed(vs, stream, args, peaks, P=64, n=40, N=5000):
                                                "note": "the algorithmic bound; measured, the kernel is bound by "
                                                        "instruction issue and load latency (65 % of issue slots, "
                                                        "every spring evaluated by both ends), not by HBM: "
-                                                       "populations that fit L2 run no faster"}}
+                                                       "populations that fit L2 run no faster"},
+            **({"cpu_baseline": cpu} if cpu else {})}
 
 
 # ------------------------------------------------------------------------------------------
@@ -659,6 +669,18 @@ def cpu_baseline(genomes, Bmat, N, budget_s=12.0):
                       f"fitness, evolve), OpenMP over robots; {dt:.1f} s",
             "single_thread": {"value": u1 / dt1, "unit": "spring-updates/s", "cores": 1,
                               "sample": f"2 of the 1024 genomes, full {N}-step generation; {dt1:.1f} s"}}
+
+
+def cpu_baseline_population(pop, N, sample):
+    """The oracle simulating a sample of one of the other workloads (direct materials, no
+    decode or evolution), OpenMP over its robots: spring updates per second."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    res = O.run_population(pop, W.CONFIG, N)
+    dt = time.perf_counter() - t0
+    upd = int(res["S"].astype(np.int64).sum()) * N
+    return {"value": upd / dt, "unit": "spring-updates/s", "cores": min(int(res["threads"]), pop.P),
+            "kind": "oracle", "sample": f"{sample}; {dt:.1f} s"}
 
 
 def run_reference(args):

@@ -620,7 +620,7 @@ double orc_robot_fitness(const orc_robot* R, const orc_params* p)
 /* Build and simulate P robots (voxel grids concatenated, robot r at voxel_off[r]), write the
  * fitness and optionally the final positions (robot r's masses at mass_off[r], 3 doubles each),
  * and the mass / spring counts.  w, kappa, phi are per voxel or NULL.  nthreads <= 0 uses the
- * OpenMP default.  Returns the number of threads used. */
+ * OpenMP default; a positive count holds for this call only.  Returns the number of threads used. */
 int orc_run_population(int P, const int32_t* dims, const int64_t* voxel_off, const uint8_t* mats,
                        const double* w, const double* kappa, const double* phi,
                        const orc_params* p, int apply_lcc, int nsteps, int nthreads,
@@ -629,13 +629,14 @@ int orc_run_population(int P, const int32_t* dims, const int64_t* voxel_off, con
 {
     int used = 1;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel
+    /* a num_threads clause, not omp_set_num_threads: a request applies to this call only */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt)
     {
 #pragma omp single
         used = omp_get_num_threads();
     }
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (int r = 0; r < P; ++r) {
         int64_t o = voxel_off[r];
