@@ -179,7 +179,10 @@ const char* sim_last_error(const voxsim_ctx* ctx);
  * message the call returns: words[1] bit 2 (a bounded wait of the tensor-core MLP query gave up;
  * the kernel drains its copies and MMAs before it frees its tensor memory) and words[0] bit 0 (the
  * component labelling hit its iteration bound) give SIM_ETIMEOUT, words[0] bit 1 (a material
- * id out of range in device-memory genomes) SIM_EINVAL, none SIM_OK.  words: host int32 [4].
+ * id out of range in device-memory genomes) SIM_EINVAL, none SIM_OK.  words[2] bit 3 is the
+ * stepping's (a segment of the lattice step gave up its bounded wait for its robots' previous
+ * segment, see sim_step_n), reported as SIM_ETIMEOUT by sim_fitness into host memory.
+ * words: host int32 [4].
  * Needs no device: it lets a caller (and the test-suite) check the mapping without making a
  * device-side wait run out.  The paper has no counterpart.  Errors: SIM_EINVAL for NULL. */
 sim_status sim_check_status_words(const int32_t* words);
@@ -206,7 +209,11 @@ sim_status sim_set_population(voxsim_ctx* ctx, int32_t P, const int32_t* dims, i
  * step n is n * dt from the last sim_set_population.  Kinetic friction removes mu_k F_n along
  * the horizontal force but never more than that force (with Table II's mu_s < mu_k it would
  * otherwise reverse it).  When checkpointing is on
- * (sim_set_checkpointing), the call records the states the adjoint needs.
+ * (sim_set_checkpointing), the call records the states the adjoint needs.  With more lattice
+ * work items than SMs (and at least 512 steps) the resident lattice step runs every item's steps
+ * as segments from one queue, each segment waiting (bounded, on the device) for its robots'
+ * previous one; the results are the same bits as whole runs.  A wait that gives up is reported
+ * by the next sim_fitness into host memory (SIM_ETIMEOUT).
  * Errors: SIM_ESTATE without a population, SIM_EINVAL for n_steps < 0. */
 sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
 
@@ -215,7 +222,9 @@ sim_status sim_step_n(voxsim_ctx* ctx, int32_t n_steps);
  * FP64.  Empty robots score 0; a robot with a non-finite coordinate, or one beyond dead_bound,
  * scores -infinity.  out: double [P] in `mem` (host: the call synchronises the stream).
  * Errors: SIM_ESTATE without a population, SIM_EINVAL for a NULL out or a `mem` other than
- * SIM_MEM_HOST / SIM_MEM_DEVICE, SIM_ECUDA. */
+ * SIM_MEM_HOST / SIM_MEM_DEVICE, SIM_ECUDA; into host memory also SIM_ETIMEOUT when a segmented
+ * lattice step since the population was set gave up a wait (its robots' state is invalid;
+ * the fitness is still written). */
 sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem);
 
 /* One generation of the evolutionary step, fully on the GPU (Section II-C; Table I):

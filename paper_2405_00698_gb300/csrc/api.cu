@@ -217,6 +217,7 @@ struct voxsim_ctx {
     DevBuf<int> d_dims;
     DevBuf<int64_t> d_voff, d_moff, d_soff, d_tmp_off;
     DevBuf<int> d_nm, d_ns, d_lpt, d_queue, d_status, d_item_robots, d_big, d_grad_rows;
+    DevBuf<int> d_progress;      // per lattice item: segments done (segmented queue)
     DevBuf<int4> d_items;
     DevBuf<uint32_t> d_cflags;
     DevBuf<float> d_prm;
@@ -351,9 +352,14 @@ sim_status copy_out(void* dst, const void* src, size_t bytes, int mem, cudaStrea
 // Status words the decode and topology kernels raise (device int32 [4], zeroed per population):
 //   word 0 bit 0: the component labelling of a robot hit its iteration bound;
 //   word 0 bit 1: a material id of device-memory genomes was out of range (decoded as empty);
-//   word 1 bit 2: a bounded wait of the tensor-core MLP query gave up (the CTA aborted).
+//   word 1 bit 2: a bounded wait of the tensor-core MLP query gave up (the CTA aborted);
+//   word 2 bit 3: a segment of the per-corner lattice step gave up waiting for its robots'
+//   previous segment (read by sim_fitness into host memory).
 sim_status status_from_words(const int32_t* w)
 {
+    if (w[2] & 8)
+        return fail(SIM_ETIMEOUT, "lattice step: a segment's bounded wait on its robots' previous segment "
+                                  "gave up (their state is invalid)");
     if (w[1] & 4)
         return fail(SIM_ETIMEOUT, "MLP query: a bounded wait on the tensor-core pipeline gave up "
                                   "(copies and MMAs drained, decoded materials invalid)");
@@ -853,6 +859,7 @@ static sim_status build_work_items(voxsim_ctx* ctx, const std::vector<int>* subs
         VX_CK(cudaMemcpyAsync(ctx->d_v_alt.p, ctx->d_v.p, sizeof(float4) * ctx->M_cap, cudaMemcpyDeviceToDevice, s));
     }
     VX_CK(ctx->d_items.ensure(items.size()));
+    VX_CK(ctx->d_progress.ensure(items.size()));
     VX_CK(ctx->d_item_robots.ensure(robots.size()));
     VX_CK(ctx->d_big.ensure(big.size()));
     if (!items.empty()) {
@@ -989,6 +996,16 @@ static sim_status timing_pair(voxsim_ctx* ctx, cudaEvent_t ev[2])
     return SIM_OK;
 }
 
+// Segments per item of the per-corner lattice launch: with more items than SMs, each item's n
+// steps are split so that the queue holds about 64 units per SM (at least 256 steps each); the
+// last wave then waits for one segment of the slowest items instead of one whole run.
+static int lattice_segments(int items, int n, int sms)
+{
+    if (items <= sms || n < 512) return 1;
+    const int want = (64 * sms + items - 1) / items, cap = n / 256;
+    return std::max(1, std::min(want, cap));
+}
+
 // record: the call is sim_step_n's with checkpointing on (checkpoints, and the whole-trajectory
 // records when they are kept, are written; every other caller steps without recording).
 static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
@@ -1042,7 +1059,19 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
     }
     if (n_corner > 0 && !(packed && ctx->pitems_cover_corner)) {
         a.n_items = n_corner;
+        // (segmented instantiations exist for the undamped per-corner steps without imposed
+        // modes, recording only on 8 x 8 x 8 robots)
+        const bool seg_ok = !a.imp_modes && !a.c.damped && (!a.rec_u || ctx->corner_cube8);
+        const int nseg = seg_ok ? lattice_segments(n_corner, n, ctx->num_sms) : 1;
+        if (nseg > 1) {
+            a.nseg = nseg;
+            a.seg_steps = (n + nseg - 1) / nseg;
+            a.progress = ctx->d_progress.p;
+            a.status = ctx->d_status.p + 2;
+            VX_CK(cudaMemsetAsync(a.progress, 0, sizeof(int) * n_corner, ctx->stream));
+        }
         VX_LAUNCH(ctx, launch_step_lattice(a, std::min(n_corner, ctx->num_sms), threads, smem, ctx->stream));
+        a.nseg = 0;
     }
     if (n_spring > 0) {
         a.items = ctx->d_items.p + n_corner;
@@ -1285,7 +1314,14 @@ sim_status sim_fitness(voxsim_ctx* ctx, double* out, int32_t mem)
     double* dst = mem == SIM_MEM_DEVICE ? out : ctx->d_fit.p;
     VX_LAUNCH(ctx, launch_fitness(ctx->view(), ctx->d_mass_corner.p, ctx->d_x.p, ctx->d_x0.p,
                                   (float)ctx->p.dead_bound, dst, s));
-    if (mem == SIM_MEM_HOST) return copy_out(out, ctx->d_fit.p, sizeof(double) * ctx->P, mem, s);
+    if (mem == SIM_MEM_HOST) {
+        // the status words ride along: a segmented lattice step that gave up waiting shows here
+        int32_t words[4];
+        VX_CK(cudaMemcpyAsync(words, ctx->d_status.p, sizeof(words), cudaMemcpyDeviceToHost, s));
+        if (sim_status st = copy_out(out, ctx->d_fit.p, sizeof(double) * ctx->P, mem, s)) return st;
+        const int32_t step_words[4] = {0, 0, words[2], 0};   // the population's own were reported
+        return status_from_words(step_words);
+    }
     return SIM_OK;
 }
 

@@ -167,6 +167,14 @@ struct LatticeArgs {
     const int4* groups;      // mass-packed kernel: per group (robot, first thread, threads,
                              // shared-memory offset in float4)
     int n_items;
+    // per-corner kernel, segmented queue (nseg > 1): unit u = seg * n_items + item steps the
+    // item's robots through steps [seg * seg_steps, min((seg + 1) * seg_steps, nsteps)) once the
+    // item's previous segment has published progress[item] = seg (zeroed before the launch);
+    // a wait that gives up sets bit 3 of *status
+    int nseg;
+    int seg_steps;
+    int* progress;
+    int* status;
     int has_split;           // the items include split ones (run by the split instantiation)
     int cube8;               // every per-corner item is one 8 x 8 x 8 robot in a 768-thread slot
     int* queue;              // work counter, zeroed before the launch

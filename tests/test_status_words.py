@@ -43,3 +43,8 @@ def test_timeout_wins_over_other_flags_and_clear_words_pass(lib):
 
 def test_null_words_rejected(lib):
     assert lib.lib().sim_check_status_words(None) == lib.SIM_EINVAL
+
+
+def test_lattice_segment_wait_gave_up_maps_to_timeout(lib):
+    st, msg = check(lib, [0, 0, 8, 0])
+    assert st == lib.SIM_ETIMEOUT and "segment" in msg and "gave up" in msg
