@@ -46,10 +46,10 @@ SMEM_PEAK_MEASURED_NOTE = ("measured: sim_measure_smem_bandwidth, two 1024-threa
 # DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
 # 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
 # stays in shared memory, so traffic grows with the robots, not with the steps.
-LATTICE_DRAM_BYTES_PER_ROBOT = 18.91e6 / 152
-LATTICE_TRAFFIC_NOTE = ("ncu dram bytes of one k_step_lattice launch (152 robots, 1000 steps) scaled by "
-                        "robots; independent of the step count (the packed kernel reads 0.127 MB per "
-                        "robot, 2 % more)")
+# DRAM bytes of the segmented per-corner step per (segment, robot) unit: none counted yet for
+# this kernel (the earlier figure was the whole-run kernel's)
+LATTICE_DRAM_BYTES_PER_UNIT = None
+LATTICE_TRAFFIC_NOTE = "not yet counted for k_step_lattice_seg"
 
 
 def parse():
@@ -334,10 +334,11 @@ def run_ours(args):
         "gpu_launches": launches,
         "spring_plus_mass_updates_per_s": sm_value,
         "roofline": {"bound": "smem",
-                     "kernel": "k_step_lattice (k_step_lattice_packed once the robots fill less than 55 % "
-                               "of their slots: generations 8 and 9)",
+                     "kernel": "k_step_lattice_seg (the per-corner step from a queue of 1000-step segments; "
+                               "k_step_lattice_packed once the robots fill less than 55 % of their slots: "
+                               "generations 8 and 9)",
                      "achieved": achieved_gbs, "peak": smem_peak, "unit": "GB/s",
-                     "frac": achieved_gbs / smem_peak, "traffic": LATTICE_DRAM_BYTES_PER_ROBOT * P,
+                     "frac": achieved_gbs / smem_peak, "traffic": (LATTICE_DRAM_BYTES_PER_UNIT * P * 10 if LATTICE_DRAM_BYTES_PER_UNIT else None),
                      "traffic_source": LATTICE_TRAFFIC_NOTE,
                      "peak_source": smem_src, "peak_nominal": SMEM_PEAK_GBS,
                      "kernel_ms_per_step": kernel_ms / args.steps},
