@@ -46,10 +46,13 @@ SMEM_PEAK_MEASURED_NOTE = ("measured: sim_measure_smem_bandwidth, two 1024-threa
 # DRAM bytes of one k_step_lattice launch per robot (ncu dram__bytes_read.sum + write of the
 # 152-robot, 1000-step capture in profiles/k_step_lattice__mlp152_8cube_1000steps.md): the state
 # stays in shared memory, so traffic grows with the robots, not with the steps.
-# DRAM bytes of the segmented per-corner step per (segment, robot) unit: none counted yet for
-# this kernel (the earlier figure was the whole-run kernel's)
-LATTICE_DRAM_BYTES_PER_UNIT = None
-LATTICE_TRAFFIC_NOTE = "not yet counted for k_step_lattice_seg"
+# DRAM bytes of one generation's k_step_lattice_seg launch of the default workload (ncu: 1.29 GB
+# read + 198.1 MB written for 1024 robots, 10 segments of 1000 steps), per robot: every
+# (segment, robot) unit reloads its robot's parameters and state
+LATTICE_DRAM_BYTES_PER_ROBOT = (1.29e9 + 198.1e6) / 1024
+LATTICE_TRAFFIC_NOTE = ("ncu dram bytes (read + write) of the generation-0 k_step_lattice_seg launch of this "
+                        "workload (1024 robots, 10,000 steps as 10 segments), scaled by robots; the "
+                        "one-launch figure the roofline's kernel is timed against, default workload only")
 
 
 def parse():
@@ -338,7 +341,7 @@ def run_ours(args):
                                "k_step_lattice_packed once the robots fill less than 55 % of their slots: "
                                "generations 8 and 9)",
                      "achieved": achieved_gbs, "peak": smem_peak, "unit": "GB/s",
-                     "frac": achieved_gbs / smem_peak, "traffic": (LATTICE_DRAM_BYTES_PER_UNIT * P * 10 if LATTICE_DRAM_BYTES_PER_UNIT else None),
+                     "frac": achieved_gbs / smem_peak, "traffic": (LATTICE_DRAM_BYTES_PER_ROBOT * P if (P, N) == (P_ROBOTS, SIM_STEPS) else None),
                      "traffic_source": LATTICE_TRAFFIC_NOTE,
                      "peak_source": smem_src, "peak_nominal": SMEM_PEAK_GBS,
                      "kernel_ms_per_step": kernel_ms / args.steps},
