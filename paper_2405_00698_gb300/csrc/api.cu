@@ -197,6 +197,10 @@ struct voxsim_ctx {
     // CUDA graph of the streamed N-step loop, cached by step count (captured on a private
     // non-blocking stream, replayed on the context's stream)
     cudaStream_t capture_stream = nullptr;
+    // the resident adjoint's replays run on their own stream (backward_lattice); events: replay
+    // of record buffer 0 / 1 done, sweep of record buffer 0 / 1 done, start of the backward
+    cudaStream_t replay_stream = nullptr;
+    cudaEvent_t ev_bwd[5] = {};
     cudaGraphExec_t stream_graph = nullptr;
     int stream_graph_n = -1;
     const void* stream_graph_key = nullptr;   // buffers the graph was captured with
@@ -422,6 +426,12 @@ sim_status sim_destroy(voxsim_ctx* ctx)
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     ctx->drop_graph();
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->replay_stream) {
+        cudaStreamSynchronize(ctx->replay_stream);
+        cudaStreamDestroy(ctx->replay_stream);
+    }
+    for (cudaEvent_t e : ctx->ev_bwd)
+        if (e) cudaEventDestroy(e);
     delete ctx;   // device buffers are released by their destructors
     return SIM_OK;
 }
@@ -1462,12 +1472,25 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     const bool full = ctx->records_usable();
     const int N = ctx->rec_n, K = full ? N : ctx->ckpt_every;
     const size_t Mc = ctx->M_cap;
+    // Without every step's record the backward replays each checkpoint segment (last to first)
+    // before its reverse sweep.  The replays run on a second stream into two record buffers, so
+    // the replay of segment s - 1 overlaps the sweep of segment s (each a persistent launch whose
+    // last wave leaves SMs idle): the sweep of s waits for its replay, and the replay into a
+    // buffer waits for the sweep that read it before.
+    cudaStream_t r = s;
     if (!full) {
-        VX_CK(ctx->d_srec_u.ensure((size_t)K * Mc));
-        VX_CK(ctx->d_srec_f.ensure((size_t)K * Mc));
+        VX_CK(ctx->d_srec_u.ensure(2 * (size_t)K * Mc));
+        VX_CK(ctx->d_srec_f.ensure(2 * (size_t)K * Mc));
         VX_CK(ctx->d_slu.ensure(Mc)); VX_CK(ctx->d_slv.ensure(Mc));
         VX_CK(ctx->d_sacc.ensure(39 * Mc));
         VX_CK(ctx->d_rep_u0.ensure(Mc)); VX_CK(ctx->d_rep_v0.ensure(Mc));
+        VX_CK(ctx->d_rep_u1.ensure(Mc)); VX_CK(ctx->d_rep_v1.ensure(Mc));
+        if (!ctx->replay_stream) VX_CK(cudaStreamCreateWithFlags(&ctx->replay_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : ctx->ev_bwd)
+            if (!e) VX_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        r = ctx->replay_stream;
+        VX_CK(cudaEventRecord(ctx->ev_bwd[4], s));     // the forward run and the zeroed sums
+        VX_CK(cudaStreamWaitEvent(r, ctx->ev_bwd[4], 0));
     }
     const int threads = lattice_max_threads();
     const size_t smem = sizeof(float4) * kLatticeSlotVec4 * (size_t)threads;
@@ -1514,17 +1537,28 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
         if (!full) {
-            VX_CK(cudaMemcpyAsync(ctx->d_rep_u0.p, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
-                                  cudaMemcpyDeviceToDevice, s));
-            VX_CK(cudaMemcpyAsync(ctx->d_rep_v0.p, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
-                                  cudaMemcpyDeviceToDevice, s));
-            f.u = ctx->d_rep_u0.p;
-            f.v = ctx->d_rep_v0.p;
+            const int b = seg & 1;                     // record buffer of this segment
+            if (seg + 2 <= nseg - 1) VX_CK(cudaStreamWaitEvent(r, ctx->ev_bwd[2 + b], 0));
+            float4* u0 = b ? ctx->d_rep_u1.p : ctx->d_rep_u0.p;
+            float4* v0 = b ? ctx->d_rep_v1.p : ctx->d_rep_v0.p;
+            VX_CK(cudaMemcpyAsync(u0, ctx->d_ckpt_u.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, r));
+            VX_CK(cudaMemcpyAsync(v0, ctx->d_ckpt_v.p + (size_t)seg * Mc, sizeof(float4) * Mc,
+                                  cudaMemcpyDeviceToDevice, r));
+            f.u = u0;
+            f.v = v0;
+            f.rec_u = ctx->d_srec_u.p + (size_t)b * K * Mc;
+            f.rec_f = ctx->d_srec_f.p + (size_t)b * K * Mc;
             f.sc = ctx->d_sc_rec.p + n0;
             f.nsteps = n1 - n0;
             f.imp_step0 = ctx->rec_step0 + n0;
-            VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
-            VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, s));
+            f.queue = ctx->d_queue.p + 1;
+            VX_CK(cudaMemsetAsync(f.queue, 0, sizeof(int), r));
+            VX_LAUNCH(ctx, launch_step_lattice(f, grid, threads, smem, r));
+            VX_CK(cudaEventRecord(ctx->ev_bwd[b], r));
+            VX_CK(cudaStreamWaitEvent(s, ctx->ev_bwd[b], 0));
+            a.rec_u = f.rec_u;
+            a.rec_f = f.rec_f;
         }
         a.n0 = n0;
         a.n1 = n1;
@@ -1533,6 +1567,7 @@ static sim_status backward_lattice(voxsim_ctx* ctx, const double* dL_df)
         VX_CK(cudaMemsetAsync(ctx->d_queue.p, 0, sizeof(int), s));
         // slots plus the double-buffered record staging (a float4 and a float2 per thread)
         VX_LAUNCH(ctx, launch_adjoint_lattice(a, grid, threads, smem + (size_t)threads * 2 * (16 + 8), s));
+        if (!full) VX_CK(cudaEventRecord(ctx->ev_bwd[2 + (seg & 1)], s));   // its record buffer is free
     }
     return SIM_OK;
 }
