@@ -338,8 +338,8 @@ def run_ours(args):
         "spring_plus_mass_updates_per_s": sm_value,
         "roofline": {"bound": "smem",
                      "kernel": "k_step_lattice_seg (the per-corner step from a queue of 1000-step segments; "
-                               "k_step_lattice_packed once the robots fill less than 55 % of their slots: "
-                               "generations 8 and 9)",
+                               "k_step_lattice_packed_seg, the mass-packed groups from the same kind of queue, "
+                               "once the robots fill less than 55 % of their slots: generations 8 and 9)",
                      "achieved": achieved_gbs, "peak": smem_peak, "unit": "GB/s",
                      "frac": achieved_gbs / smem_peak, "traffic": (LATTICE_DRAM_BYTES_PER_ROBOT * P if (P, N) == (P_ROBOTS, SIM_STEPS) else None),
                      "traffic_source": LATTICE_TRAFFIC_NOTE,

@@ -983,6 +983,7 @@ static sim_status build_packed_items(voxsim_ctx* ctx, const std::vector<std::vec
         ctx->pitem_smem = std::max(ctx->pitem_smem, bin.smem);
     }
     VX_CK(ctx->d_pitems.ensure(items.size()));
+    VX_CK(ctx->d_progress.ensure(items.size()));
     VX_CK(ctx->d_pgroups.ensure(groups.size()));
     VX_CK(cudaMemcpyAsync(ctx->d_pitems.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, ctx->stream));
     VX_CK(cudaMemcpyAsync(ctx->d_pgroups.p, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1064,6 +1065,15 @@ static sim_status step_lattice(voxsim_ctx* ctx, int n, bool record)
         b.n_items = ctx->n_pitems;
         b.queue = ctx->d_queue.p + 1;
         VX_CK(cudaMemsetAsync(b.queue, 0, sizeof(int), ctx->stream));
+        // the same segmented queue as the per-corner launch below (undamped packed groups)
+        const int nseg = !a.c.damped ? lattice_segments(ctx->n_pitems, n, ctx->num_sms) : 1;
+        if (nseg > 1) {
+            b.nseg = nseg;
+            b.seg_steps = (n + nseg - 1) / nseg;
+            b.progress = ctx->d_progress.p;
+            b.status = ctx->d_status.p + 2;
+            VX_CK(cudaMemsetAsync(b.progress, 0, sizeof(int) * ctx->n_pitems, ctx->stream));
+        }
         VX_LAUNCH(ctx, launch_step_lattice_packed(b, std::min(ctx->n_pitems, ctx->num_sms), ctx->pitem_smem,
                                                   ctx->stream));
     }

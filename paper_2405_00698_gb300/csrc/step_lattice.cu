@@ -630,13 +630,134 @@ __global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed(L
     }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Segmented queue for the mass-packed step (undamped): the packed items' steps cut into a.nseg
+// segments, queued segment-major, each unit waiting (bounded) for its item's previous segment
+// and publishing its own, exactly as k_step_lattice_seg does for the per-corner step; the step
+// itself is k_step_lattice_packed's undamped arithmetic in its order (the same bits as whole runs).
+// ----------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMaxLatticeThreads, 1) k_step_lattice_packed_seg(LatticeArgs a)
+{
+    extern __shared__ __align__(16) float4 sm4[];
+    // item (first group, groups), more work, -, -, segment, item index, segment's end
+    __shared__ int sh_item[8];
+    const int tid = threadIdx.x;
+    const StepConst c = a.c;
+    for (;;) {
+        if (tid == 0) {
+            const int it = atomicAdd(a.queue, 1);
+            if (it < a.n_items * a.nseg) {
+                const int seg = it / a.n_items, ii = it - seg * a.n_items;
+                const int4 item = a.items[ii];
+                sh_item[0] = item.x; sh_item[1] = item.y; sh_item[2] = 1;
+                sh_item[5] = seg; sh_item[6] = ii;
+                sh_item[7] = min((seg + 1) * a.seg_steps, a.nsteps);
+                if (seg > 0) {
+                    uint32_t k = 0;
+                    while (ld_acquire_gpu(a.progress + ii) < seg) {
+                        if (++k >= kSegSpinLimit) { atomicOr(a.status, 8); break; }
+                        __nanosleep(256);
+                    }
+                }
+            } else {
+                sh_item[2] = 0;
+            }
+        }
+        __syncthreads();
+        if (!sh_item[2]) break;
+        const int first = sh_item[0], count = sh_item[1];
+        const int n_begin = sh_item[5] * a.seg_steps;
+        __syncthreads();   // everyone has read the item before thread 0 may overwrite it
+        int group = -1;
+        int4 gi = make_int4(0, 0, 0, 0);
+        for (int j = 0; j < count; ++j) {
+            const int4 q = a.groups[first + j];
+            if (tid >= q.y && tid < q.y + q.z) { group = j; gi = q; }
+        }
+        if (group >= 0) {
+            const int r = gi.x, T = gi.z, lt = tid - gi.y;
+            const int nx = a.pv.dims[3 * r], ny = a.pv.dims[3 * r + 1], nz = a.pv.dims[3 * r + 2];
+            const int X = nx + 1, XY = (nx + 1) * (ny + 1), C = XY * (nz + 1);
+            const int64_t mo = a.pv.moff[r];
+            const int bar = 1 + group;
+            float4* su = sm4 + gi.w;                 // displacements by corner, slot id in .w
+            float4* fb = su + C;                     // plane d at fb + d * T, by the reader's slot;
+                                                     // then 32 rows for absent springs (never read)
+            const int M = a.pv.n_mass[r];
+            const bool in = lt < M;
+            const int cidx = in ? a.corner_order[mo + lt] : 0;
+            const uint32_t fl = in ? a.cflags[mo + cidx] : 0u;
+            const float slot = __int_as_float(lt);
+            const int junk = 13 * T + (lt & 31);     // this lane's row for absent springs
+            float pk[13], pa[13], pb[13];
+            const float* prm = a.prm + 39 * mo;
+            for_each_dir([&](auto t) {
+                constexpr int d = decltype(t)::value;
+                const bool has = (fl >> d) & 1u;
+                pk[d] = has ? prm[(0 * 13 + d) * C + cidx] : 0.f;
+                pa[d] = has ? prm[(1 * 13 + d) * C + cidx] : 0.f;
+                pb[d] = has ? prm[(2 * 13 + d) * C + cidx] : 0.f;
+            });
+            // the previous segment's state, written by another SM: read through L2
+            float4 u = in ? __ldcg(a.u + mo + cidx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = in ? __ldcg(a.v + mo + cidx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) su[cidx] = make_float4(u.x, u.y, u.z, slot);
+            group_sync(bar, T);
+            for (int n = n_begin; n < *(volatile int*)&sh_item[7]; ++n) {
+                if (a.ckpt_u && in && n % a.ckpt_every == 0) {   // state at the start of segment n / K
+                    const int64_t o = (int64_t)(n / a.ckpt_every) * a.ckpt_stride + mo + cidx;
+                    a.ckpt_u[o] = u;
+                    a.ckpt_v[o] = v;
+                }
+                const float2 sc = a.sc[n];
+                float2 Fxy = make_float2(0.f, 0.f);
+                float Fz = 0.f;
+                if (in) for_each_dir([&](auto t) {
+                    constexpr int d = decltype(t)::value;
+                    const bool has = (fl >> d) & 1u;
+                    float4 ub = u;
+                    if (has) ub = su[cidx + lattice_offset<d>(X, XY)];
+                    SpringEval e = spring_eval_ends<d>(ub, u, c.edge, lattice_rest<d>(c), lattice_rest_sq<d>(c),
+                                                      pk[d], pa[d], pb[d], sc.x, sc.y);
+                    Fxy = __fadd2_rn(Fxy, make_float2(e.gx, e.gy)); Fz = __fadd_rn(Fz, e.gz);
+                    const int row = has ? d * T + __float_as_int(ub.w) : junk;
+                    fb[row] = make_float4(e.gx, e.gy, e.gz, e.ext);
+                });
+                group_sync(bar, T);
+                if (in) {
+                    for_each_dir([&](auto t) {
+                        constexpr int d = decltype(t)::value;
+                        if (!((fl >> (16 + d)) & 1u)) return;
+                        const float4 g = fb[d * T + lt];   // force on the spring's first end
+                        Fxy = __ffma2_rn(make_float2(g.x, g.y), kMinusOne2, Fxy); Fz = __fsub_rn(Fz, g.z);
+                    });
+                    if ((fl >> 31) & 1u) {
+                        mass_update(u, v, Fxy.x, Fxy.y, Fz, c);
+                        su[cidx] = make_float4(u.x, u.y, u.z, slot);
+                    }
+                }
+                group_sync(bar, T);
+            }
+            if (in) {
+                a.u[mo + cidx] = u;
+                a.v[mo + cidx] = v;
+                __threadfence();                   // visible before the segment is published
+            }
+        }
+        __syncthreads();
+        if (tid == 0) st_release_gpu(a.progress + sh_item[6], sh_item[5] + 1);
+    }
+}
+
 }  // namespace
 
 int lattice_max_threads() { return kMaxLatticeThreads; }
 
 cudaError_t launch_step_lattice_packed(const LatticeArgs& a, int grid, size_t smem, cudaStream_t s)
 {
-    auto kernel = a.c.damped ? k_step_lattice_packed<true> : k_step_lattice_packed<false>;
+    // a segmented queue (a.nseg > 1; the host sets it only for undamped robots)
+    auto kernel = a.nseg > 1 ? k_step_lattice_packed_seg
+                : (a.c.damped ? k_step_lattice_packed<true> : k_step_lattice_packed<false>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kernel<<<grid, kMaxLatticeThreads, smem, s>>>(a);

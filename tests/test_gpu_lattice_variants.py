@@ -55,17 +55,20 @@ def test_variants_agree_bitwise(vs, case, phys_name, variant):
     assert np.array_equal(a[2], b[2])
 
 
-def test_segmented_queue_equals_whole_runs(vs):
-    """With more robots than SMs (and enough steps) the per-corner launch queues every robot's
-    steps as segments, each waiting for its robot's previous segment; with at most one robot per
-    SM every robot runs whole.  The same robots stepped either way agree bit for bit."""
+@pytest.mark.parametrize("variant", ["CORNER", "PACKED"])
+def test_segmented_queue_equals_whole_runs(vs, variant):
+    """With more work items than SMs (and enough steps) the per-corner and the mass-packed
+    launches queue every item's steps as segments, each waiting for its item's previous segment;
+    with at most one item per SM every item runs whole.  The same robots stepped either way agree
+    bit for bit (8x8x8 robots at occupancy 0.7 have too many masses to share a block)."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     P = sms + 48
     pop = W.population_bernoulli(P, (8, 8, 8), 0.7, seed=75)
     n = 700
-    a = run(vs, pop, W.CONFIG, n, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
-    parts = [run(vs, pop.subset(list(idx)), W.CONFIG, n, vs.LATTICE_CORNER, path=vs.PATH_RESIDENT)
+    lattice = getattr(vs, "LATTICE_" + variant)
+    a = run(vs, pop, W.CONFIG, n, lattice, path=vs.PATH_RESIDENT)
+    parts = [run(vs, pop.subset(list(idx)), W.CONFIG, n, lattice, path=vs.PATH_RESIDENT)
              for idx in (range(0, sms), range(sms, P))]
     assert np.array_equal(a[0], np.concatenate([b[0] for b in parts]))
     assert np.array_equal(a[1], np.concatenate([b[1] for b in parts]))
