@@ -335,7 +335,10 @@ sim_status sim_set_trajectory_records(voxsim_ctx* ctx, int32_t on);
  * by its own sweep).  The checkpoints are left intact, so the call may be repeated with another
  * dL_df on the same recorded run.  Empty voxels get 0.  dL_df: double [P]; g_w, g_kappa,
  * g_phi: float, one entry per voxel of every grid (concatenated as in sim_set_population); all
- * device memory.  Errors: SIM_ESTATE without a recorded run, SIM_EINVAL, SIM_ENOMEM. */
+ * device memory.  The resident robots' segment replays run on a second stream that the context
+ * creates on first use, ordered against the context's stream by events (the call's work starts
+ * after, and ends before, what the context's stream holds around it).
+ * Errors: SIM_ESTATE without a recorded run, SIM_EINVAL, SIM_ENOMEM. */
 sim_status sim_backward(voxsim_ctx* ctx, const double* dL_df, float* g_w, float* g_kappa,
                         float* g_phi);
 
